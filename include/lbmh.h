@@ -1,0 +1,168 @@
+/*
+ * lbmh — C ABI of a B300 (sm_103a) implementation of the lattice Boltzmann
+ * method with adaptive relaxation parameter and Lax-Friedrichs-type
+ * equilibrium for hyperbolic systems with source terms (Zhang, Lin, Zhao,
+ * Zhao, arXiv 2609.18177).
+ *
+ * One call of lbmh_step advances the whole lattice by one collide-and-stream
+ * step of Eq. (2.2) in the implementation form of Section 2.1:
+ *   U = sum_k f_k (2.3); abar_j = max_x max_r |lambda_r(dF_j/dU)| (2.19);
+ *   dt = CFL dx / sum_j abar_j, lambda = dx/dt (2.21);
+ *   Lax-Friedrichs-type equilibrium (2.20); characteristic smoothness
+ *   indicator (2.13)-(2.14), smoothed over the 3^d box (2.15), omega (2.16);
+ *   collision plus half the source at x - e_k, pull streaming, the implicit
+ *   moment (2.8) and the second half of the source at x.
+ *
+ * Conventions
+ *   - Every function returns LBMH_OK (0) or a negative LBMH_ERR_* code.  The
+ *     message of the last error of a handle is kept until the next call on
+ *     that handle (lbmh_last_error).
+ *   - The library owns the device memory of a handle (distributions, scratch,
+ *     control block); the caller owns every array it passes in.
+ *   - Work is enqueued on the CUDA stream given in the problem (NULL = the
+ *     legacy default stream).  lbmh_step and lbmh_advance_to are asynchronous
+ *     except where stated; lbmh_moments, lbmh_get_f, lbmh_omega and lbmh_info
+ *     synchronise the stream.
+ *   - A handle is not thread-safe.  Handles are independent.
+ *   - Layouts: conservative state U is SoA FP64 [m][ny][nx] (x fastest);
+ *     distributions f are FP64 [Q][m][ny][nx] with k = 0..2d in the order
+ *     e_0 = 0, e_j = unit vector j, e_{j+d} = -e_j (Section 2.3).  In 1D,
+ *     ny = 1.  Nodes sit at cell centres x_i = x0 + (i + 1/2) dx.
+ */
+#ifndef LBMH_H
+#define LBMH_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBMH_API __attribute__((visibility("default")))
+#else
+#define LBMH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBMH_OK 0
+#define LBMH_ERR_INVALID_ARG (-1)  /* bad problem description, pointer or size */
+#define LBMH_ERR_OOM (-2)          /* device allocation failed */
+#define LBMH_ERR_NONPHYSICAL (-3)  /* a step produced NaN/inf, rho<=0 or p<=0 */
+#define LBMH_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up */
+#define LBMH_ERR_CUDA (-5)         /* a CUDA runtime call failed */
+#define LBMH_ERR_UNSUPPORTED (-6)  /* valid request this build does not provide */
+
+/* Physical systems, Section 5: scalar advection u_t + a.grad u = 0; Euler
+ * (gamma-law gas); shallow water (g) with optional Gaussian bed-slope source;
+ * reactive Euler with one-step Arrhenius kinetics.  LBMH_LINEAR (constant
+ * symmetric matrices, Section 4) is accepted by the oracle only. */
+typedef enum {
+  LBMH_ADVECTION = 0,
+  LBMH_EULER = 1,
+  LBMH_SWE = 2,
+  LBMH_REACTIVE_EULER = 3,
+  LBMH_LINEAR = 4
+} lbmh_system;
+
+typedef enum { LBMH_BC_PERIODIC = 0, LBMH_BC_OUTFLOW = 1 } lbmh_bc;
+
+/* LBMH_FP64: distributions stored and collided in FP64.
+ * LBMH_FP32: distributions stored and collided in FP32; the conservation sums
+ * and the Arrhenius source and its implicit update stay in FP64. */
+typedef enum { LBMH_FP64 = 0, LBMH_FP32 = 1 } lbmh_precision;
+
+typedef enum { LBMH_OMEGA_ADAPTIVE = 0, LBMH_OMEGA_FIXED = 1 } lbmh_omega_mode;
+
+/* Step implementation: the fused single-pass kernel (default where
+ * available) or the unfused four-kernel reference path. */
+typedef enum { LBMH_KERNEL_AUTO = 0, LBMH_KERNEL_FUSED = 1, LBMH_KERNEL_UNFUSED = 2 } lbmh_kernel;
+
+/* Statement of the balance law (2.1) and its discretisation.  Field names
+ * follow the paper: cfl of (2.21), eps of alpha_j = abar_j + eps (Section 5
+ * uses 1e-10), omega from (2.16) unless omega_mode is FIXED. */
+typedef struct lbmh_problem {
+  int system;          /* lbmh_system */
+  int dim;             /* 1 or 2; the lattice is DdQ(2d+1) */
+  int nx, ny;          /* nodes per direction (ny ignored in 1D) */
+  double x0, x1, y0, y1; /* domain; 2D requires (x1-x0)/nx == (y1-y0)/ny */
+  int bc[4];           /* lbmh_bc at x-lo, x-hi, y-lo, y-hi; periodic must pair */
+  double cfl, eps;
+  double adv[2];       /* advection velocity a */
+  double gamma, g;     /* Euler ratio of specific heats; gravity */
+  double bed_amp, bed_w2, bed_xc, bed_yc; /* bed b = amp exp(-((x-xc)^2+(y-yc)^2)/w2) */
+  double K, Ti, q;     /* Arrhenius rate constant, activation temperature, heat release */
+  int m_linear;        /* LBMH_LINEAR only */
+  const double *A;     /* LBMH_LINEAR only */
+  int omega_mode;      /* lbmh_omega_mode */
+  double omega_fixed;
+  double h_dry;        /* shallow water: h < h_dry is dry (u = v = 0); 1e-8 if 0 */
+  int precision;       /* lbmh_precision */
+  int kernel;          /* lbmh_kernel */
+  void *cuda_stream;   /* cudaStream_t to enqueue on */
+} lbmh_problem;
+
+typedef struct lbmh_handle lbmh_handle;
+
+/* Diagnostics of the current state (after the last enqueued step). */
+typedef struct lbmh_info {
+  double t;            /* simulated time */
+  int64_t steps;       /* steps executed */
+  double abar[2];      /* speed bound of the current state (2.19) */
+  double last_dt, last_lambda; /* of the last executed step */
+  double sum_U[8];     /* FP64 sum over nodes of U after the last executed step */
+  uint32_t status;     /* bit 0: non-physical state (NaN/inf, rho<=0, p<=0); bit 1: reaction
+                          root not converged; bit 3: negative depth h < -1e-12 (reported
+                          only: the scheme is not positivity preserving at wet-dry fronts) */
+  int m, Q;            /* fields and velocities */
+  int kernel;          /* implementation in use: LBMH_KERNEL_FUSED or _UNFUSED */
+  int64_t device_bytes; /* device memory owned by the handle */
+} lbmh_info;
+
+/* Validate the problem and allocate device memory for it.  *out receives a
+ * handle (NULL on error).  The state is undefined until lbmh_set_state. */
+LBMH_API int lbmh_create(const lbmh_problem *p, lbmh_handle **out);
+
+/* Set t = 0 and f_k := f_k^eq(U) with alpha and lambda from U (Eq. 2.20).
+ * U: FP64 [m][ny][nx]; a device pointer when on_device != 0, else host.
+ * Enqueued on the handle's stream; a host U is copied before returning. */
+LBMH_API int lbmh_set_state(lbmh_handle *h, const double *U, int on_device);
+
+/* Enqueue n time steps (n >= 0).  Asynchronous; no host synchronisation. */
+LBMH_API int lbmh_step(lbmh_handle *h, int64_t n);
+
+/* Step until t >= T (the step that crosses T is taken whole; there is no
+ * clipped final step) or max_steps steps were taken.  Synchronises the
+ * stream every few dozen steps to test t. */
+LBMH_API int lbmh_advance_to(lbmh_handle *h, double T, int64_t max_steps);
+
+/* U = sum_k f_k of the current state into U_out (FP64 [m][ny][nx], device
+ * pointer if on_device).  Synchronises.  t and steps may be NULL.  Returns
+ * LBMH_ERR_NONPHYSICAL if a step flagged a non-physical state. */
+LBMH_API int lbmh_moments(lbmh_handle *h, double *U_out, int on_device, double *t, int64_t *steps);
+
+/* Checkpoint: copy the distributions out (FP64 [Q][m][ny][nx], host or
+ * device), or replace them together with the time and step count.  A
+ * restored handle continues bitwise-identically. */
+LBMH_API int lbmh_get_f(lbmh_handle *h, double *f_out, int on_device, double *t, int64_t *steps);
+LBMH_API int lbmh_set_f(lbmh_handle *h, const double *f_in, int on_device, double t, int64_t steps);
+
+/* omega of every node that the next step will use (Eq. 2.16), FP64 [ny][nx]. */
+LBMH_API int lbmh_omega(lbmh_handle *h, double *out, int on_device);
+
+/* Fill *out; synchronises. */
+LBMH_API int lbmh_get_info(lbmh_handle *h, lbmh_info *out);
+
+/* Free everything owned by the handle.  NULL is accepted. */
+LBMH_API int lbmh_destroy(lbmh_handle *h);
+
+/* Message of the last error on h (or of the last lbmh_create failure when h
+ * is NULL).  Never NULL. */
+LBMH_API const char *lbmh_last_error(const lbmh_handle *h);
+
+/* Library version string. */
+LBMH_API const char *lbmh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBMH_H */

@@ -1,0 +1,132 @@
+// Shared device-side definitions of the lbmh CUDA library: problem constants,
+// the per-handle step-control block and small helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmh {
+
+enum { SYS_ADV = 0, SYS_EULER = 1, SYS_SWE = 2, SYS_REACT = 3 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
+
+// number of conserved fields m of each system in d dimensions
+template <int SYS, int D>
+struct Fields {
+  static constexpr int M = SYS == SYS_ADV ? 1 : SYS == SYS_EULER ? D + 2 : SYS == SYS_SWE ? D + 1 : D + 3;
+  static constexpr int Q = 2 * D + 1;  // DdQ(2d+1) lattice, Section 2.3
+};
+
+// Problem constants, passed by value to every kernel.
+struct DevParams {
+  int nx, ny;        // ny = 1 in 1D
+  int pitch;         // elements between rows of one distribution plane
+  long long plane;   // elements between planes (ny * pitch)
+  int bc[4];         // xlo, xhi, ylo, yhi
+  double x0, y0, dx;
+  double cfl, eps;
+  double T;          // > 0: steps stop once t >= T
+  double adv[2];
+  double gamma, g, h_dry;
+  double bed_amp, bed_w2, bed_xc, bed_yc;
+  double K, Ti, q;
+  int omega_mode;    // 0 adaptive, 1 fixed
+  double omega_fixed;
+};
+
+// Step-control block in device memory.  Step n reads slot n % 3, folds the
+// next step's speed bound into slot (n+1) % 3 and clears slot (n+2) % 3, so a
+// sequence of launches needs no host round trip (the global maximum of
+// Eq. (2.19) is a side output of the previous step).
+struct Ctl {
+  unsigned long long amax[3][2];  // bit patterns of non-negative doubles
+  double t[3];
+  long long nsteps[3];
+  int parity[3];                  // distribution buffer holding the state
+  int pad;
+  double last_dt, last_lambda;    // of the most recent executed step
+  double ainit[2];                // speed bound of the initial state U0
+  unsigned int status;            // LBMH status bits, sticky
+  unsigned int pad2;
+};
+
+// status bits: NONPHYSICAL (NaN/inf, rho <= 0 or p <= 0) fails lbmh_moments;
+// NEGATIVE_DEPTH (shallow water h < -1e-12, which the scheme produces at
+// wet-dry fronts: it is not positivity preserving) is reported only.
+enum : unsigned int { ST_NONPHYSICAL = 1u, ST_NOROOT = 2u, ST_TIMEOUT = 4u, ST_NEGATIVE_DEPTH = 8u };
+
+// Coefficients of one step, computed identically by every thread from the
+// control slot: dt (2.21), lambda = dx/dt, alpha_j = abar_j + eps, and the
+// equilibrium weights a_k of (2.5)/(2.20).
+struct StepCoef {
+  double dt, lam, alpha[2], a0, aj[2];
+  int active;
+};
+
+__device__ __forceinline__ double bits_to_double(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+inline double bits_to_host(unsigned long long b) {
+  union {
+    unsigned long long u;
+    double d;
+  } v;
+  v.u = b;
+  return v.d;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* slot, double v) {
+  // max of non-negative doubles == max of their bit patterns; NaN (bit pattern
+  // above +inf) wins, which keeps a blown-up state visible
+  atomicMax(slot, (unsigned long long)__double_as_longlong(v));
+}
+
+template <int D>
+__device__ __forceinline__ StepCoef step_coef(const DevParams& P, const Ctl* ctl, int slot) {
+  StepCoef c;
+  double ab0 = bits_to_double(ctl->amax[slot][0]);
+  double ab1 = D == 2 ? bits_to_double(ctl->amax[slot][1]) : 0.0;
+  double t = ctl->t[slot];
+  c.active = !(P.T > 0.0 && t >= P.T);
+  double asum = D == 2 ? ab0 + ab1 : ab0;
+  c.dt = P.cfl * P.dx / asum;
+  c.lam = P.dx / c.dt;
+  c.alpha[0] = ab0 + P.eps;
+  c.alpha[1] = D == 2 ? ab1 + P.eps : 0.0;
+  double alsum = D == 2 ? c.alpha[0] + c.alpha[1] : c.alpha[0];
+  c.a0 = 1.0 - alsum / c.lam;
+  c.aj[0] = c.alpha[0] / (2.0 * c.lam);
+  c.aj[1] = c.alpha[1] / (2.0 * c.lam);
+  return c;
+}
+
+// Block 0 advances the control block: slot+1 receives t, step count and
+// parity; slot+2 is cleared for the step after next.
+template <int D>
+__device__ __forceinline__ void advance_ctl(Ctl* ctl, int slot, const StepCoef& c) {
+  int s1 = (slot + 1) % 3, s2 = (slot + 2) % 3;
+  if (c.active) {
+    ctl->t[s1] = ctl->t[slot] + c.dt;
+    ctl->nsteps[s1] = ctl->nsteps[slot] + 1;
+    ctl->parity[s1] = ctl->parity[slot] ^ 1;
+    ctl->last_dt = c.dt;
+    ctl->last_lambda = c.lam;
+  } else {
+    ctl->t[s1] = ctl->t[slot];
+    ctl->nsteps[s1] = ctl->nsteps[slot];
+    ctl->parity[s1] = ctl->parity[slot];
+    ctl->amax[s1][0] = ctl->amax[slot][0];
+    ctl->amax[s1][1] = ctl->amax[slot][1];
+  }
+  ctl->amax[s2][0] = 0ull;
+  ctl->amax[s2][1] = 0ull;
+}
+
+// index of a ghost coordinate e in [-3, n+3) mapped into [0, n): periodic
+// wraps, outflow clamps (every read of f^n outside the domain is a read of the
+// nearest interior node, or of the wrapped node)
+__device__ __forceinline__ int map_index(int e, int n, int bc_lo, int bc_hi) {
+  if (e < 0) return bc_lo == BC_PERIODIC ? (e % n + n) % n : 0;
+  if (e >= n) return bc_hi == BC_PERIODIC ? e % n : n - 1;
+  return e;
+}
+
+}  // namespace lbmh

@@ -1,0 +1,734 @@
+// Host side of the lbmh C ABI: validation, device memory, step launches and
+// the template dispatch over (system, dimension, precision).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lbmh.h"
+#include "common.cuh"
+#include "fused.cuh"
+#include "physics.cuh"
+#include "unfused.cuh"
+
+using namespace lbmh;
+
+namespace {
+
+constexpr int kBlock = 256;
+
+struct Ops;
+
+}  // namespace
+
+struct lbmh_handle {
+  lbmh_problem prob;
+  DevParams P;
+  int m, Q, dim, sys, prec;
+  int kernel;               // LBMH_KERNEL_FUSED or LBMH_KERNEL_UNFUSED
+  size_t elem;              // sizeof(real)
+  long long plane;          // ny * pitch
+  cudaStream_t stream;
+  void* fbuf[2];
+  void** dbuf;              // device copy of fbuf
+  void* Ue;                 // unfused scratch: U_ext [m][ey][ex]
+  void* nue;                // nu_ext
+  void* ome;                // omega_ext
+  ExtGeom G;
+  double* partials;         // per-block FP64 sums of the last step
+  int nblocks;              // blocks writing partials in the last step
+  int max_blocks;
+  Ctl* ctl;
+  double* Utmp;             // FP64 staging [m][ny][nx] or [Q][m][ny][nx]
+  long long launched;       // step launches since set_state
+  bool has_state;
+  long long device_bytes;
+  const Ops* ops;
+  FusedPlan fp;
+  std::string err;
+};
+
+namespace {
+
+std::string g_create_error;
+
+int fail(lbmh_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg; else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(lbmh_handle* h, cudaError_t e, const char* what) {
+  return fail(h, LBMH_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                    \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+int nfields(int sys, int dim) {
+  switch (sys) {
+    case SYS_ADV: return 1;
+    case SYS_EULER: return dim + 2;
+    case SYS_SWE: return dim + 1;
+    case SYS_REACT: return dim + 3;
+  }
+  return -1;
+}
+
+// ---------------------------------------------------------------------------
+// initial state and diagnostics kernels
+// ---------------------------------------------------------------------------
+
+// speed bound (2.19) of a FP64 state U0 [m][ny][nx] -> ctl->ainit
+template <int SYS, int D>
+__global__ void k_init_speed(DevParams P, const double* U0, Ctl* ctl) {
+  constexpr int M = Fields<SYS, D>::M;
+  long long nn = (long long)P.nx * P.ny;
+  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double s0 = 0.0, s1 = 0.0;
+  if (node < nn) {
+    double U[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) U[c] = U0[c * nn + node];
+    Prim<double> w = primitives<SYS, D, double>(P, U);
+    s0 = max_speed<SYS, D, double>(P, w, 0);
+    if (D == 2) s1 = max_speed<SYS, D, double>(P, w, 1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
+    s1 = fmax(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg((unsigned long long*)&ctl->ainit[0], s0);
+    atomic_max_nonneg((unsigned long long*)&ctl->ainit[1], s1);
+  }
+}
+
+// f := f^eq(U0) with alpha^0, lambda^0 from ctl->ainit (Eq. 2.20); the speed
+// bound of the stored state goes to slot 0 for the first step.
+template <int SYS, int D, class R>
+__global__ void k_init_eq(DevParams P, const double* U0, R* f, Ctl* ctl) {
+  constexpr int M = Fields<SYS, D>::M, Q = Fields<SYS, D>::Q;
+  long long nn = (long long)P.nx * P.ny;
+  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double ab0 = ctl->ainit[0], ab1 = D == 2 ? ctl->ainit[1] : 0.0;
+  double dt = P.cfl * P.dx / (D == 2 ? ab0 + ab1 : ab0);
+  double lam = P.dx / dt;
+  double al0 = ab0 + P.eps, al1 = D == 2 ? ab1 + P.eps : 0.0;
+  const R a0 = R(1.0 - (D == 2 ? al0 + al1 : al0) / lam), inv2l = R(1.0 / (2.0 * lam));
+  const R al[2] = {R(al0), R(al1)};
+  double s0 = 0.0, s1 = 0.0;
+  if (node < nn) {
+    int j = (int)(node / P.nx), i = (int)(node % P.nx);
+    R U[M], Us[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) {
+      U[c] = R(U0[c * nn + node]);
+      Us[c] = R(0);
+    }
+    Prim<R> w = primitives<SYS, D, R>(P, U);
+    long long off = (long long)j * P.pitch + i;
+#pragma unroll
+    for (int k = 0; k < Q; k++) {
+      R feq[M];
+      if (k == 0) {
+#pragma unroll
+        for (int c = 0; c < M; c++) feq[c] = a0 * U[c];
+      } else {
+        int jd = (k - 1) % D;
+        R F[M];
+        flux<SYS, D, R>(P, U, w, jd, F);
+        R sg = k <= D ? R(1) : R(-1);
+#pragma unroll
+        for (int c = 0; c < M; c++) feq[c] = (al[jd] * U[c] + sg * F[c]) * inv2l;
+      }
+#pragma unroll
+      for (int c = 0; c < M; c++) {
+        f[(long long)(k * M + c) * P.plane + off] = feq[c];
+        Us[c] += feq[c];
+      }
+    }
+    Prim<R> ws = primitives<SYS, D, R>(P, Us);
+    s0 = (double)max_speed<SYS, D, R>(P, ws, 0);
+    if (D == 2) s1 = (double)max_speed<SYS, D, R>(P, ws, 1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
+    s1 = fmax(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(&ctl->amax[0][0], s0);
+    atomic_max_nonneg(&ctl->amax[0][1], s1);
+  }
+}
+
+// U = sum_k f_k into FP64 [m][ny][nx]
+template <int M, int Q, class R>
+__global__ void k_moments(DevParams P, R* const* buf, const Ctl* ctl, int slot, double* U) {
+  long long nn = (long long)P.nx * P.ny;
+  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (node >= nn) return;
+  const R* f = buf[ctl->parity[slot]];
+  int j = (int)(node / P.nx), i = (int)(node % P.nx);
+  long long off = (long long)j * P.pitch + i;
+#pragma unroll
+  for (int c = 0; c < M; c++) {
+    R s = R(0);
+#pragma unroll
+    for (int k = 0; k < Q; k++) s += f[(long long)(k * M + c) * P.plane + off];
+    U[c * nn + node] = (double)s;
+  }
+}
+
+// f <-> FP64 [Q][m][ny][nx] (checkpointing)
+template <class R>
+__global__ void k_get_f(DevParams P, int QM, R* const* buf, const Ctl* ctl, int slot, double* out) {
+  long long nn = (long long)P.nx * P.ny;
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= nn * QM) return;
+  const R* f = buf[ctl->parity[slot]];
+  long long q = idx / nn, node = idx % nn;
+  int j = (int)(node / P.nx), i = (int)(node % P.nx);
+  out[idx] = (double)f[q * P.plane + (long long)j * P.pitch + i];
+}
+
+template <class R>
+__global__ void k_set_f(DevParams P, int QM, R* f, const double* in) {
+  long long nn = (long long)P.nx * P.ny;
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= nn * QM) return;
+  long long q = idx / nn, node = idx % nn;
+  int j = (int)(node / P.nx), i = (int)(node % P.nx);
+  f[q * P.plane + (long long)j * P.pitch + i] = R(in[idx]);
+}
+
+// speed bound of the stored distributions -> slot 0 (after lbmh_set_f)
+template <int SYS, int D, class R>
+__global__ void k_speed_of_f(DevParams P, R* const* buf, Ctl* ctl) {
+  constexpr int M = Fields<SYS, D>::M, Q = Fields<SYS, D>::Q;
+  long long nn = (long long)P.nx * P.ny;
+  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double s0 = 0.0, s1 = 0.0;
+  if (node < nn) {
+    const R* f = buf[ctl->parity[0]];
+    int j = (int)(node / P.nx), i = (int)(node % P.nx);
+    long long off = (long long)j * P.pitch + i;
+    R U[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) {
+      R s = R(0);
+#pragma unroll
+      for (int k = 0; k < Q; k++) s += f[(long long)(k * M + c) * P.plane + off];
+      U[c] = s;
+    }
+    Prim<R> w = primitives<SYS, D, R>(P, U);
+    s0 = (double)max_speed<SYS, D, R>(P, w, 0);
+    if (D == 2) s1 = (double)max_speed<SYS, D, R>(P, w, 1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
+    s1 = fmax(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(&ctl->amax[0][0], s0);
+    atomic_max_nonneg(&ctl->amax[0][1], s1);
+  }
+}
+
+template <class R>
+__global__ void k_extract_interior(DevParams P, ExtGeom G, const R* src_ext, double* out) {
+  long long nn = (long long)P.nx * P.ny;
+  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (node >= nn) return;
+  int j = (int)(node / P.nx), i = (int)(node % P.nx);
+  out[node] = (double)src_ext[G.idx(j + G.gy, i + GH)];
+}
+
+inline unsigned blocks_for(long long n, int bs = kBlock) { return (unsigned)((n + bs - 1) / bs); }
+
+// ---------------------------------------------------------------------------
+// per-(system, dimension, precision) operations
+// ---------------------------------------------------------------------------
+
+struct Ops {
+  int (*launch_step)(lbmh_handle*, int slot, double T);
+  int (*launch_unfused_diag)(lbmh_handle*, int slot);  // K0..K2 only
+  int (*init)(lbmh_handle*, const double* U0dev);
+  int (*moments)(lbmh_handle*, int slot, double* Udev);
+  int (*get_f)(lbmh_handle*, int slot, double* dev);
+  int (*set_f)(lbmh_handle*, const double* dev);
+  int (*omega_extract)(lbmh_handle*, double* dev);
+  int (*setup_fused)(lbmh_handle*);
+  bool has_fused;
+};
+
+template <int SYS, int D, class R>
+struct Impl {
+  static constexpr int M = Fields<SYS, D>::M, Q = Fields<SYS, D>::Q;
+
+  static int unfused_front(lbmh_handle* h, int slot, const DevParams& P) {
+    long long next = (long long)h->G.ex * h->G.ey;
+    unsigned nb = blocks_for(next);
+    R* const* buf = (R* const*)h->dbuf;
+    k_moments_ext<SYS, D, R><<<nb, kBlock, 0, h->stream>>>(P, buf, h->ctl, slot, h->G, (R*)h->Ue);
+    k_indicator<SYS, D, R><<<nb, kBlock, 0, h->stream>>>(P, h->ctl, slot, h->G, (const R*)h->Ue, (R*)h->nue);
+    k_omega<D, R><<<nb, kBlock, 0, h->stream>>>(P, h->ctl, slot, h->G, (const R*)h->nue, (R*)h->ome);
+    return LBMH_OK;
+  }
+
+  static int launch_step(lbmh_handle* h, int slot, double T) {
+    DevParams P = h->P;
+    P.T = T;
+    if (h->kernel == LBMH_KERNEL_FUSED) {
+      h->nblocks = fused_launch<SYS, D, R>(h->fp, P, (R* const*)h->dbuf, h->ctl, slot, h->partials, h->stream);
+    } else {
+      unfused_front(h, slot, P);
+      long long nn = (long long)P.nx * P.ny;
+      unsigned nb = blocks_for(nn);
+      k_collide_stream<SYS, D, R><<<nb, kBlock, 0, h->stream>>>(P, (R* const*)h->dbuf, h->ctl, slot, h->G,
+                                                                (const R*)h->Ue, (const R*)h->ome, h->partials);
+      h->nblocks = (int)nb;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+    return LBMH_OK;
+  }
+
+  static int launch_unfused_diag(lbmh_handle* h, int slot) {
+    DevParams P = h->P;
+    P.T = 0.0;
+    unfused_front(h, slot, P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "diagnostic launch");
+    return LBMH_OK;
+  }
+
+  static int init(lbmh_handle* h, const double* U0dev) {
+    long long nn = (long long)h->P.nx * h->P.ny;
+    unsigned nb = blocks_for(nn);
+    k_init_speed<SYS, D><<<nb, kBlock, 0, h->stream>>>(h->P, U0dev, h->ctl);
+    k_init_eq<SYS, D, R><<<nb, kBlock, 0, h->stream>>>(h->P, U0dev, (R*)h->fbuf[0], h->ctl);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "init launch");
+    return LBMH_OK;
+  }
+
+  static int moments(lbmh_handle* h, int slot, double* Udev) {
+    long long nn = (long long)h->P.nx * h->P.ny;
+    k_moments<M, Q, R><<<blocks_for(nn), kBlock, 0, h->stream>>>(h->P, (R* const*)h->dbuf, h->ctl, slot, Udev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments launch");
+    return LBMH_OK;
+  }
+
+  static int get_f(lbmh_handle* h, int slot, double* dev) {
+    long long n = (long long)h->P.nx * h->P.ny * Q * M;
+    k_get_f<R><<<blocks_for(n), kBlock, 0, h->stream>>>(h->P, Q * M, (R* const*)h->dbuf, h->ctl, slot, dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_f launch");
+    return LBMH_OK;
+  }
+
+  static int set_f(lbmh_handle* h, const double* dev) {
+    long long n = (long long)h->P.nx * h->P.ny * Q * M;
+    k_set_f<R><<<blocks_for(n), kBlock, 0, h->stream>>>(h->P, Q * M, (R*)h->fbuf[0], dev);
+    k_speed_of_f<SYS, D, R><<<blocks_for((long long)h->P.nx * h->P.ny), kBlock, 0, h->stream>>>(
+        h->P, (R* const*)h->dbuf, h->ctl);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_f launch");
+    return LBMH_OK;
+  }
+
+  static int omega_extract(lbmh_handle* h, double* dev) {
+    long long nn = (long long)h->P.nx * h->P.ny;
+    k_extract_interior<R><<<blocks_for(nn), kBlock, 0, h->stream>>>(h->P, h->G, (const R*)h->ome, dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "omega launch");
+    return LBMH_OK;
+  }
+
+  static int setup_fused(lbmh_handle* h) { return fused_setup<SYS, D, R>(h->fp, h->P, h->fbuf); }
+
+  static const Ops* ops() {
+    static const Ops o = {launch_step, launch_unfused_diag, init, moments, get_f, set_f, omega_extract, setup_fused,
+                          fused_available<SYS, D, R>()};
+    return &o;
+  }
+};
+
+template <class R>
+const Ops* pick_dim(int sys, int dim) {
+#define PICK(S)                                        \
+  case S:                                              \
+    return dim == 1 ? Impl<S, 1, R>::ops() : Impl<S, 2, R>::ops();
+  switch (sys) {
+    PICK(SYS_ADV)
+    PICK(SYS_EULER)
+    PICK(SYS_SWE)
+    PICK(SYS_REACT)
+  }
+#undef PICK
+  return nullptr;
+}
+
+const Ops* pick_ops(int sys, int dim, int prec) {
+  return prec == LBMH_FP32 ? pick_dim<float>(sys, dim) : pick_dim<double>(sys, dim);
+}
+
+int validate(const lbmh_problem* p, std::string& why) {
+  if (!p) { why = "problem is NULL"; return LBMH_ERR_INVALID_ARG; }
+  if (p->system == LBMH_LINEAR) { why = "LBMH_LINEAR is provided by the oracle only"; return LBMH_ERR_UNSUPPORTED; }
+  if (p->system < 0 || p->system > 3) { why = "unknown system"; return LBMH_ERR_INVALID_ARG; }
+  if (p->dim != 1 && p->dim != 2) { why = "dim must be 1 or 2"; return LBMH_ERR_INVALID_ARG; }
+  if (p->nx < 1 || (p->dim == 2 && p->ny < 1)) { why = "grid must have at least one node"; return LBMH_ERR_INVALID_ARG; }
+  if ((long long)p->nx * (p->dim == 2 ? p->ny : 1) > (1ll << 34)) { why = "grid too large"; return LBMH_ERR_INVALID_ARG; }
+  if (!(p->x1 > p->x0)) { why = "x1 must exceed x0"; return LBMH_ERR_INVALID_ARG; }
+  for (int s = 0; s < 4; s++)
+    if (p->bc[s] != LBMH_BC_PERIODIC && p->bc[s] != LBMH_BC_OUTFLOW) { why = "bad boundary condition"; return LBMH_ERR_INVALID_ARG; }
+  if ((p->bc[0] == LBMH_BC_PERIODIC) != (p->bc[1] == LBMH_BC_PERIODIC)) { why = "periodic x boundaries must pair"; return LBMH_ERR_INVALID_ARG; }
+  if (p->dim == 2) {
+    if ((p->bc[2] == LBMH_BC_PERIODIC) != (p->bc[3] == LBMH_BC_PERIODIC)) { why = "periodic y boundaries must pair"; return LBMH_ERR_INVALID_ARG; }
+    double dx = (p->x1 - p->x0) / p->nx, dy = (p->y1 - p->y0) / p->ny;
+    if (!(fabs(dx - dy) <= 1e-12 * dx)) { why = "2D mesh must satisfy dx == dy (Section 2.2.2)"; return LBMH_ERR_INVALID_ARG; }
+  }
+  if (!(p->cfl > 0.0)) { why = "cfl must be positive"; return LBMH_ERR_INVALID_ARG; }
+  if (!(p->eps >= 0.0)) { why = "eps must be non-negative"; return LBMH_ERR_INVALID_ARG; }
+  if (p->precision != LBMH_FP64 && p->precision != LBMH_FP32) { why = "bad precision"; return LBMH_ERR_INVALID_ARG; }
+  if (p->kernel < 0 || p->kernel > 2) { why = "bad kernel choice"; return LBMH_ERR_INVALID_ARG; }
+  if (p->omega_mode != 0 && p->omega_mode != 1) { why = "bad omega mode"; return LBMH_ERR_INVALID_ARG; }
+  if ((p->system == LBMH_EULER || p->system == LBMH_REACTIVE_EULER) && !(p->gamma > 1.0)) { why = "gamma must exceed 1"; return LBMH_ERR_INVALID_ARG; }
+  if (p->system == LBMH_SWE && !(p->g > 0.0)) { why = "g must be positive"; return LBMH_ERR_INVALID_ARG; }
+  if (p->system == LBMH_SWE && p->bed_amp != 0.0 && !(p->bed_w2 > 0.0)) { why = "bed width must be positive"; return LBMH_ERR_INVALID_ARG; }
+  return LBMH_OK;
+}
+
+void free_handle(lbmh_handle* h) {
+  if (!h) return;
+  cudaFree(h->fbuf[0]);
+  cudaFree(h->fbuf[1]);
+  cudaFree(h->dbuf);
+  cudaFree(h->Ue);
+  cudaFree(h->nue);
+  cudaFree(h->ome);
+  cudaFree(h->partials);
+  cudaFree(h->ctl);
+  cudaFree(h->Utmp);
+  delete h;
+}
+
+int sync(lbmh_handle* h) {
+  CK(h, cudaStreamSynchronize(h->stream));
+  return LBMH_OK;
+}
+
+int current_slot(const lbmh_handle* h) { return (int)(h->launched % 3); }
+
+int read_ctl(lbmh_handle* h, Ctl* out) {
+  CK(h, cudaMemcpyAsync(out, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+  return sync(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbmh_version(void) { return "lbmh 0.1 sm_103a"; }
+
+const char* lbmh_last_error(const lbmh_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
+  if (!out) return fail(nullptr, LBMH_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  int rc = validate(p, why);
+  if (rc) return fail(nullptr, rc, why);
+  lbmh_handle* h = new lbmh_handle();
+  memset(h->fbuf, 0, sizeof h->fbuf);
+  h->dbuf = nullptr; h->Ue = h->nue = h->ome = nullptr; h->partials = nullptr; h->ctl = nullptr; h->Utmp = nullptr;
+  h->prob = *p;
+  h->dim = p->dim;
+  h->sys = p->system;
+  h->prec = p->precision;
+  h->m = nfields(p->system, p->dim);
+  h->Q = 2 * p->dim + 1;
+  h->elem = p->precision == LBMH_FP32 ? sizeof(float) : sizeof(double);
+  h->stream = (cudaStream_t)p->cuda_stream;
+  h->ops = pick_ops(p->system, p->dim, p->precision);
+  h->launched = 0;
+  h->has_state = false;
+  h->nblocks = 0;
+  h->device_bytes = 0;
+  DevParams& P = h->P;
+  memset(&P, 0, sizeof P);
+  P.nx = p->nx;
+  P.ny = p->dim == 2 ? p->ny : 1;
+  int align = 128 / (int)h->elem;  // rows start on 128-byte boundaries
+  P.pitch = (P.nx + align - 1) / align * align;
+  P.plane = (long long)P.ny * P.pitch;
+  h->plane = P.plane;
+  for (int s = 0; s < 4; s++) P.bc[s] = p->bc[s];
+  if (p->dim == 1) { P.bc[2] = P.bc[3] = LBMH_BC_PERIODIC; }
+  P.x0 = p->x0;
+  P.y0 = p->dim == 2 ? p->y0 : 0.0;
+  P.dx = (p->x1 - p->x0) / p->nx;
+  P.cfl = p->cfl;
+  P.eps = p->eps;
+  P.T = 0.0;
+  P.adv[0] = p->adv[0];
+  P.adv[1] = p->adv[1];
+  P.gamma = p->gamma;
+  P.g = p->g;
+  P.h_dry = p->h_dry > 0.0 ? p->h_dry : 1e-8;
+  P.bed_amp = p->bed_amp;
+  P.bed_w2 = p->bed_w2 > 0.0 ? p->bed_w2 : 1.0;
+  P.bed_xc = p->bed_xc;
+  P.bed_yc = p->bed_yc;
+  P.K = p->K;
+  P.Ti = p->Ti;
+  P.q = p->q;
+  P.omega_mode = p->omega_mode;
+  P.omega_fixed = p->omega_fixed;
+
+  bool want_fused = p->kernel != LBMH_KERNEL_UNFUSED;
+  if (p->kernel == LBMH_KERNEL_FUSED && !h->ops->has_fused) {
+    delete h;
+    return fail(nullptr, LBMH_ERR_UNSUPPORTED, "no fused kernel for this system/dimension/precision");
+  }
+  h->kernel = (want_fused && h->ops->has_fused) ? LBMH_KERNEL_FUSED : LBMH_KERNEL_UNFUSED;
+
+  h->G.ex = P.nx + 2 * GH;
+  h->G.gy = p->dim == 2 ? GH : 0;
+  h->G.ey = p->dim == 2 ? P.ny + 2 * GH : 1;
+  long long nn = (long long)P.nx * P.ny;
+  long long next = (long long)h->G.ex * h->G.ey;
+  size_t fbytes = (size_t)h->Q * h->m * P.plane * h->elem;
+  h->max_blocks = (int)blocks_for(nn);
+  bool need_scratch = true;  // the unfused diagnostics (lbmh_omega) use it too
+  auto alloc = [&](void** ptr, size_t bytes) -> bool {
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    h->device_bytes += (long long)bytes;
+    return true;
+  };
+  bool ok = alloc(&h->fbuf[0], fbytes) && alloc(&h->fbuf[1], fbytes);
+  if (ok && h->kernel == LBMH_KERNEL_FUSED) {
+    memset(&h->fp, 0, sizeof h->fp);
+    if (h->ops->setup_fused(h) != 0) {
+      cudaGetLastError();
+      if (p->kernel == LBMH_KERNEL_FUSED) {
+        free_handle(h);
+        return fail(nullptr, LBMH_ERR_CUDA, "fused kernel setup failed");
+      }
+      h->kernel = LBMH_KERNEL_UNFUSED;
+    } else if (h->fp.blocks > h->max_blocks) {
+      h->max_blocks = h->fp.blocks;
+    }
+  }
+  ok = ok && alloc((void**)&h->dbuf, 2 * sizeof(void*)) &&
+       alloc((void**)&h->partials, (size_t)h->max_blocks * h->m * sizeof(double)) &&
+       alloc((void**)&h->ctl, sizeof(Ctl)) && alloc((void**)&h->Utmp, (size_t)nn * h->m * h->Q * sizeof(double));
+  if (ok && need_scratch)
+    ok = alloc(&h->Ue, (size_t)next * h->m * h->elem) && alloc(&h->nue, (size_t)next * h->elem) &&
+         alloc(&h->ome, (size_t)next * h->elem);
+  if (!ok) {
+    free_handle(h);
+    return fail(nullptr, LBMH_ERR_OOM, "device allocation failed");
+  }
+  cudaError_t e = cudaMemcpy(h->dbuf, h->fbuf, 2 * sizeof(void*), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(h->partials, 0, (size_t)h->max_blocks * h->m * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(h->ctl, 0, sizeof(Ctl));
+  if (e != cudaSuccess) {
+    std::string msg = std::string("setup: ") + cudaGetErrorString(e);
+    free_handle(h);
+    return fail(nullptr, LBMH_ERR_CUDA, msg);
+  }
+  *out = h;
+  return LBMH_OK;
+}
+
+int lbmh_destroy(lbmh_handle* h) {
+  if (!h) return LBMH_OK;
+  cudaStreamSynchronize(h->stream);
+  free_handle(h);
+  return LBMH_OK;
+}
+
+int lbmh_set_state(lbmh_handle* h, const double* U, int on_device) {
+  if (!h) return LBMH_ERR_INVALID_ARG;
+  if (!U) return fail(h, LBMH_ERR_INVALID_ARG, "U is NULL");
+  h->err.clear();
+  long long nn = (long long)h->P.nx * h->P.ny;
+  size_t bytes = (size_t)nn * h->m * sizeof(double);
+  const double* src = U;
+  if (!on_device) {
+    CK(h, cudaMemcpyAsync(h->Utmp, U, bytes, cudaMemcpyHostToDevice, h->stream));
+    src = h->Utmp;
+  }
+  CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->stream));
+  int rc = h->ops->init(h, src);
+  if (rc) return rc;
+  if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
+  h->launched = 0;
+  h->has_state = true;
+  h->nblocks = 0;
+  return LBMH_OK;
+}
+
+int lbmh_step(lbmh_handle* h, int64_t n) {
+  if (!h) return LBMH_ERR_INVALID_ARG;
+  if (!h->has_state) return fail(h, LBMH_ERR_INVALID_ARG, "no state: call lbmh_set_state first");
+  if (n < 0) return fail(h, LBMH_ERR_INVALID_ARG, "negative step count");
+  h->err.clear();
+  for (int64_t s = 0; s < n; s++) {
+    int rc = h->ops->launch_step(h, current_slot(h), 0.0);
+    if (rc) return rc;
+    h->launched++;
+  }
+  return LBMH_OK;
+}
+
+int lbmh_advance_to(lbmh_handle* h, double T, int64_t max_steps) {
+  if (!h) return LBMH_ERR_INVALID_ARG;
+  if (!h->has_state) return fail(h, LBMH_ERR_INVALID_ARG, "no state: call lbmh_set_state first");
+  if (!(T > 0.0) || max_steps < 0) return fail(h, LBMH_ERR_INVALID_ARG, "T must be positive");
+  h->err.clear();
+  int64_t done = 0;
+  Ctl c;
+  int rc = read_ctl(h, &c);
+  if (rc) return rc;
+  long long start = c.nsteps[current_slot(h)];
+  while (done < max_steps) {
+    int slot = current_slot(h);
+    double t = c.t[slot];
+    if (t >= T) break;
+    double ab = bits_to_host(c.amax[slot][0]) + (h->dim == 2 ? bits_to_host(c.amax[slot][1]) : 0.0);
+    double dt_est = h->P.cfl * h->P.dx / ab;
+    int64_t est = (int64_t)((T - t) / dt_est) + 1;
+    int64_t chunk = est < 8 ? 8 : (est > 256 ? 256 : est);
+    if (chunk > max_steps - done) chunk = max_steps - done;
+    for (int64_t s = 0; s < chunk; s++) {
+      rc = h->ops->launch_step(h, current_slot(h), T);
+      if (rc) return rc;
+      h->launched++;
+    }
+    rc = read_ctl(h, &c);
+    if (rc) return rc;
+    done = c.nsteps[current_slot(h)] - start;
+    if (c.status & ST_NONPHYSICAL) break;
+  }
+  return LBMH_OK;
+}
+
+int lbmh_moments(lbmh_handle* h, double* U_out, int on_device, double* t, int64_t* steps) {
+  if (!h) return LBMH_ERR_INVALID_ARG;
+  if (!h->has_state) return fail(h, LBMH_ERR_INVALID_ARG, "no state");
+  if (!U_out) return fail(h, LBMH_ERR_INVALID_ARG, "U_out is NULL");
+  long long nn = (long long)h->P.nx * h->P.ny;
+  size_t bytes = (size_t)nn * h->m * sizeof(double);
+  int slot = current_slot(h);
+  int rc = h->ops->moments(h, slot, on_device ? U_out : h->Utmp);
+  if (rc) return rc;
+  if (!on_device) CK(h, cudaMemcpyAsync(U_out, h->Utmp, bytes, cudaMemcpyDeviceToHost, h->stream));
+  Ctl c;
+  rc = read_ctl(h, &c);
+  if (rc) return rc;
+  if (t) *t = c.t[slot];
+  if (steps) *steps = c.nsteps[slot];
+  if (c.status & ST_TIMEOUT) return fail(h, LBMH_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  if (c.status & ST_NONPHYSICAL) return fail(h, LBMH_ERR_NONPHYSICAL, "a step produced a non-physical state");
+  return LBMH_OK;
+}
+
+int lbmh_get_f(lbmh_handle* h, double* f_out, int on_device, double* t, int64_t* steps) {
+  if (!h) return LBMH_ERR_INVALID_ARG;
+  if (!h->has_state) return fail(h, LBMH_ERR_INVALID_ARG, "no state");
+  if (!f_out) return fail(h, LBMH_ERR_INVALID_ARG, "f_out is NULL");
+  long long n = (long long)h->P.nx * h->P.ny * h->Q * h->m;
+  int slot = current_slot(h);
+  int rc = h->ops->get_f(h, slot, on_device ? f_out : h->Utmp);
+  if (rc) return rc;
+  if (!on_device) CK(h, cudaMemcpyAsync(f_out, h->Utmp, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  Ctl c;
+  rc = read_ctl(h, &c);
+  if (rc) return rc;
+  if (t) *t = c.t[slot];
+  if (steps) *steps = c.nsteps[slot];
+  return LBMH_OK;
+}
+
+int lbmh_set_f(lbmh_handle* h, const double* f_in, int on_device, double t, int64_t steps) {
+  if (!h) return LBMH_ERR_INVALID_ARG;
+  if (!f_in) return fail(h, LBMH_ERR_INVALID_ARG, "f_in is NULL");
+  long long n = (long long)h->P.nx * h->P.ny * h->Q * h->m;
+  const double* src = f_in;
+  if (!on_device) {
+    CK(h, cudaMemcpyAsync(h->Utmp, f_in, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    src = h->Utmp;
+  }
+  Ctl c;
+  memset(&c, 0, sizeof c);
+  c.t[0] = t;
+  c.nsteps[0] = steps;
+  CK(h, cudaMemcpyAsync(h->ctl, &c, sizeof c, cudaMemcpyHostToDevice, h->stream));
+  int rc = h->ops->set_f(h, src);
+  if (rc) return rc;
+  rc = sync(h);
+  if (rc) return rc;
+  h->launched = 0;
+  h->has_state = true;
+  return LBMH_OK;
+}
+
+int lbmh_omega(lbmh_handle* h, double* out, int on_device) {
+  if (!h) return LBMH_ERR_INVALID_ARG;
+  if (!h->has_state) return fail(h, LBMH_ERR_INVALID_ARG, "no state");
+  if (!out) return fail(h, LBMH_ERR_INVALID_ARG, "out is NULL");
+  long long nn = (long long)h->P.nx * h->P.ny;
+  int slot = current_slot(h);
+  int rc = h->ops->launch_unfused_diag(h, slot);
+  if (rc) return rc;
+  rc = h->ops->omega_extract(h, on_device ? out : h->Utmp);
+  if (rc) return rc;
+  if (!on_device) CK(h, cudaMemcpyAsync(out, h->Utmp, (size_t)nn * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return sync(h);
+}
+
+int lbmh_get_info(lbmh_handle* h, lbmh_info* out) {
+  if (!h || !out) return LBMH_ERR_INVALID_ARG;
+  memset(out, 0, sizeof *out);
+  out->m = h->m;
+  out->Q = h->Q;
+  out->kernel = h->kernel;
+  out->device_bytes = h->device_bytes;
+  if (!h->has_state) return LBMH_OK;
+  Ctl c;
+  int rc = read_ctl(h, &c);
+  if (rc) return rc;
+  int slot = current_slot(h);
+  out->t = c.t[slot];
+  out->steps = c.nsteps[slot];
+  out->abar[0] = bits_to_host(c.amax[slot][0]);
+  out->abar[1] = bits_to_host(c.amax[slot][1]);
+  out->last_dt = c.last_dt;
+  out->last_lambda = c.last_lambda;
+  out->status = c.status;
+  if (h->nblocks > 0) {
+    std::vector<double> part((size_t)h->nblocks * h->m);
+    CK(h, cudaMemcpy(part.data(), h->partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int b = 0; b < h->nblocks; b++)
+      for (int c2 = 0; c2 < h->m && c2 < 8; c2++) out->sum_U[c2] += part[(size_t)b * h->m + c2];
+  }
+  return LBMH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,253 @@
+"""Python binding of the lbmh C ABI (include/lbmh.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library ``_lbmh.so`` built from
+``csrc/`` for sm_103a.  There is no fallback: if the library is missing or no
+CUDA device is present, the calls raise.
+
+Device arrays are passed as torch tensors (their data pointers); host arrays
+as numpy arrays.  The CUDA stream is torch's current stream unless one is
+given.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lbmh.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+KERNEL_AUTO, KERNEL_FUSED, KERNEL_UNFUSED = 0, 1, 2
+FP64, FP32 = 0, 1
+
+
+class LbmhError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lbmh error {code}: {msg}")
+        self.code = code
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("system", ctypes.c_int), ("dim", ctypes.c_int),
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+        ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+        ("bc", ctypes.c_int * 4),
+        ("cfl", ctypes.c_double), ("eps", ctypes.c_double),
+        ("adv", ctypes.c_double * 2),
+        ("gamma", ctypes.c_double), ("g", ctypes.c_double),
+        ("bed_amp", ctypes.c_double), ("bed_w2", ctypes.c_double),
+        ("bed_xc", ctypes.c_double), ("bed_yc", ctypes.c_double),
+        ("K", ctypes.c_double), ("Ti", ctypes.c_double), ("q", ctypes.c_double),
+        ("m_linear", ctypes.c_int),
+        ("A", ctypes.POINTER(ctypes.c_double)),
+        ("omega_mode", ctypes.c_int), ("omega_fixed", ctypes.c_double),
+        ("h_dry", ctypes.c_double),
+        ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("t", ctypes.c_double), ("steps", ctypes.c_int64),
+        ("abar", ctypes.c_double * 2),
+        ("last_dt", ctypes.c_double), ("last_lambda", ctypes.c_double),
+        ("sum_U", ctypes.c_double * 8),
+        ("status", ctypes.c_uint32), ("m", ctypes.c_int), ("Q", ctypes.c_int),
+        ("kernel", ctypes.c_int), ("device_bytes", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {"t": self.t, "steps": self.steps, "abar": list(self.abar),
+                "last_dt": self.last_dt, "last_lambda": self.last_lambda,
+                "sum_U": list(self.sum_U)[: self.m], "status": self.status, "m": self.m,
+                "Q": self.Q, "kernel": self.kernel, "device_bytes": self.device_bytes}
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/lbmh.h
+_H = ctypes.c_void_p
+_DP = ctypes.c_void_p
+SIGNATURES = [
+    ("lbmh_create", ctypes.c_int, [ctypes.POINTER(_Problem), ctypes.POINTER(ctypes.c_void_p)]),
+    ("lbmh_set_state", ctypes.c_int, [_H, _DP, ctypes.c_int]),
+    ("lbmh_step", ctypes.c_int, [_H, ctypes.c_int64]),
+    ("lbmh_advance_to", ctypes.c_int, [_H, ctypes.c_double, ctypes.c_int64]),
+    ("lbmh_moments", ctypes.c_int, [_H, _DP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_int64)]),
+    ("lbmh_get_f", ctypes.c_int, [_H, _DP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_int64)]),
+    ("lbmh_set_f", ctypes.c_int, [_H, _DP, ctypes.c_int, ctypes.c_double, ctypes.c_int64]),
+    ("lbmh_omega", ctypes.c_int, [_H, _DP, ctypes.c_int]),
+    ("lbmh_get_info", ctypes.c_int, [_H, ctypes.POINTER(Info)]),
+    ("lbmh_destroy", ctypes.c_int, [_H]),
+    ("lbmh_last_error", ctypes.c_char_p, [_H]),
+    ("lbmh_version", ctypes.c_char_p, []),
+]
+
+
+def load(path=LIB_PATH):
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"lbmh CUDA library not built ({path}); run "
+                          "python -m paper_2609_18177_b300.build")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _c_problem(pb, precision, kernel, stream):
+    s = _Problem()
+    s.system, s.dim, s.nx = int(pb.system), int(pb.dim), int(pb.nx)
+    s.ny = int(pb.ny) if pb.dim == 2 else 1
+    s.x0, s.x1, s.y0, s.y1 = float(pb.x0), float(pb.x1), float(pb.y0), float(pb.y1)
+    for i in range(4):
+        s.bc[i] = int(pb.bc[i])
+    s.cfl, s.eps = float(pb.cfl), float(pb.eps)
+    s.adv[0], s.adv[1] = float(pb.adv[0]), float(pb.adv[1])
+    s.gamma, s.g = float(pb.gamma), float(pb.g)
+    s.bed_amp, s.bed_w2, s.bed_xc, s.bed_yc = (float(pb.bed_amp), float(pb.bed_w2),
+                                               float(pb.bed_xc), float(pb.bed_yc))
+    s.K, s.Ti, s.q = float(pb.K), float(pb.Ti), float(pb.q)
+    s.m_linear = int(getattr(pb, "m_linear", 0))
+    s.omega_mode, s.omega_fixed = int(pb.omega_mode), float(pb.omega_fixed)
+    s.h_dry = float(pb.h_dry)
+    s.precision, s.kernel = int(precision), int(kernel)
+    s.cuda_stream = stream
+    return s
+
+
+def _current_stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or a torch tensor (FP64, contiguous)."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("host arrays must be C-contiguous float64")
+        return a.ctypes.data, 0
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+class Solver:
+    """One lattice held on the GPU (a handle of the C ABI)."""
+
+    def __init__(self, pb, precision=None, kernel=KERNEL_AUTO, stream=None):
+        lib = load()
+        self.pb = pb
+        self.precision = pb.precision if precision is None else precision
+        self._stream = _current_stream() if stream is None else stream
+        self._s = _c_problem(pb, self.precision, kernel, self._stream)
+        h = ctypes.c_void_p()
+        rc = lib.lbmh_create(ctypes.byref(self._s), ctypes.byref(h))
+        if rc != OK:
+            raise LbmhError(rc, lib.lbmh_last_error(None).decode())
+        self._h = h
+        self.m = pb.nfields
+        self.Q = 2 * pb.dim + 1
+
+    def _check(self, rc):
+        if rc != OK:
+            raise LbmhError(rc, load().lbmh_last_error(self._h).decode())
+
+    @property
+    def shape_U(self):
+        return (self.m,) + self.pb.shape()
+
+    @property
+    def shape_f(self):
+        return (self.Q, self.m) + self.pb.shape()
+
+    def set_state(self, U):
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.float64).reshape(self.shape_U)
+        p, dev = _ptr(U)
+        self._check(load().lbmh_set_state(self._h, p, dev))
+        return self
+
+    def step(self, n=1):
+        self._check(load().lbmh_step(self._h, int(n)))
+        return self
+
+    def advance_to(self, T, max_steps=2**62):
+        self._check(load().lbmh_advance_to(self._h, float(T), int(max_steps)))
+        return self
+
+    def moments(self, out=None, check=True):
+        if out is None:
+            out = np.empty(self.shape_U)
+        p, dev = _ptr(out)
+        t = ctypes.c_double()
+        n = ctypes.c_int64()
+        rc = load().lbmh_moments(self._h, p, dev, ctypes.byref(t), ctypes.byref(n))
+        if check or rc != ERR_NONPHYSICAL:
+            self._check(rc)
+        self.t, self.nsteps = t.value, n.value
+        return out
+
+    def get_f(self, out=None):
+        if out is None:
+            out = np.empty(self.shape_f)
+        p, dev = _ptr(out)
+        t = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(load().lbmh_get_f(self._h, p, dev, ctypes.byref(t), ctypes.byref(n)))
+        self.t, self.nsteps = t.value, n.value
+        return out
+
+    def set_f(self, f, t=0.0, steps=0):
+        if isinstance(f, np.ndarray):
+            f = np.ascontiguousarray(f, dtype=np.float64)
+        p, dev = _ptr(f)
+        self._check(load().lbmh_set_f(self._h, p, dev, float(t), int(steps)))
+        return self
+
+    def omega(self, out=None):
+        if out is None:
+            out = np.empty(self.pb.shape())
+        p, dev = _ptr(out)
+        self._check(load().lbmh_omega(self._h, p, dev))
+        return out
+
+    def info(self):
+        inf = Info()
+        self._check(load().lbmh_get_info(self._h, ctypes.byref(inf)))
+        return inf.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lbmh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def version():
+    return load().lbmh_version().decode()
