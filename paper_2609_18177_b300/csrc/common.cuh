@@ -16,10 +16,19 @@ struct Fields {
   static constexpr int Q = 2 * D + 1;  // DdQ(2d+1) lattice, Section 2.3
 };
 
+// Every row of a distribution plane starts with XPAD padding columns: node x
+// sits at column offset x + XPAD, so interior rows start on a 32-byte sector
+// in FP32.  The NGHOST columns on each side of the interior (x in [-4, 0) and
+// [nx, nx+4)) are ghost nodes: the fused 2D kernel keeps them equal to the
+// wrapped / clamped node after each step, so a row of any strip can be
+// fetched with one in-bounds, aligned TMA box.
+constexpr int XPAD = 8;
+constexpr int NGHOST = 4;
+
 // Problem constants, passed by value to every kernel.
 struct DevParams {
   int nx, ny;        // ny = 1 in 1D
-  int pitch;         // elements between rows of one distribution plane
+  int pitch;         // elements between rows of one distribution plane (>= nx + 2*XPAD)
   long long plane;   // elements between planes (ny * pitch)
   int bc[4];         // xlo, xhi, ylo, yhi
   double x0, y0, dx;
@@ -118,6 +127,11 @@ __device__ __forceinline__ void advance_ctl(Ctl* ctl, int slot, const StepCoef& 
   }
   ctl->amax[s2][0] = 0ull;
   ctl->amax[s2][1] = 0ull;
+}
+
+// offset of node (i, j) inside a distribution plane
+__host__ __device__ __forceinline__ long long cell(const DevParams& P, int i, int j) {
+  return (long long)j * P.pitch + i + XPAD;
 }
 
 // index of a ghost coordinate e in [-3, n+3) mapped into [0, n): periodic

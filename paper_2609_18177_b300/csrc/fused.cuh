@@ -20,6 +20,7 @@
 // 1D (D1Q3): one CTA per 120-node chunk, everything in shared memory.
 #pragma once
 #include <cuda.h>
+#include <stdlib.h>
 
 #include "physics.cuh"
 #include "unfused.cuh"
@@ -28,26 +29,50 @@ namespace lbmh {
 
 constexpr int FT = 128;          // threads per CTA = columns per loaded row
 constexpr int FW = FT - 8;       // output columns per strip
-constexpr int FPREF = 2;         // rows in flight ahead of use
+// rows in flight ahead of use: 2 with one column per thread; 1 with two (the
+// ring of 3 + PREF rows must leave room for two CTAs per SM)
+template <int CPT>
+constexpr int fpref() { return CPT == 2 ? 1 : 2; }
 
 struct FusedPlan {
-  int blocks;      // grid size
+  int cpt;         // columns per thread of the 2D kernel (1 or 2)
+  int blocks;      // grid size (2D: strips * segs)
   int strips;      // ceil(nx / FW) (2D)
+  int nxs;         // columns written by the bulk store: nx rounded down to 16 bytes
+  int band;        // rows per band of the band-major work order
   int smem;        // dynamic shared memory bytes
-  CUtensorMap tm[2];
+  CUtensorMap tm[2];   // loads: padded rows of buffer b
+  CUtensorMap tms[2];  // stores: interior columns of buffer b
 };
 
 template <int SYS, int D, class R>
 constexpr bool fused_available() { return true; }
 
-template <int M, class R, int PREF>
+// bulk tensor store of a staged row (shared -> global) as its own bulk group
+__device__ __forceinline__ void tma_store_row(const CUtensorMap* tm, uint32_t src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(tm), "r"(x),
+               "r"(y), "r"(0), "r"(src)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void tma_store_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void tma_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+template <class R> struct Vec2;
+template <> struct Vec2<float> { using T = float2; };
+template <> struct Vec2<double> { using T = double2; };
+
+template <int M, class R, int PREF, int CPT>
 struct Smem2D {
-  static constexpr int QM = 5 * M, S = 3 + PREF;
-  static constexpr size_t f_bytes = (size_t)S * QM * FT * sizeof(R);
-  static constexpr size_t u_bytes = (size_t)2 * M * FT * sizeof(R);
-  static constexpr size_t c_bytes = (size_t)FT * sizeof(R);
-  static constexpr size_t p_bytes = (size_t)2 * 2 * M * FT * sizeof(R);
-  static constexpr size_t bar_off = f_bytes + u_bytes + c_bytes + p_bytes;
+  static constexpr int QM = 5 * M, S = 3 + PREF, NC = FT * CPT, WOUT = NC - 8;
+  static constexpr size_t f_bytes = (size_t)S * QM * NC * sizeof(R);   // ring of f^n rows
+  static constexpr size_t u_bytes = (size_t)2 * M * NC * sizeof(R);    // U of rows r, r-1
+  static constexpr size_t c_bytes = (size_t)NC * sizeof(R);            // nu column sums
+  static constexpr size_t p_bytes = (size_t)2 * 2 * M * FT * sizeof(R); // post_1 / post_3 of rows r-2, r-3
+  static constexpr size_t o_bytes = (size_t)QM * WOUT * sizeof(R);     // f^{n+1} row staged for the TMA store
+  static constexpr size_t o_off = f_bytes + u_bytes + c_bytes + p_bytes;
+  static constexpr size_t bar_off = o_off + o_bytes;
   static constexpr size_t total = bar_off + S * sizeof(unsigned long long);
 };
 
@@ -86,21 +111,46 @@ __device__ __forceinline__ void tma_load_row(const CUtensorMap* tm, uint32_t dst
       : "memory");
 }
 
-__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+// Block-level reduction of the fused kernels' side outputs (max speeds in R,
+// compensated sums already converted to FP64 per thread).
+template <int M, class R>
+__device__ __forceinline__ void fused_side_outputs(R sp0, R sp1, const Acc<R>* acc, Ctl* ctl, int slot1,
+                                                   double* partials, unsigned st) {
+  double usum[M];
+#pragma unroll
+  for (int c = 0; c < M; c++) usum[c] = acc[c].value();
+  block_side_outputs<M>((double)sp0, (double)sp1, usum, ctl, slot1, partials, st);
+}
 
-template <int SYS, class R, int PREF>
-__global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensorMap tm0,
-                                                const __grid_constant__ CUtensorMap tm1, DevParams P,
-                                                R* const* buf, Ctl* ctl, int slot, double* partials, int strips) {
+// CPT: columns per thread (1 or 2).  Lane t holds columns t*CPT .. t*CPT+CPT-1
+// of the CTA's NC = 128*CPT loaded columns; a strip's outputs are columns
+// [4, NC-4).  A thread's own columns pass values to each other in registers;
+// only the outermost columns exchange through shared memory.
+//
+// Work split: the strips x rows of the grid are cut into gridDim equal
+// contiguous chunks (one resident wave, every CTA the same number of rows);
+// a chunk covers one or two strip segments.  Each output row is staged in
+// shared memory and written with one TMA bulk store covering columns
+// [0, nxs), nxs = nx rounded down to 16 bytes: the bulk store writes whole
+// 16-byte granules, so the last columns and the ghost columns behind them
+// are written with plain stores instead.
+template <int SYS, class R, int PREF, int CPT>
+__global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensorMap tl0,
+                                                const __grid_constant__ CUtensorMap tl1,
+                                                const __grid_constant__ CUtensorMap ts0,
+                                                const __grid_constant__ CUtensorMap ts1, DevParams P,
+                                                R* const* buf, Ctl* ctl, int slot, double* partials, int strips,
+                                                int nxs, int band) {
   constexpr int M = Fields<SYS, 2>::M, Q = 5, QM = Q * M;
-  using L = Smem2D<M, R, PREF>;
-  constexpr int S = L::S;
+  constexpr bool SRC = HasSource<SYS>::value;
+  using L = Smem2D<M, R, PREF, CPT>;
+  constexpr int S = L::S, NC = L::NC, WOUT = L::WOUT;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   R* fring = (R*)smem_raw;
   R* Usm = (R*)(smem_raw + L::f_bytes);
   R* colsm = (R*)(smem_raw + L::f_bytes + L::u_bytes);
   R* p13 = (R*)(smem_raw + L::f_bytes + L::u_bytes + L::c_bytes);
+  R* stage = (R*)(smem_raw + L::o_off);
   unsigned long long* bars = (unsigned long long*)(smem_raw + L::bar_off);
   __shared__ int s_abort;
 
@@ -111,8 +161,8 @@ __global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensor
     return;
   }
   const int par = ctl->parity[slot];
-  const CUtensorMap* tm = par ? &tm1 : &tm0;
-  const R* fin = buf[par];
+  const CUtensorMap* tml = par ? &tl1 : &tl0;   // loads from f^n (padded rows)
+  const CUtensorMap* tms = par ? &ts0 : &ts1;   // stores to f^{n+1} (interior columns)
   R* fout = buf[par ^ 1];
 
   if (t == 0) {
@@ -122,203 +172,302 @@ __global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensor
   }
   __syncthreads();
 
+  const Phys<R> K = make_phys<R>(P);
   const R a0 = R(cf.a0), inv2l = R(1.0 / (2.0 * cf.lam)), hdt = R(0.5 * cf.dt);
   const R al0 = R(cf.alpha[0]), al1 = R(cf.alpha[1]);
   const R akk[5] = {R(cf.a0), R(cf.aj[0]), R(cf.aj[1]), R(cf.aj[0]), R(cf.aj[1])};
-  const R dxr = R(P.dx);
   const bool fixed_omega = P.omega_mode == 1;
   const R om_fixed = R(P.omega_fixed);
-  const uint32_t row_bytes = (uint32_t)(QM * FT * sizeof(R));
+  const uint32_t row_bytes = (uint32_t)(QM * NC * sizeof(R));
+  const int sc0 = t * CPT;                              // first own column
+  const int scl = sc0 > 0 ? sc0 - 1 : 0;                // left neighbour column (clamped)
+  const int scr = sc0 + CPT < NC ? sc0 + CPT : NC - 1;  // right neighbour column (clamped)
+  const int tl = t > 0 ? t - 1 : 0, tr = t < FT - 1 ? t + 1 : FT - 1;
 
-  double sp0 = 0.0, sp1 = 0.0, usum[M];
+  R sp0 = R(0), sp1 = R(0);
+  Acc<R> acc[M];
 #pragma unroll
-  for (int c = 0; c < M; c++) usum[c] = 0.0;
+  for (int c = 0; c < M; c++) acc[c].init();
   unsigned st = 0u;
 
+  // band-major work order: (band of `band` rows, strip, row); CTA b takes the
+  // b-th of gridDim equal chunks, so neighbouring strips of a band run side by
+  // side and every CTA has the same number of rows
   const long long total = (long long)strips * P.ny;
   const long long wb = total * blockIdx.x / gridDim.x, we = total * (blockIdx.x + 1) / gridDim.x;
-  unsigned seq = 0;
+  const int nbands = (P.ny + band - 1) / band;
+  const int last_rows = P.ny - (nbands - 1) * band;
+  unsigned seq = 0;        // row loads of this CTA so far (ring slot / phase)
+  unsigned issued_end = 0; // one past the last row load issued (thread 0)
+  unsigned cur = 0;
   bool aborted = false;
 
   for (long long w = wb; w < we && !aborted;) {
-    const int strip = (int)(w / P.ny);
-    const int yb = (int)(w % P.ny);
-    const int ye = (int)min((long long)P.ny, (long long)yb + (we - w));
+    const int b = (int)(w / ((long long)strips * band));
+    const int rb = b == nbands - 1 ? last_rows : band;
+    const long long local = w - (long long)b * strips * band;
+    const int strip = (int)(local / rb);
+    const int yb = b * band + (int)(local % rb);
+    const int ye = (int)min((long long)(b * band + rb), (long long)yb + (we - w));
     w += ye - yb;
-    const int x0 = strip * FW;
-    const int gx = x0 - 4 + t;
-    const bool col_in = gx >= 0 && gx < P.nx;
-    const int mx = map_index(gx, P.nx, P.bc[0], P.bc[1]);
-    const bool out_col = t >= 4 && t < FT - 4 && gx < P.nx;
-    const double xpos = P.x0 + (mx + 0.5) * P.dx;
+    const int x0 = strip * WOUT;
+    int gx[CPT];
+    bool outc[CPT];
+    R xr_ghost[CPT], xr_out[CPT];
+    unsigned pad_mask[CPT];
+#pragma unroll
+    for (int j = 0; j < CPT; j++) {
+      const int sc = sc0 + j;
+      gx[j] = x0 - 4 + sc;
+      outc[j] = sc >= 4 && sc < NC - 4 && gx[j] < P.nx;
+      const int mx = map_index(gx[j], P.nx, P.bc[0], P.bc[1]);
+      xr_ghost[j] = K.xb + R(mx) * K.dx;  // a ghost node sits where the node it copies sits
+      xr_out[j] = K.xb + R(gx[j]) * K.dx;
+      pad_mask[j] = 0u;  // ghost columns this node feeds (only near the x boundaries)
+      if (outc[j] && (gx[j] < NGHOST || gx[j] >= P.nx - NGHOST))
+#pragma unroll
+        for (int p = 0; p < 2 * NGHOST; p++) {
+          int x = p < NGHOST ? p - NGHOST : P.nx + (p - NGHOST);
+          if (map_index(x, P.nx, P.bc[0], P.bc[1]) == gx[j]) pad_mask[j] |= 1u << p;
+        }
+    }
     const int r0 = yb - 3, r1 = ye + 2;
     const unsigned seq0 = seq;
     seq += (unsigned)(r1 - r0 + 1);
-
-    unsigned issued_end = seq0;  // one past the last row copy issued (thread 0)
     if (t == 0) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       for (int i = 0; i < PREF && r0 + i <= r1; i++) {
         unsigned s = seq0 + i;
         int my = map_index(r0 + i, P.ny, P.bc[2], P.bc[3]);
-        tma_load_row(tm, smem_u32(fring + (size_t)(s % S) * QM * FT), smem_u32(&bars[s % S]), x0 - 4, my, row_bytes);
+        tma_load_row(tml, smem_u32(fring + (size_t)(s % S) * QM * NC), smem_u32(&bars[s % S]), x0 - 4 + XPAD, my, row_bytes);
         issued_end = s + 1;
       }
     }
-    unsigned cur = seq0;
 
-    R U1[M], U2[M], p0[M], p2a[M], p2b[M];
+    // register pipelines per own column: U and primitives of rows r-1, r-2; nu
+    // of rows r-1..r-3; post_0, post_1, post_3 of row r-3; post_2 of rows r-4, r-3
+    R U1[CPT][M], U2[CPT][M], p0[CPT][M], p1o[CPT][M], p3o[CPT][M], p2a[CPT][M], p2b[CPT][M];
+    Prim<R> w1[CPT], w2[CPT];
+    R nu1[CPT], nu2[CPT], nu3[CPT];
 #pragma unroll
-    for (int c = 0; c < M; c++) U1[c] = U2[c] = p0[c] = p2a[c] = p2b[c] = R(0);
-    R nu1 = R(0), nu2 = R(0), nu3 = R(0);
+    for (int j = 0; j < CPT; j++) {
+#pragma unroll
+      for (int c = 0; c < M; c++) {
+        U1[j][c] = U2[j][c] = R(1);
+        p0[j][c] = p1o[j][c] = p3o[j][c] = p2a[j][c] = p2b[j][c] = R(0);
+      }
+      w1[j] = primitives<SYS, 2, R>(K, U1[j]);
+      w2[j] = w1[j];
+      nu1[j] = nu2[j] = nu3[j] = R(0);
+    }
 
+#pragma unroll 2
     for (int r = r0; r <= r1; r++) {
       const unsigned sidx = seq0 + (unsigned)(r - r0);
       cur = sidx;
       if (t == 0 && r + PREF <= r1) {
         unsigned s = sidx + PREF;
         int my = map_index(r + PREF, P.ny, P.bc[2], P.bc[3]);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tma_load_row(tm, smem_u32(fring + (size_t)(s % S) * QM * FT), smem_u32(&bars[s % S]), x0 - 4, my, row_bytes);
+        tma_load_row(tml, smem_u32(fring + (size_t)(s % S) * QM * NC), smem_u32(&bars[s % S]), x0 - 4 + XPAD, my, row_bytes);
         issued_end = s + 1;
       }
       if (!mbar_wait_bounded(smem_u32(&bars[sidx % S]), (sidx / S) & 1u)) s_abort = 1;
-      R* frow = fring + (size_t)(sidx % S) * QM * FT;
-      const int myr = map_index(r, P.ny, P.bc[2], P.bc[3]);
-      if (!col_in) {  // ghost column: copy of the wrapped / clamped node
-        const R* src = fin + (long long)myr * P.pitch + mx;
-#pragma unroll
-        for (int q = 0; q < QM; q++) frow[q * FT + t] = src[(long long)q * P.plane];
-      }
+      const R* frow = fring + (size_t)(sidx % S) * QM * NC;
       // B: moments of row r
-      R Ur[M];
+      R Ur[CPT][M];
 #pragma unroll
       for (int c = 0; c < M; c++) {
-        R s = R(0);
 #pragma unroll
-        for (int k = 0; k < Q; k++) s += frow[(k * M + c) * FT + t];
-        Ur[c] = s;
-        Usm[((r & 1) * M + c) * FT + t] = s;
-      }
-      // C: indicator of row r-1
-      R nun = R(0);
-      if (t >= 1 && t < FT - 1) {
-        const R* Uprev = Usm + ((r - 1) & 1) * M * FT;
-        R dm[M], dp[M];
-        Prim<R> w1 = primitives<SYS, 2, R>(P, U1);
+        for (int j = 0; j < CPT; j++) Ur[j][c] = R(0);
 #pragma unroll
-        for (int c = 0; c < M; c++) {
-          dm[c] = U1[c] - Uprev[c * FT + t - 1];
-          dp[c] = Uprev[c * FT + t + 1] - U1[c];
+        for (int k = 0; k < Q; k++) {
+          if constexpr (CPT == 2) {
+            auto v = *reinterpret_cast<const typename Vec2<R>::T*>(frow + (k * M + c) * NC + sc0);
+            Ur[0][c] += v.x;
+            Ur[1][c] += v.y;
+          } else {
+            Ur[0][c] += frow[(k * M + c) * NC + sc0];
+          }
         }
-        nun = theta_sum<SYS, 2, R>(P, w1, 0, dm, dp, dxr);
 #pragma unroll
-        for (int c = 0; c < M; c++) {
-          dm[c] = U1[c] - U2[c];
-          dp[c] = Ur[c] - U1[c];
-        }
-        nun += theta_sum<SYS, 2, R>(P, w1, 1, dm, dp, dxr);
+        for (int j = 0; j < CPT; j++) Usm[((r & 1) * M + c) * NC + sc0 + j] = Ur[j][c];
       }
-      nu3 = nu2;
-      nu2 = nu1;
-      nu1 = nun;
-      colsm[t] = nu1 + nu2 + nu3;
+      // C: indicator of row r-1 (edge lanes use clamped neighbours; no valid
+      // output depends on them)
+      R colsum[CPT];
+      {
+        const R* Uprev = Usm + ((r - 1) & 1) * M * NC;
+#pragma unroll
+        for (int j = 0; j < CPT; j++) {
+          R dm[M], dp[M];
+#pragma unroll
+          for (int c = 0; c < M; c++) {
+            R left = j > 0 ? U1[j > 0 ? j - 1 : 0][c] : Uprev[c * NC + scl];
+            R right = j < CPT - 1 ? U1[j < CPT - 1 ? j + 1 : 0][c] : Uprev[c * NC + scr];
+            dm[c] = U1[j][c] - left;
+            dp[c] = right - U1[j][c];
+          }
+          R nun = theta_sum<SYS, 2, R>(K, w1[j], 0, dm, dp);
+#pragma unroll
+          for (int c = 0; c < M; c++) {
+            dm[c] = U1[j][c] - U2[j][c];
+            dp[c] = Ur[j][c] - U1[j][c];
+          }
+          nun += theta_sum<SYS, 2, R>(K, w1[j], 1, dm, dp);
+          nu3[j] = nu2[j];
+          nu2[j] = nu1[j];
+          nu1[j] = nun;
+          colsum[j] = nu1[j] + nu2[j] + nu3[j];
+          colsm[sc0 + j] = colsum[j];
+        }
+      }
+      // the staging row is free once the previous row's store has read it
+      if (t == 0) tma_store_wait_read();
       __syncthreads();
       if (s_abort) {
         aborted = true;
         break;
       }
-      // D: omega and post-collision values of row r-2
-      R om = om_fixed;
-      if (!fixed_omega && t >= 1 && t < FT - 1) om = R(1) + fdiv(R(1), R(1) + (colsm[t - 1] + colsm[t] + colsm[t + 1]));
-      const R* f2 = fring + (size_t)(((sidx % S) + S - 2) % S) * QM * FT;
-      R post[Q][M];
-      {
-        Prim<R> w2 = primitives<SYS, 2, R>(P, U2);
+      // D: omega and post-collision values of row r-2 (state U2, primitives w2)
+      const R* f2 = fring + (size_t)(((sidx % S) + S - 2) % S) * QM * NC;
+      R post[CPT][Q][M];
+#pragma unroll
+      for (int j = 0; j < CPT; j++) {
+        R cl = j > 0 ? colsum[j > 0 ? j - 1 : 0] : colsm[scl];
+        R cr = j < CPT - 1 ? colsum[j < CPT - 1 ? j + 1 : 0] : colsm[scr];
+        R om = fixed_omega ? om_fixed : R(1) + fdiv(R(1), R(1) + (cl + colsum[j] + cr));
         R Fx[M], Fy[M], Sr[M];
-        flux<SYS, 2, R>(P, U2, w2, 0, Fx);
-        flux<SYS, 2, R>(P, U2, w2, 1, Fy);
-        const int my2 = map_index(r - 2, P.ny, P.bc[2], P.bc[3]);
-        source<SYS, 2, R>(P, U2, xpos, P.y0 + (my2 + 0.5) * P.dx, Sr);
+        flux<SYS, 2, R>(K, U2[j], w2[j], 0, Fx);
+        flux<SYS, 2, R>(K, U2[j], w2[j], 1, Fy);
+        if constexpr (SRC) {
+          const int my2 = map_index(r - 2, P.ny, P.bc[2], P.bc[3]);
+          source<SYS, 2, R>(K, U2[j], xr_ghost[j], K.yb + R(my2) * K.dx, Sr);
+        }
 #pragma unroll
         for (int c = 0; c < M; c++) {
           R feq[Q];
-          feq[0] = a0 * U2[c];
-          feq[1] = (al0 * U2[c] + Fx[c]) * inv2l;
-          feq[2] = (al1 * U2[c] + Fy[c]) * inv2l;
-          feq[3] = (al0 * U2[c] - Fx[c]) * inv2l;
-          feq[4] = (al1 * U2[c] - Fy[c]) * inv2l;
+          feq[0] = a0 * U2[j][c];
+          feq[1] = (al0 * U2[j][c] + Fx[c]) * inv2l;
+          feq[2] = (al1 * U2[j][c] + Fy[c]) * inv2l;
+          feq[3] = (al0 * U2[j][c] - Fx[c]) * inv2l;
+          feq[4] = (al1 * U2[j][c] - Fy[c]) * inv2l;
 #pragma unroll
           for (int k = 0; k < Q; k++) {
-            R fk = f2[(k * M + c) * FT + t];
-            post[k][c] = fk - om * (fk - feq[k]) + hdt * akk[k] * Sr[c];
+            R fk = f2[(k * M + c) * NC + sc0 + j];
+            R pk = fk - om * (fk - feq[k]);
+            if constexpr (SRC) pk += hdt * akk[k] * Sr[c];
+            post[j][k][c] = pk;
           }
         }
       }
+      // neighbours need post_1 of the last own column and post_3 of the first
       R* p13w = p13 + (((r - 2) & 1) * 2) * M * FT;
 #pragma unroll
       for (int c = 0; c < M; c++) {
-        p13w[c * FT + t] = post[1][c];
-        p13w[(M + c) * FT + t] = post[3][c];
+        p13w[c * FT + t] = post[CPT - 1][1][c];
+        p13w[(M + c) * FT + t] = post[0][3][c];
       }
-      // E: row r-3
+      // E: pull streaming into row r-3, implicit moment, second half-source
       const int y = r - 3;
-      if (out_col && y >= yb && y < ye) {
-        const R* p13r = p13 + (((r - 3) & 1) * 2) * M * FT;
-        R Fk[Q][M], Ubar[M], Un[M], Sn[M];
+      const bool row_out = y >= yb && y < ye;
+      const R* p13r = p13 + (((r - 3) & 1) * 2) * M * FT;
+#pragma unroll
+      for (int j = 0; j < CPT; j++) {
+        R Fk[Q][M], Ubar[M];
 #pragma unroll
         for (int c = 0; c < M; c++) {
-          Fk[0][c] = p0[c];
-          Fk[1][c] = p13r[c * FT + t - 1];
-          Fk[2][c] = p2a[c];
-          Fk[3][c] = p13r[(M + c) * FT + t + 1];
-          Fk[4][c] = post[4][c];
+          Fk[0][c] = p0[j][c];
+          Fk[1][c] = j > 0 ? p1o[j > 0 ? j - 1 : 0][c] : p13r[c * FT + tl];
+          Fk[2][c] = p2a[j][c];
+          Fk[3][c] = j < CPT - 1 ? p3o[j < CPT - 1 ? j + 1 : 0][c] : p13r[(M + c) * FT + tr];
+          Fk[4][c] = post[j][4][c];
           R s = R(0);
 #pragma unroll
           for (int k = 0; k < Q; k++) s += Fk[k][c];
           Ubar[c] = s;
         }
-        const double ypos = P.y0 + (y + 0.5) * P.dx, xo = P.x0 + (gx + 0.5) * P.dx;
-        st |= implicit_moment<SYS, 2, R>(P, Ubar, xo, ypos, cf.dt, Un);
-        source<SYS, 2, R>(P, Un, xo, ypos, Sn);
-        R Us[M];
-        const long long off = (long long)y * P.pitch + gx;
+        R Us[M];  // moments of the stored f^{n+1}, summed k = 0..Q-1 as the next step does
+        if constexpr (SRC) {
+          R Un[M], Sn[M];
+          const R yr = K.yb + R(y) * K.dx;
+          unsigned stn = implicit_moment<SYS, 2, R>(K, Ubar, xr_out[j], yr, cf.dt, hdt, Un);
+          source<SYS, 2, R>(K, Un, xr_out[j], yr, Sn);
 #pragma unroll
-        for (int c = 0; c < M; c++) Us[c] = R(0);
+          for (int c = 0; c < M; c++) Us[c] = R(0);
 #pragma unroll
-        for (int k = 0; k < Q; k++)
+          for (int k = 0; k < Q; k++)
 #pragma unroll
-          for (int c = 0; c < M; c++) {
-            R v = Fk[k][c] + hdt * akk[k] * Sn[c];
-            fout[(long long)(k * M + c) * P.plane + off] = v;
-            Us[c] += v;
+            for (int c = 0; c < M; c++) {
+              Fk[k][c] += hdt * akk[k] * Sn[c];
+              Us[c] += Fk[k][c];
+            }
+          if (outc[j] && row_out) st |= stn;
+        } else {
+#pragma unroll
+          for (int c = 0; c < M; c++) Us[c] = Ubar[c];
+        }
+        Prim<R> wn = primitives<SYS, 2, R>(K, Us);
+        const int so = sc0 + j - 4;  // column in the staged output row
+        if (so >= 0 && so < WOUT) {
+#pragma unroll
+          for (int k = 0; k < Q; k++)
+#pragma unroll
+            for (int c = 0; c < M; c++) stage[(k * M + c) * WOUT + so] = Fk[k][c];
+        }
+        if (outc[j] && row_out) {
+          if (gx[j] >= nxs) {  // tail columns outside the bulk store
+            R* base = fout + (long long)y * P.pitch + XPAD + gx[j];
+#pragma unroll
+            for (int k = 0; k < Q; k++)
+#pragma unroll
+              for (int c = 0; c < M; c++) base[(long long)(k * M + c) * P.plane] = Fk[k][c];
           }
-        Prim<R> wn = primitives<SYS, 2, R>(P, Us);
-        sp0 = fmax(sp0, (double)max_speed<SYS, 2, R>(P, wn, 0));
-        sp1 = fmax(sp1, (double)max_speed<SYS, 2, R>(P, wn, 1));
+          if (pad_mask[j]) {
+            R* base = fout + (long long)y * P.pitch + XPAD;
 #pragma unroll
-        for (int c = 0; c < M; c++) usum[c] += (double)Us[c];
-        st |= state_status<SYS, 2, R>(P, Us);
+            for (int p = 0; p < 2 * NGHOST; p++)
+              if (pad_mask[j] & (1u << p)) {
+                int x = p < NGHOST ? p - NGHOST : P.nx + (p - NGHOST);
+#pragma unroll
+                for (int k = 0; k < Q; k++)
+#pragma unroll
+                  for (int c = 0; c < M; c++) base[(long long)(k * M + c) * P.plane + x] = Fk[k][c];
+              }
+          }
+          sp0 = rmax(sp0, max_speed<SYS, 2, R>(K, wn, 0));
+          sp1 = rmax(sp1, max_speed<SYS, 2, R>(K, wn, 1));
+#pragma unroll
+          for (int c = 0; c < M; c++) acc[c].add(Us[c]);
+          st |= state_status<SYS, 2, R>(Us, wn);
+        }
       }
+      fence_proxy_async();  // staged row visible to the TMA store
 #pragma unroll
-      for (int c = 0; c < M; c++) {
-        p0[c] = post[0][c];
-        p2a[c] = p2b[c];
-        p2b[c] = post[2][c];
-        U2[c] = U1[c];
-        U1[c] = Ur[c];
+      for (int j = 0; j < CPT; j++) {
+        w2[j] = w1[j];
+#pragma unroll
+        for (int c = 0; c < M; c++) {
+          p0[j][c] = post[j][0][c];
+          p1o[j][c] = post[j][1][c];
+          p3o[j][c] = post[j][3][c];
+          p2a[j][c] = p2b[j][c];
+          p2b[j][c] = post[j][2][c];
+          U2[j][c] = U1[j][c];
+          U1[j][c] = Ur[j][c];
+        }
+        w1[j] = primitives<SYS, 2, R>(K, U1[j]);
       }
       __syncthreads();
-    }
-    if (aborted) {
-      // let every row copy this CTA issued land before the CTA exits
-      if (t == 0)
-        for (unsigned s = cur; s < issued_end; s++) mbar_wait_bounded(smem_u32(&bars[s % S]), (s / S) & 1u);
-      st |= ST_TIMEOUT;
-      __syncthreads();
+      if (t == 0 && row_out && x0 < nxs) tma_store_row(tms, smem_u32(stage), x0, y);
     }
   }
-  block_side_outputs<M>(sp0, sp1, usum, ctl, (slot + 1) % 3, partials, st);
+  if (t == 0) {
+    if (aborted)  // let every row copy this CTA issued land before it exits
+      for (unsigned s = cur; s < issued_end; s++) mbar_wait_bounded(smem_u32(&bars[s % S]), (s / S) & 1u);
+    tma_store_wait_all();
+  }
+  if (aborted) st |= ST_TIMEOUT;
+  __syncthreads();
+  fused_side_outputs<M, R>(sp0, sp1, acc, ctl, (slot + 1) % 3, partials, st);
   if (blockIdx.x == 0 && t == 0) advance_ctl<2>(ctl, slot, cf);
 }
 
@@ -326,6 +475,7 @@ __global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensor
 template <int SYS, class R>
 __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl* ctl, int slot, double* partials) {
   constexpr int M = Fields<SYS, 1>::M, Q = 3;
+  constexpr bool SRC = HasSource<SYS>::value;
   __shared__ R Us[M][FT];
   __shared__ R nus[FT];
   __shared__ R p1s[M][FT], p2s[M][FT];
@@ -335,6 +485,7 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
     if (blockIdx.x == 0 && t == 0) advance_ctl<1>(ctl, slot, cf);
     return;
   }
+  const Phys<R> K = make_phys<R>(P);
   const int par = ctl->parity[slot];
   const R* fin = buf[par];
   R* fout = buf[par ^ 1];
@@ -346,14 +497,14 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
     R s = R(0);
 #pragma unroll
     for (int k = 0; k < Q; k++) {
-      f[k][c] = fin[(long long)(k * M + c) * P.plane + mx];
+      f[k][c] = fin[(long long)(k * M + c) * P.plane + mx + XPAD];
       s += f[k][c];
     }
     U[c] = s;
     Us[c][t] = s;
   }
   __syncthreads();
-  Prim<R> w = primitives<SYS, 1, R>(P, U);
+  Prim<R> w = primitives<SYS, 1, R>(K, U);
   R nu = R(0);
   if (t >= 1 && t < FT - 1) {
     R dm[M], dp[M];
@@ -362,7 +513,7 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
       dm[c] = U[c] - Us[c][t - 1];
       dp[c] = Us[c][t + 1] - U[c];
     }
-    nu = theta_sum<SYS, 1, R>(P, w, 0, dm, dp, R(P.dx));
+    nu = theta_sum<SYS, 1, R>(K, w, 0, dm, dp);
   }
   nus[t] = nu;
   __syncthreads();
@@ -371,19 +522,26 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
   const R a0 = R(cf.a0), a1 = R(cf.aj[0]), inv2l = R(1.0 / (2.0 * cf.lam)), hdt = R(0.5 * cf.dt);
   const R al0 = R(cf.alpha[0]);
   R F[M], S[M], post0[M];
-  flux<SYS, 1, R>(P, U, w, 0, F);
-  source<SYS, 1, R>(P, U, P.x0 + (mx + 0.5) * P.dx, 0.0, S);
+  flux<SYS, 1, R>(K, U, w, 0, F);
+  if constexpr (SRC) source<SYS, 1, R>(K, U, K.xb + R(mx) * K.dx, R(0), S);
 #pragma unroll
   for (int c = 0; c < M; c++) {
     R feq0 = a0 * U[c], feq1 = (al0 * U[c] + F[c]) * inv2l, feq2 = (al0 * U[c] - F[c]) * inv2l;
-    post0[c] = f[0][c] - om * (f[0][c] - feq0) + hdt * a0 * S[c];
-    p1s[c][t] = f[1][c] - om * (f[1][c] - feq1) + hdt * a1 * S[c];
-    p2s[c][t] = f[2][c] - om * (f[2][c] - feq2) + hdt * a1 * S[c];
+    post0[c] = f[0][c] - om * (f[0][c] - feq0);
+    R q1 = f[1][c] - om * (f[1][c] - feq1), q2 = f[2][c] - om * (f[2][c] - feq2);
+    if constexpr (SRC) {
+      post0[c] += hdt * a0 * S[c];
+      q1 += hdt * a1 * S[c];
+      q2 += hdt * a1 * S[c];
+    }
+    p1s[c][t] = q1;
+    p2s[c][t] = q2;
   }
   __syncthreads();
-  double sp0 = 0.0, usum[M];
+  R sp0 = R(0);
+  Acc<R> acc[M];
 #pragma unroll
-  for (int c = 0; c < M; c++) usum[c] = 0.0;
+  for (int c = 0; c < M; c++) acc[c].init();
   unsigned st = 0u;
   if (t >= 4 && t < FT - 4 && gx < P.nx) {
     R Fk[Q][M], Ubar[M], Un[M], Sn[M], Uo[M];
@@ -394,9 +552,11 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
       Fk[2][c] = p2s[c][t + 1];
       Ubar[c] = Fk[0][c] + Fk[1][c] + Fk[2][c];
     }
-    const double xo = P.x0 + (gx + 0.5) * P.dx;
-    st |= implicit_moment<SYS, 1, R>(P, Ubar, xo, 0.0, cf.dt, Un);
-    source<SYS, 1, R>(P, Un, xo, 0.0, Sn);
+    const R xo = K.xb + R(gx) * K.dx;
+    if constexpr (SRC) {
+      st |= implicit_moment<SYS, 1, R>(K, Ubar, xo, R(0), cf.dt, hdt, Un);
+      source<SYS, 1, R>(K, Un, xo, R(0), Sn);
+    }
     const R ak[3] = {a0, a1, a1};
 #pragma unroll
     for (int c = 0; c < M; c++) Uo[c] = R(0);
@@ -404,17 +564,18 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
     for (int k = 0; k < Q; k++)
 #pragma unroll
       for (int c = 0; c < M; c++) {
-        R v = Fk[k][c] + hdt * ak[k] * Sn[c];
-        fout[(long long)(k * M + c) * P.plane + gx] = v;
+        R v = Fk[k][c];
+        if constexpr (SRC) v += hdt * ak[k] * Sn[c];
+        fout[(long long)(k * M + c) * P.plane + gx + XPAD] = v;
         Uo[c] += v;
       }
-    Prim<R> wn = primitives<SYS, 1, R>(P, Uo);
-    sp0 = (double)max_speed<SYS, 1, R>(P, wn, 0);
+    Prim<R> wn = primitives<SYS, 1, R>(K, Uo);
+    sp0 = max_speed<SYS, 1, R>(K, wn, 0);
 #pragma unroll
-    for (int c = 0; c < M; c++) usum[c] = (double)Uo[c];
-    st |= state_status<SYS, 1, R>(P, Uo);
+    for (int c = 0; c < M; c++) acc[c].add(Uo[c]);
+    st |= state_status<SYS, 1, R>(Uo, wn);
   }
-  block_side_outputs<M>(sp0, 0.0, usum, ctl, (slot + 1) % 3, partials, st);
+  fused_side_outputs<M, R>(sp0, R(0), acc, ctl, (slot + 1) % 3, partials, st);
   if (blockIdx.x == 0 && t == 0) advance_ctl<1>(ctl, slot, cf);
 }
 
@@ -438,57 +599,85 @@ inline EncodeTiledFn encode_fn() {
   return fn;
 }
 
-template <int SYS, class R>
-inline size_t fused2d_smem() {
-  return Smem2D<Fields<SYS, 2>::M, R, FPREF>::total;
-}
-
-template <int SYS, int D, class R>
-inline int fused_setup(FusedPlan& fp, const DevParams& P, void* const* fbuf) {
-  constexpr int M = Fields<SYS, D>::M, QM = Fields<SYS, D>::Q * M;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (D == 1) {
-    fp.strips = 1;
-    fp.smem = 0;
-    fp.blocks = (P.nx + FW - 1) / FW;
-    return 0;
-  }
-  fp.strips = (P.nx + FW - 1) / FW;
-  size_t smem = fused2d_smem<SYS, R>();
-  fp.smem = (int)smem;
-  auto kern = k_fused2d<SYS, R, FPREF>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+template <int SYS, class R, int CPT>
+inline int fused2d_prepare(FusedPlan& fp, const DevParams& P, void* const* fbuf, int sms) {
+  constexpr int M = Fields<SYS, 2>::M, QM = 5 * M;
+  using L = Smem2D<M, R, fpref<CPT>(), CPT>;
+  fp.cpt = CPT;
+  fp.strips = (P.nx + L::WOUT - 1) / L::WOUT;
+  fp.nxs = P.nx - P.nx % (int)(16 / sizeof(R));
+  fp.smem = (int)L::total;
+  auto kern = k_fused2d<SYS, R, fpref<CPT>(), CPT>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, fp.smem) != cudaSuccess) return -1;
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FT, smem) != cudaSuccess || per_sm < 1) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FT, fp.smem) != cudaSuccess || per_sm < 1) return -1;
+  // one resident wave; every CTA gets the same number of (strip, row) units,
+  // at least 16 rows each
+  long long slots = (long long)per_sm * sms;
   long long total = (long long)fp.strips * P.ny;
-  long long want = (long long)per_sm * sms;
-  long long cap = (total + 7) / 8;  // at least ~8 rows per CTA
-  fp.blocks = (int)(want < cap ? want : (cap < 1 ? 1 : cap));
+  long long cap = total / 16 > 0 ? total / 16 : 1;
+  fp.blocks = (int)(slots < cap ? slots : cap);
+  long long chunk = (total + fp.blocks - 1) / fp.blocks;
+  fp.band = (int)(chunk < 16 ? 16 : (chunk > P.ny ? P.ny : chunk));
   EncodeTiledFn enc = encode_fn();
   if (!enc) return -1;
   for (int b = 0; b < 2; b++) {
-    cuuint64_t dims[3] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, (cuuint64_t)QM};
     cuuint64_t strides[2] = {(cuuint64_t)P.pitch * sizeof(R), (cuuint64_t)P.plane * sizeof(R)};
-    cuuint32_t box[3] = {(cuuint32_t)FT, 1u, (cuuint32_t)QM};
     cuuint32_t estr[3] = {1u, 1u, 1u};
-    CUresult r = enc(&fp.tm[b], sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
-                     fbuf[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const CUtensorMapDataType dt = sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    cuuint64_t ldims[3] = {(cuuint64_t)(P.nx + 2 * XPAD), (cuuint64_t)P.ny, (cuuint64_t)QM};
+    cuuint32_t lbox[3] = {(cuuint32_t)L::NC, 1u, (cuuint32_t)QM};
+    CUresult r = enc(&fp.tm[b], dt, 3, fbuf[b], ldims, strides, lbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return -1;
+    cuuint64_t sdims[3] = {(cuuint64_t)(fp.nxs > 0 ? fp.nxs : 1), (cuuint64_t)P.ny, (cuuint64_t)QM};
+    cuuint32_t sbox[3] = {(cuuint32_t)L::WOUT, 1u, (cuuint32_t)QM};
+    r = enc(&fp.tms[b], dt, 3, (R*)fbuf[b] + XPAD, sdims, strides, sbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return -1;
   }
   return 0;
 }
 
+// Columns per thread of the 2D kernel: 1 (measured faster than 2 on B300:
+// two columns per thread need 255 registers and a one-row prefetch to fit two
+// CTAs per SM).  LBMH_FUSED_CPT=1|2 overrides it for tuning runs.
+template <class R>
+inline int default_cpt() {
+  const char* e = getenv("LBMH_FUSED_CPT");
+  if (e && (e[0] == '1' || e[0] == '2') && e[1] == 0) return e[0] - '0';
+  return 1;
+}
+
+template <int SYS, int D, class R>
+inline int fused_setup(FusedPlan& fp, const DevParams& P, void* const* fbuf) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (D == 1) {
+    fp.cpt = 1;
+    fp.strips = 1;
+    fp.smem = 0;
+    fp.blocks = (P.nx + FW - 1) / FW;
+    return 0;
+  }
+  return default_cpt<R>() == 2 ? fused2d_prepare<SYS, R, 2>(fp, P, fbuf, sms)
+                                : fused2d_prepare<SYS, R, 1>(fp, P, fbuf, sms);
+}
+
 template <int SYS, int D, class R>
 inline int fused_launch(const FusedPlan& fp, const DevParams& P, R* const* buf, Ctl* ctl, int slot, double* partials,
                         cudaStream_t stream) {
-  if (D == 1) {
+  if constexpr (D == 1) {
     k_fused1d<SYS, R><<<fp.blocks, FT, 0, stream>>>(P, buf, ctl, slot, partials);
   } else {
-    k_fused2d<SYS, R, FPREF><<<fp.blocks, FT, fp.smem, stream>>>(fp.tm[0], fp.tm[1], P, buf, ctl, slot, partials,
-                                                                 fp.strips);
+    if (fp.cpt == 2)
+      k_fused2d<SYS, R, fpref<2>(), 2><<<fp.blocks, FT, fp.smem, stream>>>(fp.tm[0], fp.tm[1], fp.tms[0], fp.tms[1], P,
+                                                                            buf, ctl, slot, partials, fp.strips, fp.nxs, fp.band);
+    else
+      k_fused2d<SYS, R, fpref<1>(), 1><<<fp.blocks, FT, fp.smem, stream>>>(fp.tm[0], fp.tm[1], fp.tms[0], fp.tms[1], P,
+                                                                            buf, ctl, slot, partials, fp.strips, fp.nxs, fp.band);
   }
   return fp.blocks;
 }

@@ -42,7 +42,8 @@ struct lbmh_handle {
   int nblocks;              // blocks writing partials in the last step
   int max_blocks;
   Ctl* ctl;
-  double* Utmp;             // FP64 staging [m][ny][nx] or [Q][m][ny][nx]
+  double* Utmp;             // FP64 staging, allocated on first use
+  size_t utmp_bytes;
   long long launched;       // step launches since set_state
   bool has_state;
   long long device_bytes;
@@ -92,12 +93,13 @@ __global__ void k_init_speed(DevParams P, const double* U0, Ctl* ctl) {
   long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   double s0 = 0.0, s1 = 0.0;
   if (node < nn) {
+    const Phys<double> K = make_phys<double>(P);
     double U[M];
 #pragma unroll
     for (int c = 0; c < M; c++) U[c] = U0[c * nn + node];
-    Prim<double> w = primitives<SYS, D, double>(P, U);
-    s0 = max_speed<SYS, D, double>(P, w, 0);
-    if (D == 2) s1 = max_speed<SYS, D, double>(P, w, 1);
+    Prim<double> w = primitives<SYS, D, double>(K, U);
+    s0 = max_speed<SYS, D, double>(K, w, 0);
+    if (D == 2) s1 = max_speed<SYS, D, double>(K, w, 1);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -132,8 +134,9 @@ __global__ void k_init_eq(DevParams P, const double* U0, R* f, Ctl* ctl) {
       U[c] = R(U0[c * nn + node]);
       Us[c] = R(0);
     }
-    Prim<R> w = primitives<SYS, D, R>(P, U);
-    long long off = (long long)j * P.pitch + i;
+    const Phys<R> K = make_phys<R>(P);
+    Prim<R> w = primitives<SYS, D, R>(K, U);
+    long long off = cell(P, i, j);
 #pragma unroll
     for (int k = 0; k < Q; k++) {
       R feq[M];
@@ -143,7 +146,7 @@ __global__ void k_init_eq(DevParams P, const double* U0, R* f, Ctl* ctl) {
       } else {
         int jd = (k - 1) % D;
         R F[M];
-        flux<SYS, D, R>(P, U, w, jd, F);
+        flux<SYS, D, R>(K, U, w, jd, F);
         R sg = k <= D ? R(1) : R(-1);
 #pragma unroll
         for (int c = 0; c < M; c++) feq[c] = (al[jd] * U[c] + sg * F[c]) * inv2l;
@@ -154,9 +157,9 @@ __global__ void k_init_eq(DevParams P, const double* U0, R* f, Ctl* ctl) {
         Us[c] += feq[c];
       }
     }
-    Prim<R> ws = primitives<SYS, D, R>(P, Us);
-    s0 = (double)max_speed<SYS, D, R>(P, ws, 0);
-    if (D == 2) s1 = (double)max_speed<SYS, D, R>(P, ws, 1);
+    Prim<R> ws = primitives<SYS, D, R>(K, Us);
+    s0 = (double)max_speed<SYS, D, R>(K, ws, 0);
+    if (D == 2) s1 = (double)max_speed<SYS, D, R>(K, ws, 1);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -177,7 +180,7 @@ __global__ void k_moments(DevParams P, R* const* buf, const Ctl* ctl, int slot, 
   if (node >= nn) return;
   const R* f = buf[ctl->parity[slot]];
   int j = (int)(node / P.nx), i = (int)(node % P.nx);
-  long long off = (long long)j * P.pitch + i;
+  long long off = cell(P, i, j);
 #pragma unroll
   for (int c = 0; c < M; c++) {
     R s = R(0);
@@ -196,7 +199,7 @@ __global__ void k_get_f(DevParams P, int QM, R* const* buf, const Ctl* ctl, int 
   const R* f = buf[ctl->parity[slot]];
   long long q = idx / nn, node = idx % nn;
   int j = (int)(node / P.nx), i = (int)(node % P.nx);
-  out[idx] = (double)f[q * P.plane + (long long)j * P.pitch + i];
+  out[idx] = (double)f[q * P.plane + cell(P, i, j)];
 }
 
 template <class R>
@@ -206,7 +209,7 @@ __global__ void k_set_f(DevParams P, int QM, R* f, const double* in) {
   if (idx >= nn * QM) return;
   long long q = idx / nn, node = idx % nn;
   int j = (int)(node / P.nx), i = (int)(node % P.nx);
-  f[q * P.plane + (long long)j * P.pitch + i] = R(in[idx]);
+  f[q * P.plane + cell(P, i, j)] = R(in[idx]);
 }
 
 // speed bound of the stored distributions -> slot 0 (after lbmh_set_f)
@@ -219,7 +222,7 @@ __global__ void k_speed_of_f(DevParams P, R* const* buf, Ctl* ctl) {
   if (node < nn) {
     const R* f = buf[ctl->parity[0]];
     int j = (int)(node / P.nx), i = (int)(node % P.nx);
-    long long off = (long long)j * P.pitch + i;
+    long long off = cell(P, i, j);
     R U[M];
 #pragma unroll
     for (int c = 0; c < M; c++) {
@@ -228,9 +231,10 @@ __global__ void k_speed_of_f(DevParams P, R* const* buf, Ctl* ctl) {
       for (int k = 0; k < Q; k++) s += f[(long long)(k * M + c) * P.plane + off];
       U[c] = s;
     }
-    Prim<R> w = primitives<SYS, D, R>(P, U);
-    s0 = (double)max_speed<SYS, D, R>(P, w, 0);
-    if (D == 2) s1 = (double)max_speed<SYS, D, R>(P, w, 1);
+    const Phys<R> K = make_phys<R>(P);
+    Prim<R> w = primitives<SYS, D, R>(K, U);
+    s0 = (double)max_speed<SYS, D, R>(K, w, 0);
+    if (D == 2) s1 = (double)max_speed<SYS, D, R>(K, w, 1);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -241,6 +245,22 @@ __global__ void k_speed_of_f(DevParams P, R* const* buf, Ctl* ctl) {
     atomic_max_nonneg(&ctl->amax[0][0], s0);
     atomic_max_nonneg(&ctl->amax[0][1], s1);
   }
+}
+
+// ghost columns of every row := the wrapped / clamped node (after the
+// distributions were written by something other than a fused 2D step)
+template <class R>
+__global__ void k_fill_pads(DevParams P, int QM, R* f) {
+  long long rows = (long long)P.ny * QM;
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= rows * 2 * NGHOST) return;
+  long long row = idx / (2 * NGHOST);
+  int p = (int)(idx % (2 * NGHOST));
+  int x = p < NGHOST ? p - NGHOST : P.nx + (p - NGHOST);
+  int src = map_index(x, P.nx, P.bc[0], P.bc[1]);
+  long long q = row / P.ny, j = row % P.ny;
+  R* base = f + q * P.plane + j * P.pitch + XPAD;
+  base[x] = base[src];
 }
 
 template <class R>
@@ -273,6 +293,11 @@ struct Ops {
 template <int SYS, int D, class R>
 struct Impl {
   static constexpr int M = Fields<SYS, D>::M, Q = Fields<SYS, D>::Q;
+
+  static void fill_pads(lbmh_handle* h, R* f) {
+    long long n = (long long)h->P.ny * Q * M * 2 * NGHOST;
+    k_fill_pads<R><<<blocks_for(n), kBlock, 0, h->stream>>>(h->P, Q * M, f);
+  }
 
   static int unfused_front(lbmh_handle* h, int slot, const DevParams& P) {
     long long next = (long long)h->G.ex * h->G.ey;
@@ -316,6 +341,7 @@ struct Impl {
     unsigned nb = blocks_for(nn);
     k_init_speed<SYS, D><<<nb, kBlock, 0, h->stream>>>(h->P, U0dev, h->ctl);
     k_init_eq<SYS, D, R><<<nb, kBlock, 0, h->stream>>>(h->P, U0dev, (R*)h->fbuf[0], h->ctl);
+    fill_pads(h, (R*)h->fbuf[0]);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "init launch");
     return LBMH_OK;
@@ -340,6 +366,7 @@ struct Impl {
   static int set_f(lbmh_handle* h, const double* dev) {
     long long n = (long long)h->P.nx * h->P.ny * Q * M;
     k_set_f<R><<<blocks_for(n), kBlock, 0, h->stream>>>(h->P, Q * M, (R*)h->fbuf[0], dev);
+    fill_pads(h, (R*)h->fbuf[0]);
     k_speed_of_f<SYS, D, R><<<blocks_for((long long)h->P.nx * h->P.ny), kBlock, 0, h->stream>>>(
         h->P, (R* const*)h->dbuf, h->ctl);
     cudaError_t e = cudaGetLastError();
@@ -424,6 +451,41 @@ void free_handle(lbmh_handle* h) {
   delete h;
 }
 
+// device staging for host transfers and FP64 conversions, grown on demand
+int ensure_utmp(lbmh_handle* h, size_t bytes) {
+  if (h->utmp_bytes >= bytes) return LBMH_OK;
+  cudaStreamSynchronize(h->stream);
+  cudaFree(h->Utmp);
+  h->device_bytes -= (long long)h->utmp_bytes;
+  h->Utmp = nullptr;
+  h->utmp_bytes = 0;
+  if (cudaMalloc((void**)&h->Utmp, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, LBMH_ERR_OOM, "device allocation of the staging buffer failed");
+  }
+  h->utmp_bytes = bytes;
+  h->device_bytes += (long long)bytes;
+  return LBMH_OK;
+}
+
+// ghost-extended scratch of the unfused path (also used by lbmh_omega)
+int ensure_scratch(lbmh_handle* h) {
+  if (h->Ue) return LBMH_OK;
+  long long next = (long long)h->G.ex * h->G.ey;
+  size_t b1 = (size_t)next * h->m * h->elem, b2 = (size_t)next * h->elem;
+  if (cudaMalloc(&h->Ue, b1) != cudaSuccess || cudaMalloc(&h->nue, b2) != cudaSuccess ||
+      cudaMalloc(&h->ome, b2) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(h->Ue);
+    cudaFree(h->nue);
+    cudaFree(h->ome);
+    h->Ue = h->nue = h->ome = nullptr;
+    return fail(h, LBMH_ERR_OOM, "device allocation of the unfused scratch failed");
+  }
+  h->device_bytes += (long long)(b1 + 2 * b2);
+  return LBMH_OK;
+}
+
 int sync(lbmh_handle* h) {
   CK(h, cudaStreamSynchronize(h->stream));
   return LBMH_OK;
@@ -471,7 +533,7 @@ int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
   P.nx = p->nx;
   P.ny = p->dim == 2 ? p->ny : 1;
   int align = 128 / (int)h->elem;  // rows start on 128-byte boundaries
-  P.pitch = (P.nx + align - 1) / align * align;
+  P.pitch = (P.nx + 2 * XPAD + align - 1) / align * align;
   P.plane = (long long)P.ny * P.pitch;
   h->plane = P.plane;
   for (int s = 0; s < 4; s++) P.bc[s] = p->bc[s];
@@ -508,10 +570,9 @@ int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
   h->G.gy = p->dim == 2 ? GH : 0;
   h->G.ey = p->dim == 2 ? P.ny + 2 * GH : 1;
   long long nn = (long long)P.nx * P.ny;
-  long long next = (long long)h->G.ex * h->G.ey;
   size_t fbytes = (size_t)h->Q * h->m * P.plane * h->elem;
   h->max_blocks = (int)blocks_for(nn);
-  bool need_scratch = true;  // the unfused diagnostics (lbmh_omega) use it too
+  h->utmp_bytes = 0;
   auto alloc = [&](void** ptr, size_t bytes) -> bool {
     if (cudaMalloc(ptr, bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -536,10 +597,8 @@ int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
   }
   ok = ok && alloc((void**)&h->dbuf, 2 * sizeof(void*)) &&
        alloc((void**)&h->partials, (size_t)h->max_blocks * h->m * sizeof(double)) &&
-       alloc((void**)&h->ctl, sizeof(Ctl)) && alloc((void**)&h->Utmp, (size_t)nn * h->m * h->Q * sizeof(double));
-  if (ok && need_scratch)
-    ok = alloc(&h->Ue, (size_t)next * h->m * h->elem) && alloc(&h->nue, (size_t)next * h->elem) &&
-         alloc(&h->ome, (size_t)next * h->elem);
+       alloc((void**)&h->ctl, sizeof(Ctl));
+  if (ok && h->kernel == LBMH_KERNEL_UNFUSED && ensure_scratch(h) != LBMH_OK) ok = false;
   if (!ok) {
     free_handle(h);
     return fail(nullptr, LBMH_ERR_OOM, "device allocation failed");
@@ -571,6 +630,8 @@ int lbmh_set_state(lbmh_handle* h, const double* U, int on_device) {
   size_t bytes = (size_t)nn * h->m * sizeof(double);
   const double* src = U;
   if (!on_device) {
+    int rc0 = ensure_utmp(h, bytes);
+    if (rc0) return rc0;
     CK(h, cudaMemcpyAsync(h->Utmp, U, bytes, cudaMemcpyHostToDevice, h->stream));
     src = h->Utmp;
   }
@@ -636,6 +697,10 @@ int lbmh_moments(lbmh_handle* h, double* U_out, int on_device, double* t, int64_
   long long nn = (long long)h->P.nx * h->P.ny;
   size_t bytes = (size_t)nn * h->m * sizeof(double);
   int slot = current_slot(h);
+  if (!on_device) {
+    int rc0 = ensure_utmp(h, bytes);
+    if (rc0) return rc0;
+  }
   int rc = h->ops->moments(h, slot, on_device ? U_out : h->Utmp);
   if (rc) return rc;
   if (!on_device) CK(h, cudaMemcpyAsync(U_out, h->Utmp, bytes, cudaMemcpyDeviceToHost, h->stream));
@@ -655,6 +720,10 @@ int lbmh_get_f(lbmh_handle* h, double* f_out, int on_device, double* t, int64_t*
   if (!f_out) return fail(h, LBMH_ERR_INVALID_ARG, "f_out is NULL");
   long long n = (long long)h->P.nx * h->P.ny * h->Q * h->m;
   int slot = current_slot(h);
+  if (!on_device) {
+    int rc0 = ensure_utmp(h, (size_t)n * sizeof(double));
+    if (rc0) return rc0;
+  }
   int rc = h->ops->get_f(h, slot, on_device ? f_out : h->Utmp);
   if (rc) return rc;
   if (!on_device) CK(h, cudaMemcpyAsync(f_out, h->Utmp, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -672,6 +741,8 @@ int lbmh_set_f(lbmh_handle* h, const double* f_in, int on_device, double t, int6
   long long n = (long long)h->P.nx * h->P.ny * h->Q * h->m;
   const double* src = f_in;
   if (!on_device) {
+    int rc0 = ensure_utmp(h, (size_t)n * sizeof(double));
+    if (rc0) return rc0;
     CK(h, cudaMemcpyAsync(h->Utmp, f_in, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     src = h->Utmp;
   }
@@ -695,7 +766,13 @@ int lbmh_omega(lbmh_handle* h, double* out, int on_device) {
   if (!out) return fail(h, LBMH_ERR_INVALID_ARG, "out is NULL");
   long long nn = (long long)h->P.nx * h->P.ny;
   int slot = current_slot(h);
-  int rc = h->ops->launch_unfused_diag(h, slot);
+  int rc = ensure_scratch(h);
+  if (rc) return rc;
+  if (!on_device) {
+    rc = ensure_utmp(h, (size_t)nn * sizeof(double));
+    if (rc) return rc;
+  }
+  rc = h->ops->launch_unfused_diag(h, slot);
   if (rc) return rc;
   rc = h->ops->omega_extract(h, on_device ? out : h->Utmp);
   if (rc) return rc;

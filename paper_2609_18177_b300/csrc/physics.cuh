@@ -2,57 +2,114 @@
 // system, the dimension and the arithmetic type R (float or double):
 // flux F_j(U), the speed bound max_r |lambda_r(dF_j/dU)|, the characteristic
 // smoothness indicator, the source S(U) and the implicit moment of Eq. (2.8).
+//
+// All constants arrive pre-converted to R in a Phys<R> block built once per
+// thread, so the FP32 path issues no FP64 instruction per node except in the
+// Arrhenius source and its implicit update (kept in FP64 on purpose).
 #pragma once
 #include "common.cuh"
 
 namespace lbmh {
 
-template <class R> __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
-__device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
-__device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
-__device__ __forceinline__ float rexp_(float x) { return expf(x); }
-__device__ __forceinline__ double rexp_(double x) { return exp(x); }
+__device__ __forceinline__ float rabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double rabs(double x) { return fabs(x); }
+
+// Division, reciprocal and square root: IEEE in FP64; in FP32 the MUFU
+// approximations (<= 2 ulp), which is the precision the FP32 mode runs at.
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float frcp(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ double frcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ float fsqrt(float x) {
+  // x * rsqrt(x) with the argument of rsqrt kept positive: 0 stays 0; a
+  // negative x (a non-physical state, flagged separately) gives a negative c
+  return x * rsqrtf(fmaxf(x, 1e-37f));
+}
+__device__ __forceinline__ double fsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float fexp(float x) { return __expf(x); }
+__device__ __forceinline__ float rmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double rmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ double fexp(double x) { return exp(x); }
+
+// Problem constants in the arithmetic type of the path.
+template <class R>
+struct Phys {
+  R gamma, gm1, g, half_g, h_dry, cmin, q, adv0, adv1, dx;
+  R bed_amp, bed_inv_w2, bed_m2_inv_w2;  // amp, 1/w2, -2/w2
+  R xb, yb;                              // x0 + dx/2 - xc, y0 + dx/2 - yc: node i sits at xb + i dx
+  double gamma_d, q_d, K, Ti;            // Arrhenius, FP64
+  bool bed, react;
+};
+
+template <class R>
+__device__ __forceinline__ Phys<R> make_phys(const DevParams& P) {
+  Phys<R> k;
+  k.gamma = R(P.gamma);
+  k.gm1 = R(P.gamma - 1.0);
+  k.g = R(P.g);
+  k.half_g = R(0.5 * P.g);
+  k.h_dry = R(P.h_dry);
+  k.cmin = R(sqrt(P.g * P.h_dry));
+  k.q = R(P.q);
+  k.adv0 = R(P.adv[0]);
+  k.adv1 = R(P.adv[1]);
+  k.dx = R(P.dx);
+  k.bed_amp = R(P.bed_amp);
+  k.bed_inv_w2 = R(1.0 / P.bed_w2);
+  k.bed_m2_inv_w2 = R(-2.0 / P.bed_w2);
+  k.xb = R(P.x0 + 0.5 * P.dx - P.bed_xc);
+  k.yb = R(P.y0 + 0.5 * P.dx - P.bed_yc);
+  k.gamma_d = P.gamma;
+  k.q_d = P.q;
+  k.K = P.K;
+  k.Ti = P.Ti;
+  k.bed = P.bed_amp != 0.0;
+  k.react = P.K != 0.0;
+  return k;
+}
+
+template <int SYS>
+struct HasSource {
+  static constexpr bool value = SYS == SYS_SWE || SYS == SYS_REACT;
+};
 
 // Primitive variables of an Euler-type or shallow-water state.
 template <class R>
 struct Prim {
   R rho, u, v, p, c, Y;  // Euler / reactive; for shallow water rho holds h
-  bool dry;
 };
 
 template <int SYS, int D, class R>
-__device__ __forceinline__ Prim<R> primitives(const DevParams& P, const R* U) {
+__device__ __forceinline__ Prim<R> primitives(const Phys<R>& K, const R* U) {
   Prim<R> w;
   w.Y = R(0);
-  w.dry = false;
+  w.p = R(0);
   if constexpr (SYS == SYS_EULER || SYS == SYS_REACT) {
     w.rho = U[0];
-    R inv = R(1) / w.rho;
+    R inv = frcp(w.rho);
     w.u = U[1] * inv;
     w.v = D == 2 ? U[2] * inv : R(0);
     R kin = R(0.5) * w.rho * (w.u * w.u + w.v * w.v);
     R chem = R(0);
     if constexpr (SYS == SYS_REACT) {
       w.Y = U[D + 2] * inv;
-      chem = R(P.q) * U[D + 2];
+      chem = K.q * U[D + 2];
     }
-    w.p = R(P.gamma - 1.0) * (U[D + 1] - kin - chem);
-    w.c = rsqrt_(R(P.gamma) * w.p / w.rho);
+    w.p = K.gm1 * (U[D + 1] - kin - chem);
+    w.c = fsqrt(K.gamma * w.p * inv);
   } else if constexpr (SYS == SYS_SWE) {
     w.rho = U[0];
-    w.dry = w.rho < R(P.h_dry);
-    if (w.dry) {
+    if (w.rho < K.h_dry) {  // dry node: at rest
       w.u = R(0);
       w.v = R(0);
     } else {
-      R inv = R(1) / w.rho;
+      R inv = frcp(w.rho);
       w.u = U[1] * inv;
       w.v = D == 2 ? U[2] * inv : R(0);
     }
-    w.c = rsqrt_(R(P.g) * (w.rho > R(0) ? w.rho : R(0)));
-    w.p = R(0);
+    w.c = fsqrt(K.g * (w.rho > R(0) ? w.rho : R(0)));
   } else {
-    w.rho = w.u = w.v = w.p = w.c = R(0);
+    w.rho = w.u = w.v = w.c = R(0);
   }
   return w;
 }
@@ -60,12 +117,12 @@ __device__ __forceinline__ Prim<R> primitives(const DevParams& P, const R* U) {
 // Flux F_dir(U): Section 5 (shallow water, reactive Euler; Euler is the
 // reactive flux without species).
 template <int SYS, int D, class R>
-__device__ __forceinline__ void flux(const DevParams& P, const R* U, const Prim<R>& w, int dir, R* F) {
+__device__ __forceinline__ void flux(const Phys<R>& K, const R* U, const Prim<R>& w, int dir, R* F) {
   if constexpr (SYS == SYS_ADV) {
-    F[0] = R(P.adv[dir]) * U[0];
+    F[0] = (dir == 0 ? K.adv0 : K.adv1) * U[0];
   } else if constexpr (SYS == SYS_SWE) {
     R vn = dir == 0 ? w.u : w.v;
-    R pres = R(0.5) * R(P.g) * w.rho * w.rho;
+    R pres = K.half_g * w.rho * w.rho;
     F[0] = w.rho * vn;
     F[1] = w.rho * w.u * vn + (dir == 0 ? pres : R(0));
     if constexpr (D == 2) F[2] = w.rho * w.v * vn + (dir == 1 ? pres : R(0));
@@ -81,9 +138,9 @@ __device__ __forceinline__ void flux(const DevParams& P, const R* U, const Prim<
 
 // max_r |lambda_r(dF_dir/dU)|, the inner maximum of Eq. (2.17)/(2.19)
 template <int SYS, int D, class R>
-__device__ __forceinline__ R max_speed(const DevParams& P, const Prim<R>& w, int dir) {
+__device__ __forceinline__ R max_speed(const Phys<R>& K, const Prim<R>& w, int dir) {
   if constexpr (SYS == SYS_ADV) {
-    return rabs(R(P.adv[dir]));
+    return rabs(dir == 0 ? K.adv0 : K.adv1);
   } else {
     R vn = dir == 0 ? w.u : w.v;
     return rabs(vn) + w.c;
@@ -98,18 +155,15 @@ __device__ __forceinline__ R max_speed(const DevParams& P, const Prim<R>& w, int
 // (0, 0, 1, v[, 0]), (0, 0, 0, q, 1), (1, u+c, v, H+uc[, Y]) (Euler-type) or
 // (1, u-c, v), (0, 0, 1), (1, u+c, v) (shallow water), rotated for dir = y.
 template <int SYS, int D, class R>
-__device__ __forceinline__ R theta_sum(const DevParams& P, const Prim<R>& w, int dir, const R* dm,
-                                       const R* dp, R dx) {
+__device__ __forceinline__ R theta_sum(const Phys<R>& K, const Prim<R>& w, int dir, const R* dm, const R* dp) {
   constexpr int M = Fields<SYS, D>::M;
   R wm[M], wp[M];
   if constexpr (SYS == SYS_ADV) {
     wm[0] = dm[0];
     wp[0] = dp[0];
   } else if constexpr (SYS == SYS_SWE) {
-    R c = w.c;
-    R cmin = rsqrt_(R(P.g) * R(P.h_dry));
-    c = c < cmin ? cmin : c;
-    R inv_c = R(1) / c;
+    R c = w.c < K.cmin ? K.cmin : w.c;
+    R inv_c = frcp(c);
     R un = dir == 0 ? w.u : w.v;
     R hdn_m = dm[1 + dir] - un * dm[0];  // h d(u_n)
     R hdn_p = dp[1 + dir] - un * dp[0];
@@ -123,9 +177,8 @@ __device__ __forceinline__ R theta_sum(const DevParams& P, const Prim<R>& w, int
     wm[M - 1] = R(0.5) * (dm[0] + hdn_m * inv_c);
     wp[M - 1] = R(0.5) * (dp[0] + hdn_p * inv_c);
   } else {
-    const R gm1 = R(P.gamma - 1.0);
     const R c = w.c;
-    const R inv_c2 = R(1) / (c * c);
+    const R inv_c2 = frcp(c * c);
     const R q2 = R(0.5) * (w.u * w.u + w.v * w.v);
     const R un = dir == 0 ? w.u : w.v;
     const R ut = dir == 0 ? w.v : w.u;
@@ -135,8 +188,8 @@ __device__ __forceinline__ R theta_sum(const DevParams& P, const Prim<R>& w, int
       R* out = s == 0 ? wm : wp;
       R dmy = D == 2 ? dU[2] : R(0);
       R chem = R(0);
-      if constexpr (SYS == SYS_REACT) chem = R(P.q) * dU[D + 2];
-      R dpres = gm1 * (dU[D + 1] - w.u * dU[1] - w.v * dmy + q2 * dU[0] - chem);
+      if constexpr (SYS == SYS_REACT) chem = K.q * dU[D + 2];
+      R dpres = K.gm1 * (dU[D + 1] - w.u * dU[1] - w.v * dmy + q2 * dU[0] - chem);
       R rdun = (dir == 0 ? dU[1] : dmy) - un * dU[0];  // rho d(u_n)
       out[0] = R(0.5) * (dpres - c * rdun) * inv_c2;
       out[1] = dU[0] - dpres * inv_c2;
@@ -152,44 +205,45 @@ __device__ __forceinline__ R theta_sum(const DevParams& P, const Prim<R>& w, int
 #pragma unroll
   for (int r = 0; r < M; r++) {
     R am = rabs(wm[r]), ap = rabs(wp[r]);
-    nu += rabs(wp[r] - wm[r]) / (am + ap + dx) + am + ap;
+    nu += fdiv(rabs(wp[r] - wm[r]), am + ap + K.dx) + am + ap;
   }
   return nu;
 }
 
-// Bed gradient of b = amp exp(-((x-xc)^2 + (y-yc)^2)/w2)
+// Gradient of the bed b = amp exp(-(xr^2 + yr^2)/w2); xr, yr relative to the
+// bump centre
 template <class R>
-__device__ __forceinline__ void bed_gradient(const DevParams& P, double x, double y, int D, R* bx, R* by) {
-  R dxr = R(x - P.bed_xc), dyr = D == 2 ? R(y - P.bed_yc) : R(0);
-  R b = R(P.bed_amp) * rexp_(-(dxr * dxr + dyr * dyr) / R(P.bed_w2));
-  *bx = R(-2.0) * dxr / R(P.bed_w2) * b;
-  *by = R(-2.0) * dyr / R(P.bed_w2) * b;
+__device__ __forceinline__ void bed_gradient(const Phys<R>& K, R xr, R yr, R* bx, R* by) {
+  R b = K.bed_amp * fexp(-(xr * xr + yr * yr) * K.bed_inv_w2);
+  *bx = K.bed_m2_inv_w2 * xr * b;
+  *by = K.bed_m2_inv_w2 * yr * b;
 }
 
 // Arrhenius rate R = K rho Y exp(-Ti/T), T = p/rho (Section 5.4), in FP64
-__device__ __forceinline__ double arrhenius(const DevParams& P, double rho, double momsq, double E, double z) {
-  double pres = (P.gamma - 1.0) * (E - 0.5 * momsq / rho - P.q * z);
-  return P.K * z * exp(-P.Ti / (pres / rho));
+template <class R>
+__device__ __forceinline__ double arrhenius(const Phys<R>& K, double rho, double momsq, double E, double z) {
+  double pres = (K.gamma_d - 1.0) * (E - 0.5 * momsq / rho - K.q_d * z);
+  return K.K * z * exp(-K.Ti / (pres / rho));
 }
 
-// Source S(U) at (x, y).  Shallow water: bed slope; reactive: Arrhenius
-// (evaluated in FP64 in both precisions).
+// Source S(U) at a node whose position relative to the bump centre is
+// (xr, yr).  Shallow water: bed slope; reactive: Arrhenius (FP64).
 template <int SYS, int D, class R>
-__device__ __forceinline__ void source(const DevParams& P, const R* U, double x, double y, R* S) {
+__device__ __forceinline__ void source(const Phys<R>& K, const R* U, R xr, R yr, R* S) {
   constexpr int M = Fields<SYS, D>::M;
 #pragma unroll
   for (int c = 0; c < M; c++) S[c] = R(0);
   if constexpr (SYS == SYS_SWE) {
-    if (P.bed_amp != 0.0) {
+    if (K.bed) {
       R bx, by;
-      bed_gradient<R>(P, x, y, D, &bx, &by);
-      S[1] = -R(P.g) * U[0] * bx;
-      if constexpr (D == 2) S[2] = -R(P.g) * U[0] * by;
+      bed_gradient<R>(K, xr, D == 2 ? yr : R(0), &bx, &by);
+      S[1] = -K.g * U[0] * bx;
+      if constexpr (D == 2) S[2] = -K.g * U[0] * by;
     }
   } else if constexpr (SYS == SYS_REACT) {
-    if (P.K != 0.0) {
+    if (K.react) {
       double rho = (double)U[0], m1 = (double)U[1], m2 = D == 2 ? (double)U[2] : 0.0;
-      S[D + 2] = R(-arrhenius(P, rho, m1 * m1 + m2 * m2, (double)U[D + 1], (double)U[D + 2]));
+      S[D + 2] = R(-arrhenius(K, rho, m1 * m1 + m2 * m2, (double)U[D + 1], (double)U[D + 2]));
     }
   }
 }
@@ -200,40 +254,39 @@ __device__ __forceinline__ void source(const DevParams& P, const R* U, double x,
 // Newton's method safeguarded by bisection on the bracket between 0 and zbar.
 // Returns status bits.
 template <int SYS, int D, class R>
-__device__ __forceinline__ unsigned implicit_moment(const DevParams& P, const R* Ubar, double x, double y,
-                                                    double dt, R* Un) {
+__device__ __forceinline__ unsigned implicit_moment(const Phys<R>& K, const R* Ubar, R xr, R yr, double dt, R hdt,
+                                                    R* Un) {
   constexpr int M = Fields<SYS, D>::M;
 #pragma unroll
   for (int c = 0; c < M; c++) Un[c] = Ubar[c];
   if constexpr (SYS == SYS_SWE) {
-    if (P.bed_amp != 0.0) {
+    if (K.bed) {
       R bx, by;
-      bed_gradient<R>(P, x, y, D, &bx, &by);
-      R half = R(0.5 * dt);
-      Un[1] = Ubar[1] + half * (-R(P.g) * Un[0] * bx);
-      if constexpr (D == 2) Un[2] = Ubar[2] + half * (-R(P.g) * Un[0] * by);
+      bed_gradient<R>(K, xr, D == 2 ? yr : R(0), &bx, &by);
+      Un[1] = Ubar[1] + hdt * (-K.g * Un[0] * bx);
+      if constexpr (D == 2) Un[2] = Ubar[2] + hdt * (-K.g * Un[0] * by);
     }
     return 0u;
   } else if constexpr (SYS == SYS_REACT) {
-    if (P.K == 0.0) return 0u;
+    if (!K.react) return 0u;
     const double zbar = (double)Ubar[D + 2];
     if (zbar == 0.0) return 0u;
     const double rho = (double)Ubar[0], E = (double)Ubar[D + 1];
     const double m1 = (double)Ubar[1], m2 = D == 2 ? (double)Ubar[2] : 0.0;
     const double momsq = m1 * m1 + m2 * m2;
-    const double hk = 0.5 * dt * P.K;
-    const double dTdz = -(P.gamma - 1.0) * P.q / rho;
-    const double e0 = (P.gamma - 1.0) * (E - 0.5 * momsq / rho) / rho;  // T at z = 0
+    const double hk = 0.5 * dt * K.K;
+    const double dTdz = -(K.gamma_d - 1.0) * K.q_d / rho;
+    const double e0 = (K.gamma_d - 1.0) * (E - 0.5 * momsq / rho) / rho;  // T at z = 0
     double lo = zbar < 0.0 ? zbar : 0.0, hi = zbar < 0.0 ? 0.0 : zbar;
-    double z = zbar / (1.0 + hk * exp(-P.Ti / (e0 + dTdz * zbar)));
+    double z = zbar / (1.0 + hk * exp(-K.Ti / (e0 + dTdz * zbar)));
     unsigned st = ST_NOROOT;
     for (int it = 0; it < 60; it++) {
       double T = e0 + dTdz * z;
-      double ex = exp(-P.Ti / T);
+      double ex = exp(-K.Ti / T);
       double gz = z - zbar + hk * z * ex;
       if (gz == 0.0) { st = 0u; break; }
       if (gz > 0.0) hi = z; else lo = z;
-      double dg = 1.0 + hk * ex * (1.0 + z * P.Ti / (T * T) * dTdz);
+      double dg = 1.0 + hk * ex * (1.0 + z * K.Ti / (T * T) * dTdz);
       double zn = z - gz / dg;
       if (!(zn > lo && zn < hi)) zn = 0.5 * (lo + hi);
       double tol = 1e-15 * fmax(fabs(zbar), 1e-300);
@@ -247,21 +300,49 @@ __device__ __forceinline__ unsigned implicit_moment(const DevParams& P, const R*
   }
 }
 
-// status bits of a new state U^{n+1}
+// status bits of a new state U^{n+1} with primitives w
 template <int SYS, int D, class R>
-__device__ __forceinline__ unsigned state_status(const DevParams& P, const R* U) {
+__device__ __forceinline__ unsigned state_status(const R* U, const Prim<R>& w) {
   constexpr int M = Fields<SYS, D>::M;
-  bool bad = false;
-#pragma unroll
-  for (int c = 0; c < M; c++) bad |= !(rabs(U[c]) <= R(3.0e38));  // NaN or inf
-  unsigned st = 0u;
   if constexpr (SYS == SYS_EULER || SYS == SYS_REACT) {
-    Prim<R> w = primitives<SYS, D, R>(P, U);
-    bad |= !(w.rho > R(0)) || !(w.p > R(0));
-  } else if constexpr (SYS == SYS_SWE) {
-    if (U[0] < R(-1e-12)) st |= ST_NEGATIVE_DEPTH;
+    // a NaN or inf in any field makes p NaN or +-inf (or rho non-positive)
+    bool ok = w.rho > R(0) && w.p > R(0) && w.p <= R(3.0e38);
+    return ok ? 0u : ST_NONPHYSICAL;
+  } else {
+    bool bad = false;
+#pragma unroll
+    for (int c = 0; c < M; c++) bad |= !(rabs(U[c]) <= R(3.0e38));  // NaN or inf
+    unsigned st = bad ? ST_NONPHYSICAL : 0u;
+    if constexpr (SYS == SYS_SWE) {
+      if (U[0] < R(-1e-12)) st |= ST_NEGATIVE_DEPTH;
+    }
+    return st;
   }
-  return st | (bad ? ST_NONPHYSICAL : 0u);
 }
+
+// Error-free accumulation of FP32 values (Knuth's TwoSum into a hi/lo pair):
+// the pair carries the running sum to ~2^-48 relative, so per-thread partial
+// sums keep FP64-level accuracy without FP64 instructions per node.
+template <class R>
+struct Acc {
+  R hi, lo;
+  __device__ __forceinline__ void init() { hi = lo = R(0); }
+  __device__ __forceinline__ void add(R x) {
+    R s = hi + x;
+    R bp = s - hi;
+    R err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+template <>
+struct Acc<double> {
+  double hi;
+  __device__ __forceinline__ void init() { hi = 0.0; }
+  __device__ __forceinline__ void add(double x) { hi += x; }
+  __device__ __forceinline__ double value() const { return hi; }
+};
 
 }  // namespace lbmh

@@ -33,7 +33,7 @@ __global__ void k_moments_ext(DevParams P, R* const* buf, const Ctl* ctl, int sl
   int ej = (int)(e / G.ex), ei = (int)(e % G.ex);
   int i = map_index(ei - GH, P.nx, P.bc[0], P.bc[1]);
   int j = D == 2 ? map_index(ej - G.gy, P.ny, P.bc[2], P.bc[3]) : 0;
-  long long off = (long long)j * P.pitch + i;
+  long long off = cell(P, i, j);
 #pragma unroll
   for (int c = 0; c < M; c++) {
     R s = R(0);
@@ -54,10 +54,11 @@ __global__ void k_indicator(DevParams P, const Ctl* ctl, int slot, ExtGeom G, co
   int ej = (int)(e / G.ex), ei = (int)(e % G.ex);
   if (ei < 1 || ei >= G.ex - 1) return;
   if (D == 2 && (ej < 1 || ej >= G.ey - 1)) return;
+  const Phys<R> K = make_phys<R>(P);
   R U0[M], dm[M], dp[M];
 #pragma unroll
   for (int c = 0; c < M; c++) U0[c] = Ue[(long long)c * n + e];
-  Prim<R> w = primitives<SYS, D, R>(P, U0);
+  Prim<R> w = primitives<SYS, D, R>(K, U0);
   R s = R(0);
 #pragma unroll
   for (int dir = 0; dir < D; dir++) {
@@ -67,7 +68,7 @@ __global__ void k_indicator(DevParams P, const Ctl* ctl, int slot, ExtGeom G, co
       dm[c] = U0[c] - Ue[(long long)c * n + e - step];
       dp[c] = Ue[(long long)c * n + e + step] - U0[c];
     }
-    s += theta_sum<SYS, D, R>(P, w, dir, dm, dp, R(P.dx));
+    s += theta_sum<SYS, D, R>(K, w, dir, dm, dp);
   }
   nu[e] = s;
 }
@@ -89,7 +90,7 @@ __global__ void k_omega(DevParams P, const Ctl* ctl, int slot, ExtGeom G, const 
     R s = R(0);
     for (int bj = (D == 2 ? -1 : 0); bj <= (D == 2 ? 1 : 0); bj++)
       for (int bi = -1; bi <= 1; bi++) s += nu[e + (long long)bj * G.ex + bi];
-    w = R(1) + R(1) / (R(1) + s);
+    w = R(1) + fdiv(R(1), R(1) + s);
   }
   om[e] = w;
 }
@@ -171,6 +172,7 @@ __global__ void k_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
 #pragma unroll
   for (int c = 0; c < M; c++) usum[c] = 0.0;
   unsigned st = 0u;
+  const Phys<R> K = make_phys<R>(P);
   const R a0 = R(cf.a0), inv2l = R(1.0 / (2.0 * cf.lam)), hdt = R(0.5 * cf.dt);
   const R al[2] = {R(cf.alpha[0]), R(cf.alpha[1])};
   const R ak[3] = {R(cf.a0), R(cf.aj[0]), R(cf.aj[1])};
@@ -188,7 +190,7 @@ __global__ void k_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
       for (int c = 0; c < M; c++) U[c] = Ue[(long long)c * next + e];
       int si = map_index(ei - GH, P.nx, P.bc[0], P.bc[1]);
       int sj = D == 2 ? map_index(ej - G.gy, P.ny, P.bc[2], P.bc[3]) : 0;
-      Prim<R> w = primitives<SYS, D, R>(P, U);
+      Prim<R> w = primitives<SYS, D, R>(K, U);
       R feq[M];
       if (k == 0) {
 #pragma unroll
@@ -196,15 +198,15 @@ __global__ void k_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
       } else {
         int jd = (k - 1) % D;
         R F[M];
-        flux<SYS, D, R>(P, U, w, jd, F);
+        flux<SYS, D, R>(K, U, w, jd, F);
         R sg = k <= D ? R(1) : R(-1);
 #pragma unroll
         for (int c = 0; c < M; c++) feq[c] = (al[jd] * U[c] + sg * F[c]) * inv2l;
       }
-      source<SYS, D, R>(P, U, P.x0 + (si + 0.5) * P.dx, P.y0 + (sj + 0.5) * P.dx, S);
+      source<SYS, D, R>(K, U, K.xb + R(si) * K.dx, K.yb + R(sj) * K.dx, S);
       R wk = om[e];
       R akk = k == 0 ? ak[0] : ak[1 + (k - 1) % D];
-      long long off = (long long)sj * P.pitch + si;
+      long long off = cell(P, si, sj);
 #pragma unroll
       for (int c = 0; c < M; c++) {
         R fk = f[(long long)(k * M + c) * P.plane + off];
@@ -219,10 +221,10 @@ __global__ void k_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
       for (int k = 0; k < Q; k++) s += Fk[k][c];
       Ubar[c] = s;
     }
-    double xn = P.x0 + (i + 0.5) * P.dx, yn = P.y0 + (j + 0.5) * P.dx;
-    st |= implicit_moment<SYS, D, R>(P, Ubar, xn, yn, cf.dt, Un);
-    source<SYS, D, R>(P, Un, xn, yn, S);
-    long long off = (long long)j * P.pitch + i;
+    const R xn = K.xb + R(i) * K.dx, yn = K.yb + R(j) * K.dx;
+    st |= implicit_moment<SYS, D, R>(K, Ubar, xn, yn, cf.dt, hdt, Un);
+    source<SYS, D, R>(K, Un, xn, yn, S);
+    long long off = cell(P, i, j);
     R Us[M];
 #pragma unroll
     for (int c = 0; c < M; c++) Us[c] = R(0);
@@ -236,12 +238,12 @@ __global__ void k_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
         Us[c] += v;  // the moments the next step will see (Eq. 2.3, k = 0..Q-1)
       }
     }
-    Prim<R> wn = primitives<SYS, D, R>(P, Us);
-    sp0 = (double)max_speed<SYS, D, R>(P, wn, 0);
-    if (D == 2) sp1 = (double)max_speed<SYS, D, R>(P, wn, 1);
+    Prim<R> wn = primitives<SYS, D, R>(K, Us);
+    sp0 = (double)max_speed<SYS, D, R>(K, wn, 0);
+    if (D == 2) sp1 = (double)max_speed<SYS, D, R>(K, wn, 1);
 #pragma unroll
     for (int c = 0; c < M; c++) usum[c] = (double)Us[c];
-    st |= state_status<SYS, D, R>(P, Us);
+    st |= state_status<SYS, D, R>(Us, wn);
   }
   block_side_outputs<M>(sp0, sp1, usum, ctl, (slot + 1) % 3, partials, st);
   if (blockIdx.x == 0 && threadIdx.x == 0) advance_ctl<D>(ctl, slot, cf);

@@ -126,7 +126,20 @@ def test_fp32_accuracy(system, dim, bc, kernel):
 
 
 @pytest.mark.parametrize("kernel", KERNELS, ids=["unfused", "auto"])
-@pytest.mark.parametrize("shape", [(1, 1), (2, 1), (3, 1), (1, 1, 2), (2, 2, 2), (5, 3, 2), (40, 1, 2)])
+@pytest.mark.parametrize("system,bc", [(s, bc) for s in SYSTEMS for bc in (W.PERIODIC, W.OUTFLOW)])
+@pytest.mark.parametrize("nx,ny", [(257, 40), (361, 23)])
+def test_fp64_parity_several_strips(system, bc, nx, ny, kernel):
+    """Grids wider than one strip of the fused kernel (120 columns), ragged in
+    both directions, 12 steps."""
+    pb, U0 = make_case(system, 2, bc, nx=nx, ny=ny, seed=5)
+    run_pair(pb, U0, 12, lbmh.FP64, kernel, check_every=4)
+    pb, U0 = make_case(system, 2, bc, nx=nx, ny=ny, seed=6)
+    run_pair(pb, U0, 12, lbmh.FP32, kernel, check_every=4)
+
+
+@pytest.mark.parametrize("kernel", KERNELS, ids=["unfused", "auto"])
+@pytest.mark.parametrize("shape", [(1, 1), (2, 1), (3, 1), (1, 1, 2), (2, 2, 2), (5, 3, 2), (40, 1, 2), (6, 9, 2),
+                                   (7, 5, 2)])
 def test_tiny_and_degenerate_grids(shape, kernel):
     nx, ny = shape[0], shape[1]
     dim = shape[2] if len(shape) > 2 else 1
