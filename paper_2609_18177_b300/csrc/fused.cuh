@@ -133,7 +133,8 @@ __device__ __forceinline__ void fused_side_outputs(R sp0, R sp1, const Acc<R>* a
 // shared memory and written with one TMA bulk store covering columns
 // [0, nxs), nxs = nx rounded down to 16 bytes: the bulk store writes whole
 // 16-byte granules, so the last columns and the ghost columns behind them
-// are written with plain stores instead.
+// are written with plain stores instead (the ghost columns by the whole CTA,
+// from the staged row).
 template <int SYS, class R, int PREF, int CPT>
 __global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensorMap tl0,
                                                 const __grid_constant__ CUtensorMap tl1,
@@ -214,7 +215,6 @@ __global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensor
     int gx[CPT];
     bool outc[CPT];
     R xr_ghost[CPT], xr_out[CPT];
-    unsigned pad_mask[CPT];
 #pragma unroll
     for (int j = 0; j < CPT; j++) {
       const int sc = sc0 + j;
@@ -223,13 +223,35 @@ __global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensor
       const int mx = map_index(gx[j], P.nx, P.bc[0], P.bc[1]);
       xr_ghost[j] = K.xb + R(mx) * K.dx;  // a ghost node sits where the node it copies sits
       xr_out[j] = K.xb + R(gx[j]) * K.dx;
-      pad_mask[j] = 0u;  // ghost columns this node feeds (only near the x boundaries)
-      if (outc[j] && (gx[j] < NGHOST || gx[j] >= P.nx - NGHOST))
+    }
+    // ghost columns whose source node lies in this strip's output range: the
+    // CTA writes them after each row from the staged output
+    const int xe = min(x0 + WOUT, P.nx);
+    bool has_pads = false;
 #pragma unroll
-        for (int p = 0; p < 2 * NGHOST; p++) {
-          int x = p < NGHOST ? p - NGHOST : P.nx + (p - NGHOST);
-          if (map_index(x, P.nx, P.bc[0], P.bc[1]) == gx[j]) pad_mask[j] |= 1u << p;
+    for (int p = 0; p < 2 * NGHOST; p++) {
+      int src = map_index(p < NGHOST ? p - NGHOST : P.nx + (p - NGHOST), P.nx, P.bc[0], P.bc[1]);
+      has_pads |= src >= x0 && src < xe;
+    }
+    // this thread's share of the ghost-column stores (item = ghost column x
+    // of plane q): offset from the row base and index into the staged row
+    constexpr int NPAD = (2 * NGHOST * QM + FT - 1) / FT;
+    long long pad_goff[NPAD];
+    int pad_sidx[NPAD];
+#pragma unroll
+    for (int i = 0; i < NPAD; i++) {
+      const int item = t + i * FT;
+      pad_sidx[i] = -1;
+      pad_goff[i] = 0;
+      if (item < 2 * NGHOST * QM) {
+        const int p = item / QM, q = item % QM;
+        const int x = p < NGHOST ? p - NGHOST : P.nx + (p - NGHOST);
+        const int src = map_index(x, P.nx, P.bc[0], P.bc[1]);
+        if (src >= x0 && src < xe) {
+          pad_sidx[i] = q * WOUT + (src - x0);
+          pad_goff[i] = (long long)q * P.plane + x;
         }
+      }
     }
     const int r0 = yb - 3, r1 = ye + 2;
     const unsigned seq0 = seq;
@@ -421,18 +443,6 @@ __global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensor
 #pragma unroll
               for (int c = 0; c < M; c++) base[(long long)(k * M + c) * P.plane] = Fk[k][c];
           }
-          if (pad_mask[j]) {
-            R* base = fout + (long long)y * P.pitch + XPAD;
-#pragma unroll
-            for (int p = 0; p < 2 * NGHOST; p++)
-              if (pad_mask[j] & (1u << p)) {
-                int x = p < NGHOST ? p - NGHOST : P.nx + (p - NGHOST);
-#pragma unroll
-                for (int k = 0; k < Q; k++)
-#pragma unroll
-                  for (int c = 0; c < M; c++) base[(long long)(k * M + c) * P.plane + x] = Fk[k][c];
-              }
-          }
           sp0 = rmax(sp0, max_speed<SYS, 2, R>(K, wn, 0));
           sp1 = rmax(sp1, max_speed<SYS, 2, R>(K, wn, 1));
 #pragma unroll
@@ -458,6 +468,12 @@ __global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensor
       }
       __syncthreads();
       if (t == 0 && row_out && x0 < nxs) tma_store_row(tms, smem_u32(stage), x0, y);
+      if (row_out && has_pads) {
+        R* base = fout + (long long)y * P.pitch + XPAD;
+#pragma unroll
+        for (int i = 0; i < NPAD; i++)
+          if (pad_sidx[i] >= 0) base[pad_goff[i]] = stage[pad_sidx[i]];
+      }
     }
   }
   if (t == 0) {
