@@ -159,6 +159,31 @@ LBMH_API int lbmh_destroy(lbmh_handle *h);
  * is NULL).  Never NULL. */
 LBMH_API const char *lbmh_last_error(const lbmh_handle *h);
 
+/* One time step that allocates no device memory (the paper has no
+ * counterpart: this is a deployment entry point).  Meant for callers that
+ * cannot call cudaMalloc: code inside a host callback or a CUDA-graph node
+ * where allocation is illegal, runtimes that only hand out memory from a
+ * frozen pool, or real-time loops that cannot afford the implicit device
+ * synchronisation an allocation may cause.  No handle is needed.
+ *
+ * f_in, f_out: distinct device arrays, FP64 [Q][m][ny][nx] (the layout of
+ * lbmh_get_f); the step reads f_in and writes f_out.  The speed bound, time
+ * step and lambda are computed from f_in (Eq. 2.19, 2.21).  dt_out: NULL, or
+ * a host pointer that receives the step's dt; when given, the call
+ * synchronises the stream and returns LBMH_ERR_NONPHYSICAL if the new state
+ * is non-physical.  Only LBMH_FP64 is accepted.
+ *
+ * The intermediate arrays live in one static device array of 16 MiB that
+ * every GPU loading this library holds until the process exits; grids whose
+ * ghost-extended scratch does not fit ((nx+6)(ny+6)(m+2) doubles plus a few
+ * KB) are rejected with LBMH_ERR_INVALID_ARG.  The first call on a device
+ * looks the array up (cudaGetSymbolAddress), so make that first call before
+ * any stream capture.  All calls share the array and each call clears the
+ * part that must start from zero: calls that may overlap on the GPU (other
+ * streams, other host threads) race with each other and must be serialised
+ * by the caller. */
+LBMH_API int lbmh_step_static(const lbmh_problem *p, const double *f_in, double *f_out, double *dt_out);
+
 /* Library version string. */
 LBMH_API const char *lbmh_version(void);
 

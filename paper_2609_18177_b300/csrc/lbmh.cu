@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -809,3 +810,154 @@ int lbmh_get_info(lbmh_handle* h, lbmh_info* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free single step
+//
+// For callers that must not allocate device memory: code running where
+// cudaMalloc is unavailable or forbidden (inside a host callback or a
+// memory-pool-only runtime, under an allocator that must stay frozen after
+// start-up, or a real-time loop that cannot afford an allocation's implicit
+// synchronisation).  The step runs the unfused kernels with their scratch
+// (ghost-extended U, nu, omega, the control block and the per-block sums)
+// placed in one file-scope device array of kStaticScratchBytes that every
+// GPU loading this library holds until the process exits.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;  // 16 MiB per device
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices];  // device address of g_static_scratch, per device
+
+// control block and distribution-pointer pair of the allocation-free step
+__global__ void k_static_begin(Ctl* ctl, void** bufs, void* f_in, void* f_out) {
+  unsigned char* c = (unsigned char*)ctl;
+  for (size_t i = 0; i < sizeof(Ctl); i++) c[i] = 0;
+  bufs[0] = f_in;
+  bufs[1] = f_out;
+}
+
+template <int SYS, int D>
+void static_step_launch(const DevParams& P, const ExtGeom& G, Ctl* ctl, double* const* bufs, double* partials,
+                        double* Ue, double* nue, double* ome, cudaStream_t stream) {
+  long long nn = (long long)P.nx * P.ny;
+  long long next = (long long)G.ex * G.ey;
+  unsigned nb = blocks_for(next), nbn = blocks_for(nn);
+  k_speed_of_f<SYS, D, double><<<nbn, kBlock, 0, stream>>>(P, bufs, ctl);
+  k_moments_ext<SYS, D, double><<<nb, kBlock, 0, stream>>>(P, bufs, ctl, 0, G, Ue);
+  k_indicator<SYS, D, double><<<nb, kBlock, 0, stream>>>(P, ctl, 0, G, Ue, nue);
+  k_omega<D, double><<<nb, kBlock, 0, stream>>>(P, ctl, 0, G, nue, ome);
+  k_collide_stream<SYS, D, double><<<nbn, kBlock, 0, stream>>>(P, bufs, ctl, 0, G, Ue, ome, partials);
+}
+
+}  // namespace
+
+extern "C" int lbmh_step_static(const lbmh_problem* p, const double* f_in, double* f_out, double* dt_out) {
+  std::string why;
+  int rc = validate(p, why);
+  if (rc) return fail(nullptr, rc, why);
+  if (p->precision != LBMH_FP64) return fail(nullptr, LBMH_ERR_UNSUPPORTED, "lbmh_step_static runs in FP64 only");
+  if (!f_in || !f_out || f_in == f_out) return fail(nullptr, LBMH_ERR_INVALID_ARG, "f_in and f_out must be distinct device arrays");
+  const int m = nfields(p->system, p->dim), Q = 2 * p->dim + 1;
+  DevParams P;
+  memset(&P, 0, sizeof P);
+  P.nx = p->nx;
+  P.ny = p->dim == 2 ? p->ny : 1;
+  P.pitch = P.nx;  // the caller's arrays are unpadded [Q][m][ny][nx]
+  P.plane = (long long)P.nx * P.ny;
+  for (int s = 0; s < 4; s++) P.bc[s] = p->bc[s];
+  if (p->dim == 1) P.bc[2] = P.bc[3] = LBMH_BC_PERIODIC;
+  P.x0 = p->x0;
+  P.y0 = p->dim == 2 ? p->y0 : 0.0;
+  P.dx = (p->x1 - p->x0) / p->nx;
+  P.cfl = p->cfl;
+  P.eps = p->eps;
+  P.adv[0] = p->adv[0];
+  P.adv[1] = p->adv[1];
+  P.gamma = p->gamma;
+  P.g = p->g;
+  P.h_dry = p->h_dry > 0.0 ? p->h_dry : 1e-8;
+  P.bed_amp = p->bed_amp;
+  P.bed_w2 = p->bed_w2 > 0.0 ? p->bed_w2 : 1.0;
+  P.bed_xc = p->bed_xc;
+  P.bed_yc = p->bed_yc;
+  P.K = p->K;
+  P.Ti = p->Ti;
+  P.q = p->q;
+  P.omega_mode = p->omega_mode;
+  P.omega_fixed = p->omega_fixed;
+  ExtGeom G;
+  G.ex = P.nx + 2 * GH;
+  G.gy = p->dim == 2 ? GH : 0;
+  G.ey = p->dim == 2 ? P.ny + 2 * GH : 1;
+
+  // scratch layout: control block | pointer pair | per-block sums | U_ext | nu_ext | omega_ext
+  const long long nn = (long long)P.nx * P.ny, next = (long long)G.ex * G.ey;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t off_bufs = up(sizeof(Ctl));
+  const size_t off_part = off_bufs + 256;
+  const size_t off_U = off_part + up((size_t)blocks_for(nn) * m * sizeof(double));
+  const size_t off_nu = off_U + up((size_t)next * m * sizeof(double));
+  const size_t off_om = off_nu + up((size_t)next * sizeof(double));
+  const size_t need = off_om + up((size_t)next * sizeof(double));
+  if (need > kStaticScratchBytes)
+    return fail(nullptr, LBMH_ERR_INVALID_ARG,
+                "grid too large for the static scratch: needs " + std::to_string(need) + " bytes, the limit is " +
+                    std::to_string(kStaticScratchBytes) + " bytes (16 MiB)");
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, LBMH_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, LBMH_ERR_UNSUPPORTED, "device index beyond the static table");
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {  // first call on this device: look the array up once
+      e = cudaGetSymbolAddress(&g_static_addr[dev], g_static_scratch);
+      if (e != cudaSuccess) {
+        g_static_addr[dev] = nullptr;
+        return fail(nullptr, LBMH_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      }
+    }
+    base = g_static_addr[dev];
+  }
+  unsigned char* b = (unsigned char*)base;
+  Ctl* ctl = (Ctl*)b;
+  double** bufs = (double**)(b + off_bufs);
+  double* partials = (double*)(b + off_part);
+  double* Ue = (double*)(b + off_U);
+  double* nue = (double*)(b + off_nu);
+  double* ome = (double*)(b + off_om);
+  cudaStream_t stream = (cudaStream_t)p->cuda_stream;
+
+  // the kernels address node (i, j) of plane q at q*plane + j*pitch + i + XPAD;
+  // shifting the base pointers by -XPAD maps that onto the unpadded arrays
+  k_static_begin<<<1, 1, 0, stream>>>(ctl, (void**)bufs, (void*)(f_in - XPAD), (void*)(f_out - XPAD));
+  switch (p->system * 2 + (p->dim - 1)) {
+    case SYS_ADV * 2 + 0: static_step_launch<SYS_ADV, 1>(P, G, ctl, bufs, partials, Ue, nue, ome, stream); break;
+    case SYS_ADV * 2 + 1: static_step_launch<SYS_ADV, 2>(P, G, ctl, bufs, partials, Ue, nue, ome, stream); break;
+    case SYS_EULER * 2 + 0: static_step_launch<SYS_EULER, 1>(P, G, ctl, bufs, partials, Ue, nue, ome, stream); break;
+    case SYS_EULER * 2 + 1: static_step_launch<SYS_EULER, 2>(P, G, ctl, bufs, partials, Ue, nue, ome, stream); break;
+    case SYS_SWE * 2 + 0: static_step_launch<SYS_SWE, 1>(P, G, ctl, bufs, partials, Ue, nue, ome, stream); break;
+    case SYS_SWE * 2 + 1: static_step_launch<SYS_SWE, 2>(P, G, ctl, bufs, partials, Ue, nue, ome, stream); break;
+    case SYS_REACT * 2 + 0: static_step_launch<SYS_REACT, 1>(P, G, ctl, bufs, partials, Ue, nue, ome, stream); break;
+    case SYS_REACT * 2 + 1: static_step_launch<SYS_REACT, 2>(P, G, ctl, bufs, partials, Ue, nue, ome, stream); break;
+    default: return fail(nullptr, LBMH_ERR_INVALID_ARG, "unknown system");
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(nullptr, LBMH_ERR_CUDA, std::string("static step launch: ") + cudaGetErrorString(e));
+  if (dt_out) {
+    Ctl c;
+    e = cudaMemcpyAsync(&c, ctl, sizeof c, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return fail(nullptr, LBMH_ERR_CUDA, std::string("static step readback: ") + cudaGetErrorString(e));
+    *dt_out = c.last_dt;
+    if (c.status & ST_NONPHYSICAL) return fail(nullptr, LBMH_ERR_NONPHYSICAL, "the step produced a non-physical state");
+  }
+  (void)Q;
+  return LBMH_OK;
+}

@@ -84,6 +84,7 @@ SIGNATURES = [
     ("lbmh_omega", ctypes.c_int, [_H, _DP, ctypes.c_int]),
     ("lbmh_get_info", ctypes.c_int, [_H, ctypes.POINTER(Info)]),
     ("lbmh_destroy", ctypes.c_int, [_H]),
+    ("lbmh_step_static", ctypes.c_int, [ctypes.POINTER(_Problem), _DP, _DP, ctypes.POINTER(ctypes.c_double)]),
     ("lbmh_last_error", ctypes.c_char_p, [_H]),
     ("lbmh_version", ctypes.c_char_p, []),
 ]
@@ -247,6 +248,23 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def step_static(pb, f_in, f_out, stream=None, want_dt=True):
+    """One FP64 step f_in -> f_out on device tensors [Q][m][ny][nx] through the
+    allocation-free entry point (scratch in the library's static device
+    array).  Returns dt when want_dt (which synchronises the stream)."""
+    lib = load()
+    s = _c_problem(pb, FP64, KERNEL_UNFUSED, _current_stream() if stream is None else stream)
+    pi, di = _ptr(f_in)
+    po, do = _ptr(f_out)
+    if not (di and do):
+        raise TypeError("step_static takes device tensors")
+    dt = ctypes.c_double(0.0)
+    rc = lib.lbmh_step_static(ctypes.byref(s), pi, po, ctypes.byref(dt) if want_dt else None)
+    if rc != OK:
+        raise LbmhError(rc, lib.lbmh_last_error(None).decode())
+    return dt.value if want_dt else None
 
 
 def version():
