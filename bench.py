@@ -49,9 +49,13 @@ def parse():
     return ap.parse_args()
 
 
+KERNEL_SOURCES = ("common.cuh", "physics.cuh", "unfused.cuh", "fused.cuh")
+
+
 def source_hash():
+    """Hash of the sources that define the step kernels (not the host code)."""
     h = hashlib.sha256()
-    for name in sorted(os.listdir(CSRC)):
+    for name in KERNEL_SOURCES:
         with open(os.path.join(CSRC, name), "rb") as fh:
             h.update(name.encode())
             h.update(fh.read())
