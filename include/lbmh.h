@@ -159,6 +159,63 @@ LBMH_API int lbmh_destroy(lbmh_handle *h);
  * is NULL).  Never NULL. */
 LBMH_API const char *lbmh_last_error(const lbmh_handle *h);
 
+/* ------------------------------------------------------------------------
+ * Batches: many 2D lattices of one system and precision, of uneven sizes,
+ * advanced together by one persistent kernel launch per step (replayed from
+ * a captured CUDA graph three steps at a time).  Each lattice keeps its own
+ * time step (Eq. 2.21 from its own speed bound), time and step count, and
+ * stops by itself at its step target or end time.  Lattices live in a device
+ * arena of fixed capacity allocated at creation; lbmh_batch_add admits a
+ * lattice only if its footprint fits (first-fit), so a caller can queue work
+ * by HBM footprint.  Not thread-safe; batches are independent.
+ * ------------------------------------------------------------------------ */
+typedef struct lbmh_batch lbmh_batch;
+
+/* Create an empty batch of `system` (2D only) in `precision` with a device
+ * arena of capacity_bytes and room for max_instances lattices. */
+LBMH_API int lbmh_batch_create(int system, int precision, int64_t capacity_bytes, int max_instances,
+                               void *cuda_stream, lbmh_batch **out);
+
+/* Device bytes one lattice of problem p occupies in a batch arena (two
+ * distribution copies), or -1 for an invalid problem. */
+LBMH_API int64_t lbmh_batch_footprint(const lbmh_problem *p);
+
+/* Admit a lattice: f := f^eq(U0) (U0 FP64 [m][ny][nx], host or device).  It
+ * stops after max_steps steps (if > 0) or once t >= T (if T > 0).  *slot
+ * receives its index.  LBMH_ERR_OOM when the arena or the slots are full.
+ * Synchronises the stream. */
+LBMH_API int lbmh_batch_add(lbmh_batch *b, const lbmh_problem *p, const double *U0, int on_device,
+                            int64_t max_steps, double T, int *slot);
+
+/* Free a lattice's slot and arena space.  Synchronises. */
+LBMH_API int lbmh_batch_remove(lbmh_batch *b, int slot);
+
+/* Enqueue n batched steps (lattices that reached their target are skipped). */
+LBMH_API int lbmh_batch_step(lbmh_batch *b, int64_t n);
+
+/* Time each kernel variant (ring depth 1 or 2 rows ahead; segments of one
+ * chunk or half a chunk) on the live batch for steps_per_candidate steps and
+ * keep the fastest.  Every timed launch is a real step of the batch.
+ * *best_ms (may be NULL) receives the chosen variant's time per step. */
+LBMH_API int lbmh_batch_autotune(lbmh_batch *b, int steps_per_candidate, double *best_ms);
+
+/* Per slot (arrays of max_instances, any may be NULL): done = 1 finished
+ * (target reached or non-physical), 0 running, -1 free; time; steps; status
+ * bits.  Synchronises. */
+LBMH_API int lbmh_batch_poll(lbmh_batch *b, int *done, double *t, int64_t *steps, uint32_t *status);
+
+/* U = sum_k f_k of one lattice into U_out (FP64 [m][ny][nx]).  Synchronises
+ * when U_out is a host array. */
+LBMH_API int lbmh_batch_moments(lbmh_batch *b, int slot, double *U_out, int on_device);
+
+/* Arena use, capacity, live lattices, grid size and the chosen variant
+ * (10 * rows ahead + segments per chunk). */
+LBMH_API int lbmh_batch_info(lbmh_batch *b, int64_t *used_bytes, int64_t *capacity_bytes, int *active, int *grid,
+                             int *variant);
+
+LBMH_API int lbmh_batch_destroy(lbmh_batch *b);
+LBMH_API const char *lbmh_batch_last_error(const lbmh_batch *b);
+
 /* One time step that allocates no device memory (the paper has no
  * counterpart: this is a deployment entry point).  Meant for callers that
  * cannot call cudaMalloc: code inside a host callback or a CUDA-graph node

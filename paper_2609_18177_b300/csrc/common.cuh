@@ -34,6 +34,7 @@ struct DevParams {
   double x0, y0, dx;
   double cfl, eps;
   double T;          // > 0: steps stop once t >= T
+  long long max_steps;  // > 0: steps stop once this many were taken
   double adv[2];
   double gamma, g, h_dry;
   double bed_amp, bed_w2, bed_xc, bed_yc;
@@ -94,7 +95,7 @@ __device__ __forceinline__ StepCoef step_coef(const DevParams& P, const Ctl* ctl
   double ab0 = bits_to_double(ctl->amax[slot][0]);
   double ab1 = D == 2 ? bits_to_double(ctl->amax[slot][1]) : 0.0;
   double t = ctl->t[slot];
-  c.active = !(P.T > 0.0 && t >= P.T);
+  c.active = !(P.T > 0.0 && t >= P.T) && !(P.max_steps > 0 && ctl->nsteps[slot] >= P.max_steps);
   double asum = D == 2 ? ab0 + ab1 : ab0;
   c.dt = P.cfl * P.dx / asum;
   c.lam = P.dx / c.dt;

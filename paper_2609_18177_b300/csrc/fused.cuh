@@ -122,19 +122,384 @@ __device__ __forceinline__ void fused_side_outputs(R sp0, R sp1, const Acc<R>* a
   block_side_outputs<M>((double)sp0, (double)sp1, usum, ctl, slot1, partials, st);
 }
 
-// CPT: columns per thread (1 or 2).  Lane t holds columns t*CPT .. t*CPT+CPT-1
-// of the CTA's NC = 128*CPT loaded columns; a strip's outputs are columns
-// [4, NC-4).  A thread's own columns pass values to each other in registers;
-// only the outermost columns exchange through shared memory.
-//
-// Work split: the strips x rows of the grid are cut into gridDim equal
+// Coefficients of one step of one lattice, in the arithmetic type of the path
+// (Eq. 2.20, 2.21 and the weights a_k of Eq. 2.5).
+template <class R>
+struct Coef2D {
+  R a0, inv2l, hdt, al0, al1, akk[5], om_fixed;
+  double dt;
+  bool fixed_omega;
+};
+
+template <class R>
+__device__ __forceinline__ Coef2D<R> make_coef2d(const StepCoef& cf, const DevParams& P) {
+  Coef2D<R> c;
+  c.a0 = R(cf.a0);
+  c.inv2l = R(1.0 / (2.0 * cf.lam));
+  c.hdt = R(0.5 * cf.dt);
+  c.al0 = R(cf.alpha[0]);
+  c.al1 = R(cf.alpha[1]);
+  c.akk[0] = R(cf.a0);
+  c.akk[1] = c.akk[3] = R(cf.aj[0]);
+  c.akk[2] = c.akk[4] = R(cf.aj[1]);
+  c.om_fixed = R(P.omega_fixed);
+  c.dt = cf.dt;
+  c.fixed_omega = P.omega_mode == 1;
+  return c;
+}
+
+// Row-pipeline state of a CTA: the shared-memory ring, its row-load counters
+// and the abort flag, carried from one segment to the next.
+struct Pipe2D {
+  unsigned char* smem;
+  int* s_abort;
+  unsigned seq;         // row loads so far (ring slot / mbarrier phase)
+  unsigned issued_end;  // one past the last row load issued (thread 0)
+  unsigned cur;         // row load being consumed
+  bool aborted;
+};
+
+// One strip segment of one lattice: rows [yb, ye) of strip `strip`, written
+// to fout.  CPT: columns per thread (1 or 2).  Lane t holds columns
+// t*CPT .. t*CPT+CPT-1 of the NC = 128*CPT loaded columns; the strip's outputs
+// are columns [4, NC-4).  A thread's own columns pass values to each other in
+// registers; only the outermost columns exchange through shared memory.  Each
+// output row is staged in shared memory and written with one TMA bulk store
+// covering columns [0, nxs), nxs = nx rounded down to 16 bytes: the bulk store
+// writes whole 16-byte granules, so the last columns and the ghost columns
+// behind them are written with plain stores instead (the ghost columns by the
+// whole CTA, from the staged row).
+template <int SYS, class R, int PREF, int CPT>
+__device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml, const CUtensorMap* tms, R* fout,
+                                              const DevParams& P, const Phys<R>& K, const Coef2D<R>& cc, int strip,
+                                              int yb, int ye, int nxs, R& sp0, R& sp1, Acc<R>* acc, unsigned& st) {
+  constexpr int M = Fields<SYS, 2>::M, Q = 5, QM = Q * M;
+  constexpr bool SRC = HasSource<SYS>::value;
+  using L = Smem2D<M, R, PREF, CPT>;
+  constexpr int S = L::S, NC = L::NC, WOUT = L::WOUT;
+  unsigned char* smem_raw = pp.smem;
+  R* fring = (R*)smem_raw;
+  R* Usm = (R*)(smem_raw + L::f_bytes);
+  R* colsm = (R*)(smem_raw + L::f_bytes + L::u_bytes);
+  R* p13 = (R*)(smem_raw + L::f_bytes + L::u_bytes + L::c_bytes);
+  R* stage = (R*)(smem_raw + L::o_off);
+  unsigned long long* bars = (unsigned long long*)(smem_raw + L::bar_off);
+  int* s_abort = pp.s_abort;
+  unsigned& seq = pp.seq;
+  unsigned& issued_end = pp.issued_end;
+  unsigned& cur = pp.cur;
+  bool& aborted = pp.aborted;
+  const int t = threadIdx.x;
+  const int sc0 = t * CPT;                              // first own column
+  const int scl = sc0 > 0 ? sc0 - 1 : 0;                // left neighbour column (clamped)
+  const int scr = sc0 + CPT < NC ? sc0 + CPT : NC - 1;  // right neighbour column (clamped)
+  const int tl = t > 0 ? t - 1 : 0, tr = t < FT - 1 ? t + 1 : FT - 1;
+  const R a0 = cc.a0, inv2l = cc.inv2l, hdt = cc.hdt, al0 = cc.al0, al1 = cc.al1;
+  const R* akk = cc.akk;
+  const bool fixed_omega = cc.fixed_omega;
+  const R om_fixed = cc.om_fixed;
+  const uint32_t row_bytes = (uint32_t)(QM * NC * sizeof(R));
+      const int x0 = strip * WOUT;
+      int gx[CPT];
+      bool outc[CPT];
+      R xr_ghost[CPT], xr_out[CPT];
+  #pragma unroll
+      for (int j = 0; j < CPT; j++) {
+        const int sc = sc0 + j;
+        gx[j] = x0 - 4 + sc;
+        outc[j] = sc >= 4 && sc < NC - 4 && gx[j] < P.nx;
+        const int mx = map_index(gx[j], P.nx, P.bc[0], P.bc[1]);
+        xr_ghost[j] = K.xb + R(mx) * K.dx;  // a ghost node sits where the node it copies sits
+        xr_out[j] = K.xb + R(gx[j]) * K.dx;
+      }
+      // ghost columns whose source node lies in this strip's output range: the
+      // CTA writes them after each row from the staged output
+      const int xe = min(x0 + WOUT, P.nx);
+      bool has_pads = false;
+  #pragma unroll
+      for (int p = 0; p < 2 * NGHOST; p++) {
+        int src = map_index(p < NGHOST ? p - NGHOST : P.nx + (p - NGHOST), P.nx, P.bc[0], P.bc[1]);
+        has_pads |= src >= x0 && src < xe;
+      }
+      // this thread's share of the ghost-column stores (item = ghost column x
+      // of plane q): offset from the row base and index into the staged row
+      constexpr int NPAD = (2 * NGHOST * QM + FT - 1) / FT;
+      long long pad_goff[NPAD];
+      int pad_sidx[NPAD];
+  #pragma unroll
+      for (int i = 0; i < NPAD; i++) {
+        const int item = t + i * FT;
+        pad_sidx[i] = -1;
+        pad_goff[i] = 0;
+        if (item < 2 * NGHOST * QM) {
+          const int p = item / QM, q = item % QM;
+          const int x = p < NGHOST ? p - NGHOST : P.nx + (p - NGHOST);
+          const int src = map_index(x, P.nx, P.bc[0], P.bc[1]);
+          if (src >= x0 && src < xe) {
+            pad_sidx[i] = q * WOUT + (src - x0);
+            pad_goff[i] = (long long)q * P.plane + x;
+          }
+        }
+      }
+      const int r0 = yb - 3, r1 = ye + 2;
+      const unsigned seq0 = seq;
+      seq += (unsigned)(r1 - r0 + 1);
+      if (t == 0) {
+        for (int i = 0; i < PREF && r0 + i <= r1; i++) {
+          unsigned s = seq0 + i;
+          int my = map_index(r0 + i, P.ny, P.bc[2], P.bc[3]);
+          tma_load_row(tml, smem_u32(fring + (size_t)(s % S) * QM * NC), smem_u32(&bars[s % S]), x0 - 4 + XPAD, my, row_bytes);
+          issued_end = s + 1;
+        }
+      }
+
+      // register pipelines per own column: U and primitives of rows r-1, r-2; nu
+      // of rows r-1..r-3; post_0, post_1, post_3 of row r-3; post_2 of rows r-4, r-3
+      R U1[CPT][M], U2[CPT][M], p0[CPT][M], p1o[CPT][M], p3o[CPT][M], p2a[CPT][M], p2b[CPT][M];
+      Prim<R> w1[CPT], w2[CPT];
+      R nu1[CPT], nu2[CPT], nu3[CPT];
+  #pragma unroll
+      for (int j = 0; j < CPT; j++) {
+  #pragma unroll
+        for (int c = 0; c < M; c++) {
+          U1[j][c] = U2[j][c] = R(1);
+          p0[j][c] = p1o[j][c] = p3o[j][c] = p2a[j][c] = p2b[j][c] = R(0);
+        }
+        w1[j] = primitives<SYS, 2, R>(K, U1[j]);
+        w2[j] = w1[j];
+        nu1[j] = nu2[j] = nu3[j] = R(0);
+      }
+
+  #pragma unroll 2
+      for (int r = r0; r <= r1; r++) {
+        const unsigned sidx = seq0 + (unsigned)(r - r0);
+        cur = sidx;
+        if (t == 0 && r + PREF <= r1) {
+          unsigned s = sidx + PREF;
+          int my = map_index(r + PREF, P.ny, P.bc[2], P.bc[3]);
+          tma_load_row(tml, smem_u32(fring + (size_t)(s % S) * QM * NC), smem_u32(&bars[s % S]), x0 - 4 + XPAD, my, row_bytes);
+          issued_end = s + 1;
+        }
+        if (!mbar_wait_bounded(smem_u32(&bars[sidx % S]), (sidx / S) & 1u)) *s_abort = 1;
+        const R* frow = fring + (size_t)(sidx % S) * QM * NC;
+        // B: moments of row r
+        R Ur[CPT][M];
+  #pragma unroll
+        for (int c = 0; c < M; c++) {
+  #pragma unroll
+          for (int j = 0; j < CPT; j++) Ur[j][c] = R(0);
+  #pragma unroll
+          for (int k = 0; k < Q; k++) {
+            if constexpr (CPT == 2) {
+              auto v = *reinterpret_cast<const typename Vec2<R>::T*>(frow + (k * M + c) * NC + sc0);
+              Ur[0][c] += v.x;
+              Ur[1][c] += v.y;
+            } else {
+              Ur[0][c] += frow[(k * M + c) * NC + sc0];
+            }
+          }
+  #pragma unroll
+          for (int j = 0; j < CPT; j++) Usm[((r & 1) * M + c) * NC + sc0 + j] = Ur[j][c];
+        }
+        // C: indicator of row r-1 (edge lanes use clamped neighbours; no valid
+        // output depends on them)
+        R colsum[CPT];
+        {
+          const R* Uprev = Usm + ((r - 1) & 1) * M * NC;
+  #pragma unroll
+          for (int j = 0; j < CPT; j++) {
+            R dm[M], dp[M];
+  #pragma unroll
+            for (int c = 0; c < M; c++) {
+              R left = j > 0 ? U1[j > 0 ? j - 1 : 0][c] : Uprev[c * NC + scl];
+              R right = j < CPT - 1 ? U1[j < CPT - 1 ? j + 1 : 0][c] : Uprev[c * NC + scr];
+              dm[c] = U1[j][c] - left;
+              dp[c] = right - U1[j][c];
+            }
+            R nun = theta_sum<SYS, 2, R>(K, w1[j], 0, dm, dp);
+  #pragma unroll
+            for (int c = 0; c < M; c++) {
+              dm[c] = U1[j][c] - U2[j][c];
+              dp[c] = Ur[j][c] - U1[j][c];
+            }
+            nun += theta_sum<SYS, 2, R>(K, w1[j], 1, dm, dp);
+            nu3[j] = nu2[j];
+            nu2[j] = nu1[j];
+            nu1[j] = nun;
+            colsum[j] = nu1[j] + nu2[j] + nu3[j];
+            colsm[sc0 + j] = colsum[j];
+          }
+        }
+        // the staging row is free once the previous row's store has read it
+        if (t == 0) tma_store_wait_read();
+        __syncthreads();
+        if (*s_abort) {
+          aborted = true;
+          break;
+        }
+        // D: omega and post-collision values of row r-2 (state U2, primitives w2)
+        const R* f2 = fring + (size_t)(((sidx % S) + S - 2) % S) * QM * NC;
+        R post[CPT][Q][M];
+  #pragma unroll
+        for (int j = 0; j < CPT; j++) {
+          R cl = j > 0 ? colsum[j > 0 ? j - 1 : 0] : colsm[scl];
+          R cr = j < CPT - 1 ? colsum[j < CPT - 1 ? j + 1 : 0] : colsm[scr];
+          R om = fixed_omega ? om_fixed : R(1) + fdiv(R(1), R(1) + (cl + colsum[j] + cr));
+          R Fx[M], Fy[M], Sr[M];
+          flux<SYS, 2, R>(K, U2[j], w2[j], 0, Fx);
+          flux<SYS, 2, R>(K, U2[j], w2[j], 1, Fy);
+          if constexpr (SRC) {
+            const int my2 = map_index(r - 2, P.ny, P.bc[2], P.bc[3]);
+            source<SYS, 2, R>(K, U2[j], xr_ghost[j], K.yb + R(my2) * K.dx, Sr);
+          }
+  #pragma unroll
+          for (int c = 0; c < M; c++) {
+            R feq[Q];
+            feq[0] = a0 * U2[j][c];
+            feq[1] = (al0 * U2[j][c] + Fx[c]) * inv2l;
+            feq[2] = (al1 * U2[j][c] + Fy[c]) * inv2l;
+            feq[3] = (al0 * U2[j][c] - Fx[c]) * inv2l;
+            feq[4] = (al1 * U2[j][c] - Fy[c]) * inv2l;
+  #pragma unroll
+            for (int k = 0; k < Q; k++) {
+              R fk = f2[(k * M + c) * NC + sc0 + j];
+              R pk = fk - om * (fk - feq[k]);
+              if constexpr (SRC) pk += hdt * akk[k] * Sr[c];
+              post[j][k][c] = pk;
+            }
+          }
+        }
+        // neighbours need post_1 of the last own column and post_3 of the first
+        R* p13w = p13 + (((r - 2) & 1) * 2) * M * FT;
+  #pragma unroll
+        for (int c = 0; c < M; c++) {
+          p13w[c * FT + t] = post[CPT - 1][1][c];
+          p13w[(M + c) * FT + t] = post[0][3][c];
+        }
+        // E: pull streaming into row r-3, implicit moment, second half-source
+        const int y = r - 3;
+        const bool row_out = y >= yb && y < ye;
+        const R* p13r = p13 + (((r - 3) & 1) * 2) * M * FT;
+  #pragma unroll
+        for (int j = 0; j < CPT; j++) {
+          R Fk[Q][M], Ubar[M];
+  #pragma unroll
+          for (int c = 0; c < M; c++) {
+            Fk[0][c] = p0[j][c];
+            Fk[1][c] = j > 0 ? p1o[j > 0 ? j - 1 : 0][c] : p13r[c * FT + tl];
+            Fk[2][c] = p2a[j][c];
+            Fk[3][c] = j < CPT - 1 ? p3o[j < CPT - 1 ? j + 1 : 0][c] : p13r[(M + c) * FT + tr];
+            Fk[4][c] = post[j][4][c];
+            R s = R(0);
+  #pragma unroll
+            for (int k = 0; k < Q; k++) s += Fk[k][c];
+            Ubar[c] = s;
+          }
+          R Us[M];  // moments of the stored f^{n+1}, summed k = 0..Q-1 as the next step does
+          if constexpr (SRC) {
+            R Un[M], Sn[M];
+            const R yr = K.yb + R(y) * K.dx;
+            unsigned stn = implicit_moment<SYS, 2, R>(K, Ubar, xr_out[j], yr, cc.dt, hdt, Un);
+            source<SYS, 2, R>(K, Un, xr_out[j], yr, Sn);
+  #pragma unroll
+            for (int c = 0; c < M; c++) Us[c] = R(0);
+  #pragma unroll
+            for (int k = 0; k < Q; k++)
+  #pragma unroll
+              for (int c = 0; c < M; c++) {
+                Fk[k][c] += hdt * akk[k] * Sn[c];
+                Us[c] += Fk[k][c];
+              }
+            if (outc[j] && row_out) st |= stn;
+          } else {
+  #pragma unroll
+            for (int c = 0; c < M; c++) Us[c] = Ubar[c];
+          }
+          Prim<R> wn = primitives<SYS, 2, R>(K, Us);
+          const int so = sc0 + j - 4;  // column in the staged output row
+          if (so >= 0 && so < WOUT) {
+  #pragma unroll
+            for (int k = 0; k < Q; k++)
+  #pragma unroll
+              for (int c = 0; c < M; c++) stage[(k * M + c) * WOUT + so] = Fk[k][c];
+          }
+          if (outc[j] && row_out) {
+            if (gx[j] >= nxs) {  // tail columns outside the bulk store
+              R* base = fout + (long long)y * P.pitch + XPAD + gx[j];
+  #pragma unroll
+              for (int k = 0; k < Q; k++)
+  #pragma unroll
+                for (int c = 0; c < M; c++) base[(long long)(k * M + c) * P.plane] = Fk[k][c];
+            }
+            sp0 = rmax(sp0, max_speed<SYS, 2, R>(K, wn, 0));
+            sp1 = rmax(sp1, max_speed<SYS, 2, R>(K, wn, 1));
+  #pragma unroll
+            for (int c = 0; c < M; c++) acc[c].add(Us[c]);
+            st |= state_status<SYS, 2, R>(Us, wn);
+          }
+        }
+        fence_proxy_async();  // staged row visible to the TMA store
+  #pragma unroll
+        for (int j = 0; j < CPT; j++) {
+          w2[j] = w1[j];
+  #pragma unroll
+          for (int c = 0; c < M; c++) {
+            p0[j][c] = post[j][0][c];
+            p1o[j][c] = post[j][1][c];
+            p3o[j][c] = post[j][3][c];
+            p2a[j][c] = p2b[j][c];
+            p2b[j][c] = post[j][2][c];
+            U2[j][c] = U1[j][c];
+            U1[j][c] = Ur[j][c];
+          }
+          w1[j] = primitives<SYS, 2, R>(K, U1[j]);
+        }
+        __syncthreads();
+        if (t == 0 && row_out && x0 < nxs) tma_store_row(tms, smem_u32(stage), x0, y);
+        if (row_out && has_pads) {
+          R* base = fout + (long long)y * P.pitch + XPAD;
+  #pragma unroll
+          for (int i = 0; i < NPAD; i++)
+            if (pad_sidx[i] >= 0) base[pad_goff[i]] = stage[pad_sidx[i]];
+        }
+      }
+}
+
+template <int SYS, class R, int PREF, int CPT>
+__device__ __forceinline__ void pipe2d_init(Pipe2D& pp, unsigned char* smem_raw, int* s_abort) {
+  using L = Smem2D<Fields<SYS, 2>::M, R, PREF, CPT>;
+  unsigned long long* bars = (unsigned long long*)(smem_raw + L::bar_off);
+  pp.smem = smem_raw;
+  pp.s_abort = s_abort;
+  pp.seq = pp.issued_end = pp.cur = 0;
+  pp.aborted = false;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < L::S; i++) mbar_init(smem_u32(&bars[i]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *s_abort = 0;
+  }
+  __syncthreads();
+}
+
+// Before the CTA exits: let every row load it issued land (after an abort) and
+// every bulk store finish.
+template <int SYS, class R, int PREF, int CPT>
+__device__ __forceinline__ void pipe2d_drain(Pipe2D& pp) {
+  using L = Smem2D<Fields<SYS, 2>::M, R, PREF, CPT>;
+  unsigned long long* bars = (unsigned long long*)(pp.smem + L::bar_off);
+  if (threadIdx.x == 0) {
+    if (pp.aborted)
+      for (unsigned s = pp.cur; s < pp.issued_end; s++) mbar_wait_bounded(smem_u32(&bars[s % L::S]), (s / L::S) & 1u);
+    tma_store_wait_all();
+  }
+  __syncthreads();
+}
+
+// Single lattice.  Work split: the strips x rows of the grid are ordered
+// band-major (band of `band` rows, strip, row) and cut into gridDim equal
 // contiguous chunks (one resident wave, every CTA the same number of rows);
-// a chunk covers one or two strip segments.  Each output row is staged in
-// shared memory and written with one TMA bulk store covering columns
-// [0, nxs), nxs = nx rounded down to 16 bytes: the bulk store writes whole
-// 16-byte granules, so the last columns and the ghost columns behind them
-// are written with plain stores instead (the ghost columns by the whole CTA,
-// from the staged row).
+// neighbouring strips of a band run side by side, so the halo sectors they
+// share hit in L2.
 template <int SYS, class R, int PREF, int CPT>
 __global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensorMap tl0,
                                                 const __grid_constant__ CUtensorMap tl1,
@@ -142,19 +507,9 @@ __global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensor
                                                 const __grid_constant__ CUtensorMap ts1, DevParams P,
                                                 R* const* buf, Ctl* ctl, int slot, double* partials, int strips,
                                                 int nxs, int band) {
-  constexpr int M = Fields<SYS, 2>::M, Q = 5, QM = Q * M;
-  constexpr bool SRC = HasSource<SYS>::value;
-  using L = Smem2D<M, R, PREF, CPT>;
-  constexpr int S = L::S, NC = L::NC, WOUT = L::WOUT;
+  constexpr int M = Fields<SYS, 2>::M;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  R* fring = (R*)smem_raw;
-  R* Usm = (R*)(smem_raw + L::f_bytes);
-  R* colsm = (R*)(smem_raw + L::f_bytes + L::u_bytes);
-  R* p13 = (R*)(smem_raw + L::f_bytes + L::u_bytes + L::c_bytes);
-  R* stage = (R*)(smem_raw + L::o_off);
-  unsigned long long* bars = (unsigned long long*)(smem_raw + L::bar_off);
   __shared__ int s_abort;
-
   const int t = threadIdx.x;
   const StepCoef cf = step_coef<2>(P, ctl, slot);
   if (!cf.active) {
@@ -162,48 +517,24 @@ __global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensor
     return;
   }
   const int par = ctl->parity[slot];
-  const CUtensorMap* tml = par ? &tl1 : &tl0;   // loads from f^n (padded rows)
-  const CUtensorMap* tms = par ? &ts0 : &ts1;   // stores to f^{n+1} (interior columns)
+  const CUtensorMap* tml = par ? &tl1 : &tl0;  // loads from f^n (padded rows)
+  const CUtensorMap* tms = par ? &ts0 : &ts1;  // stores to f^{n+1} (interior columns)
   R* fout = buf[par ^ 1];
-
-  if (t == 0) {
-    for (int i = 0; i < S; i++) mbar_init(smem_u32(&bars[i]), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_abort = 0;
-  }
-  __syncthreads();
-
+  Pipe2D pp;
+  pipe2d_init<SYS, R, PREF, CPT>(pp, smem_raw, &s_abort);
   const Phys<R> K = make_phys<R>(P);
-  const R a0 = R(cf.a0), inv2l = R(1.0 / (2.0 * cf.lam)), hdt = R(0.5 * cf.dt);
-  const R al0 = R(cf.alpha[0]), al1 = R(cf.alpha[1]);
-  const R akk[5] = {R(cf.a0), R(cf.aj[0]), R(cf.aj[1]), R(cf.aj[0]), R(cf.aj[1])};
-  const bool fixed_omega = P.omega_mode == 1;
-  const R om_fixed = R(P.omega_fixed);
-  const uint32_t row_bytes = (uint32_t)(QM * NC * sizeof(R));
-  const int sc0 = t * CPT;                              // first own column
-  const int scl = sc0 > 0 ? sc0 - 1 : 0;                // left neighbour column (clamped)
-  const int scr = sc0 + CPT < NC ? sc0 + CPT : NC - 1;  // right neighbour column (clamped)
-  const int tl = t > 0 ? t - 1 : 0, tr = t < FT - 1 ? t + 1 : FT - 1;
-
+  const Coef2D<R> cc = make_coef2d<R>(cf, P);
   R sp0 = R(0), sp1 = R(0);
   Acc<R> acc[M];
 #pragma unroll
   for (int c = 0; c < M; c++) acc[c].init();
   unsigned st = 0u;
 
-  // band-major work order: (band of `band` rows, strip, row); CTA b takes the
-  // b-th of gridDim equal chunks, so neighbouring strips of a band run side by
-  // side and every CTA has the same number of rows
   const long long total = (long long)strips * P.ny;
   const long long wb = total * blockIdx.x / gridDim.x, we = total * (blockIdx.x + 1) / gridDim.x;
   const int nbands = (P.ny + band - 1) / band;
   const int last_rows = P.ny - (nbands - 1) * band;
-  unsigned seq = 0;        // row loads of this CTA so far (ring slot / phase)
-  unsigned issued_end = 0; // one past the last row load issued (thread 0)
-  unsigned cur = 0;
-  bool aborted = false;
-
-  for (long long w = wb; w < we && !aborted;) {
+  for (long long w = wb; w < we && !pp.aborted;) {
     const int b = (int)(w / ((long long)strips * band));
     const int rb = b == nbands - 1 ? last_rows : band;
     const long long local = w - (long long)b * strips * band;
@@ -211,278 +542,10 @@ __global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensor
     const int yb = b * band + (int)(local % rb);
     const int ye = (int)min((long long)(b * band + rb), (long long)yb + (we - w));
     w += ye - yb;
-    const int x0 = strip * WOUT;
-    int gx[CPT];
-    bool outc[CPT];
-    R xr_ghost[CPT], xr_out[CPT];
-#pragma unroll
-    for (int j = 0; j < CPT; j++) {
-      const int sc = sc0 + j;
-      gx[j] = x0 - 4 + sc;
-      outc[j] = sc >= 4 && sc < NC - 4 && gx[j] < P.nx;
-      const int mx = map_index(gx[j], P.nx, P.bc[0], P.bc[1]);
-      xr_ghost[j] = K.xb + R(mx) * K.dx;  // a ghost node sits where the node it copies sits
-      xr_out[j] = K.xb + R(gx[j]) * K.dx;
-    }
-    // ghost columns whose source node lies in this strip's output range: the
-    // CTA writes them after each row from the staged output
-    const int xe = min(x0 + WOUT, P.nx);
-    bool has_pads = false;
-#pragma unroll
-    for (int p = 0; p < 2 * NGHOST; p++) {
-      int src = map_index(p < NGHOST ? p - NGHOST : P.nx + (p - NGHOST), P.nx, P.bc[0], P.bc[1]);
-      has_pads |= src >= x0 && src < xe;
-    }
-    // this thread's share of the ghost-column stores (item = ghost column x
-    // of plane q): offset from the row base and index into the staged row
-    constexpr int NPAD = (2 * NGHOST * QM + FT - 1) / FT;
-    long long pad_goff[NPAD];
-    int pad_sidx[NPAD];
-#pragma unroll
-    for (int i = 0; i < NPAD; i++) {
-      const int item = t + i * FT;
-      pad_sidx[i] = -1;
-      pad_goff[i] = 0;
-      if (item < 2 * NGHOST * QM) {
-        const int p = item / QM, q = item % QM;
-        const int x = p < NGHOST ? p - NGHOST : P.nx + (p - NGHOST);
-        const int src = map_index(x, P.nx, P.bc[0], P.bc[1]);
-        if (src >= x0 && src < xe) {
-          pad_sidx[i] = q * WOUT + (src - x0);
-          pad_goff[i] = (long long)q * P.plane + x;
-        }
-      }
-    }
-    const int r0 = yb - 3, r1 = ye + 2;
-    const unsigned seq0 = seq;
-    seq += (unsigned)(r1 - r0 + 1);
-    if (t == 0) {
-      for (int i = 0; i < PREF && r0 + i <= r1; i++) {
-        unsigned s = seq0 + i;
-        int my = map_index(r0 + i, P.ny, P.bc[2], P.bc[3]);
-        tma_load_row(tml, smem_u32(fring + (size_t)(s % S) * QM * NC), smem_u32(&bars[s % S]), x0 - 4 + XPAD, my, row_bytes);
-        issued_end = s + 1;
-      }
-    }
-
-    // register pipelines per own column: U and primitives of rows r-1, r-2; nu
-    // of rows r-1..r-3; post_0, post_1, post_3 of row r-3; post_2 of rows r-4, r-3
-    R U1[CPT][M], U2[CPT][M], p0[CPT][M], p1o[CPT][M], p3o[CPT][M], p2a[CPT][M], p2b[CPT][M];
-    Prim<R> w1[CPT], w2[CPT];
-    R nu1[CPT], nu2[CPT], nu3[CPT];
-#pragma unroll
-    for (int j = 0; j < CPT; j++) {
-#pragma unroll
-      for (int c = 0; c < M; c++) {
-        U1[j][c] = U2[j][c] = R(1);
-        p0[j][c] = p1o[j][c] = p3o[j][c] = p2a[j][c] = p2b[j][c] = R(0);
-      }
-      w1[j] = primitives<SYS, 2, R>(K, U1[j]);
-      w2[j] = w1[j];
-      nu1[j] = nu2[j] = nu3[j] = R(0);
-    }
-
-#pragma unroll 2
-    for (int r = r0; r <= r1; r++) {
-      const unsigned sidx = seq0 + (unsigned)(r - r0);
-      cur = sidx;
-      if (t == 0 && r + PREF <= r1) {
-        unsigned s = sidx + PREF;
-        int my = map_index(r + PREF, P.ny, P.bc[2], P.bc[3]);
-        tma_load_row(tml, smem_u32(fring + (size_t)(s % S) * QM * NC), smem_u32(&bars[s % S]), x0 - 4 + XPAD, my, row_bytes);
-        issued_end = s + 1;
-      }
-      if (!mbar_wait_bounded(smem_u32(&bars[sidx % S]), (sidx / S) & 1u)) s_abort = 1;
-      const R* frow = fring + (size_t)(sidx % S) * QM * NC;
-      // B: moments of row r
-      R Ur[CPT][M];
-#pragma unroll
-      for (int c = 0; c < M; c++) {
-#pragma unroll
-        for (int j = 0; j < CPT; j++) Ur[j][c] = R(0);
-#pragma unroll
-        for (int k = 0; k < Q; k++) {
-          if constexpr (CPT == 2) {
-            auto v = *reinterpret_cast<const typename Vec2<R>::T*>(frow + (k * M + c) * NC + sc0);
-            Ur[0][c] += v.x;
-            Ur[1][c] += v.y;
-          } else {
-            Ur[0][c] += frow[(k * M + c) * NC + sc0];
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < CPT; j++) Usm[((r & 1) * M + c) * NC + sc0 + j] = Ur[j][c];
-      }
-      // C: indicator of row r-1 (edge lanes use clamped neighbours; no valid
-      // output depends on them)
-      R colsum[CPT];
-      {
-        const R* Uprev = Usm + ((r - 1) & 1) * M * NC;
-#pragma unroll
-        for (int j = 0; j < CPT; j++) {
-          R dm[M], dp[M];
-#pragma unroll
-          for (int c = 0; c < M; c++) {
-            R left = j > 0 ? U1[j > 0 ? j - 1 : 0][c] : Uprev[c * NC + scl];
-            R right = j < CPT - 1 ? U1[j < CPT - 1 ? j + 1 : 0][c] : Uprev[c * NC + scr];
-            dm[c] = U1[j][c] - left;
-            dp[c] = right - U1[j][c];
-          }
-          R nun = theta_sum<SYS, 2, R>(K, w1[j], 0, dm, dp);
-#pragma unroll
-          for (int c = 0; c < M; c++) {
-            dm[c] = U1[j][c] - U2[j][c];
-            dp[c] = Ur[j][c] - U1[j][c];
-          }
-          nun += theta_sum<SYS, 2, R>(K, w1[j], 1, dm, dp);
-          nu3[j] = nu2[j];
-          nu2[j] = nu1[j];
-          nu1[j] = nun;
-          colsum[j] = nu1[j] + nu2[j] + nu3[j];
-          colsm[sc0 + j] = colsum[j];
-        }
-      }
-      // the staging row is free once the previous row's store has read it
-      if (t == 0) tma_store_wait_read();
-      __syncthreads();
-      if (s_abort) {
-        aborted = true;
-        break;
-      }
-      // D: omega and post-collision values of row r-2 (state U2, primitives w2)
-      const R* f2 = fring + (size_t)(((sidx % S) + S - 2) % S) * QM * NC;
-      R post[CPT][Q][M];
-#pragma unroll
-      for (int j = 0; j < CPT; j++) {
-        R cl = j > 0 ? colsum[j > 0 ? j - 1 : 0] : colsm[scl];
-        R cr = j < CPT - 1 ? colsum[j < CPT - 1 ? j + 1 : 0] : colsm[scr];
-        R om = fixed_omega ? om_fixed : R(1) + fdiv(R(1), R(1) + (cl + colsum[j] + cr));
-        R Fx[M], Fy[M], Sr[M];
-        flux<SYS, 2, R>(K, U2[j], w2[j], 0, Fx);
-        flux<SYS, 2, R>(K, U2[j], w2[j], 1, Fy);
-        if constexpr (SRC) {
-          const int my2 = map_index(r - 2, P.ny, P.bc[2], P.bc[3]);
-          source<SYS, 2, R>(K, U2[j], xr_ghost[j], K.yb + R(my2) * K.dx, Sr);
-        }
-#pragma unroll
-        for (int c = 0; c < M; c++) {
-          R feq[Q];
-          feq[0] = a0 * U2[j][c];
-          feq[1] = (al0 * U2[j][c] + Fx[c]) * inv2l;
-          feq[2] = (al1 * U2[j][c] + Fy[c]) * inv2l;
-          feq[3] = (al0 * U2[j][c] - Fx[c]) * inv2l;
-          feq[4] = (al1 * U2[j][c] - Fy[c]) * inv2l;
-#pragma unroll
-          for (int k = 0; k < Q; k++) {
-            R fk = f2[(k * M + c) * NC + sc0 + j];
-            R pk = fk - om * (fk - feq[k]);
-            if constexpr (SRC) pk += hdt * akk[k] * Sr[c];
-            post[j][k][c] = pk;
-          }
-        }
-      }
-      // neighbours need post_1 of the last own column and post_3 of the first
-      R* p13w = p13 + (((r - 2) & 1) * 2) * M * FT;
-#pragma unroll
-      for (int c = 0; c < M; c++) {
-        p13w[c * FT + t] = post[CPT - 1][1][c];
-        p13w[(M + c) * FT + t] = post[0][3][c];
-      }
-      // E: pull streaming into row r-3, implicit moment, second half-source
-      const int y = r - 3;
-      const bool row_out = y >= yb && y < ye;
-      const R* p13r = p13 + (((r - 3) & 1) * 2) * M * FT;
-#pragma unroll
-      for (int j = 0; j < CPT; j++) {
-        R Fk[Q][M], Ubar[M];
-#pragma unroll
-        for (int c = 0; c < M; c++) {
-          Fk[0][c] = p0[j][c];
-          Fk[1][c] = j > 0 ? p1o[j > 0 ? j - 1 : 0][c] : p13r[c * FT + tl];
-          Fk[2][c] = p2a[j][c];
-          Fk[3][c] = j < CPT - 1 ? p3o[j < CPT - 1 ? j + 1 : 0][c] : p13r[(M + c) * FT + tr];
-          Fk[4][c] = post[j][4][c];
-          R s = R(0);
-#pragma unroll
-          for (int k = 0; k < Q; k++) s += Fk[k][c];
-          Ubar[c] = s;
-        }
-        R Us[M];  // moments of the stored f^{n+1}, summed k = 0..Q-1 as the next step does
-        if constexpr (SRC) {
-          R Un[M], Sn[M];
-          const R yr = K.yb + R(y) * K.dx;
-          unsigned stn = implicit_moment<SYS, 2, R>(K, Ubar, xr_out[j], yr, cf.dt, hdt, Un);
-          source<SYS, 2, R>(K, Un, xr_out[j], yr, Sn);
-#pragma unroll
-          for (int c = 0; c < M; c++) Us[c] = R(0);
-#pragma unroll
-          for (int k = 0; k < Q; k++)
-#pragma unroll
-            for (int c = 0; c < M; c++) {
-              Fk[k][c] += hdt * akk[k] * Sn[c];
-              Us[c] += Fk[k][c];
-            }
-          if (outc[j] && row_out) st |= stn;
-        } else {
-#pragma unroll
-          for (int c = 0; c < M; c++) Us[c] = Ubar[c];
-        }
-        Prim<R> wn = primitives<SYS, 2, R>(K, Us);
-        const int so = sc0 + j - 4;  // column in the staged output row
-        if (so >= 0 && so < WOUT) {
-#pragma unroll
-          for (int k = 0; k < Q; k++)
-#pragma unroll
-            for (int c = 0; c < M; c++) stage[(k * M + c) * WOUT + so] = Fk[k][c];
-        }
-        if (outc[j] && row_out) {
-          if (gx[j] >= nxs) {  // tail columns outside the bulk store
-            R* base = fout + (long long)y * P.pitch + XPAD + gx[j];
-#pragma unroll
-            for (int k = 0; k < Q; k++)
-#pragma unroll
-              for (int c = 0; c < M; c++) base[(long long)(k * M + c) * P.plane] = Fk[k][c];
-          }
-          sp0 = rmax(sp0, max_speed<SYS, 2, R>(K, wn, 0));
-          sp1 = rmax(sp1, max_speed<SYS, 2, R>(K, wn, 1));
-#pragma unroll
-          for (int c = 0; c < M; c++) acc[c].add(Us[c]);
-          st |= state_status<SYS, 2, R>(Us, wn);
-        }
-      }
-      fence_proxy_async();  // staged row visible to the TMA store
-#pragma unroll
-      for (int j = 0; j < CPT; j++) {
-        w2[j] = w1[j];
-#pragma unroll
-        for (int c = 0; c < M; c++) {
-          p0[j][c] = post[j][0][c];
-          p1o[j][c] = post[j][1][c];
-          p3o[j][c] = post[j][3][c];
-          p2a[j][c] = p2b[j][c];
-          p2b[j][c] = post[j][2][c];
-          U2[j][c] = U1[j][c];
-          U1[j][c] = Ur[j][c];
-        }
-        w1[j] = primitives<SYS, 2, R>(K, U1[j]);
-      }
-      __syncthreads();
-      if (t == 0 && row_out && x0 < nxs) tma_store_row(tms, smem_u32(stage), x0, y);
-      if (row_out && has_pads) {
-        R* base = fout + (long long)y * P.pitch + XPAD;
-#pragma unroll
-        for (int i = 0; i < NPAD; i++)
-          if (pad_sidx[i] >= 0) base[pad_goff[i]] = stage[pad_sidx[i]];
-      }
-    }
+    run_segment2d<SYS, R, PREF, CPT>(pp, tml, tms, fout, P, K, cc, strip, yb, ye, nxs, sp0, sp1, acc, st);
   }
-  if (t == 0) {
-    if (aborted)  // let every row copy this CTA issued land before it exits
-      for (unsigned s = cur; s < issued_end; s++) mbar_wait_bounded(smem_u32(&bars[s % S]), (s / S) & 1u);
-    tma_store_wait_all();
-  }
-  if (aborted) st |= ST_TIMEOUT;
-  __syncthreads();
+  pipe2d_drain<SYS, R, PREF, CPT>(pp);
+  if (pp.aborted) st |= ST_TIMEOUT;
   fused_side_outputs<M, R>(sp0, sp1, acc, ctl, (slot + 1) % 3, partials, st);
   if (blockIdx.x == 0 && t == 0) advance_ctl<2>(ctl, slot, cf);
 }
@@ -615,13 +678,39 @@ inline EncodeTiledFn encode_fn() {
   return fn;
 }
 
+// TMA descriptors of both distribution buffers of one lattice: loads of
+// padded row boxes {nc columns, 1 row, qm planes}; bulk stores of the interior
+// columns [0, nxs) in boxes of wout columns.  Also sets strips and nxs.
+template <class R>
+inline int encode_maps(FusedPlan& fp, const DevParams& P, void* const* fbuf, int qm, int nc, int wout) {
+  fp.strips = (P.nx + wout - 1) / wout;
+  fp.nxs = P.nx - P.nx % (int)(16 / sizeof(R));
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return -1;
+  for (int b = 0; b < 2; b++) {
+    cuuint64_t strides[2] = {(cuuint64_t)P.pitch * sizeof(R), (cuuint64_t)P.plane * sizeof(R)};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    const CUtensorMapDataType dt = sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    cuuint64_t ldims[3] = {(cuuint64_t)(P.nx + 2 * XPAD), (cuuint64_t)P.ny, (cuuint64_t)qm};
+    cuuint32_t lbox[3] = {(cuuint32_t)nc, 1u, (cuuint32_t)qm};
+    CUresult r = enc(&fp.tm[b], dt, 3, fbuf[b], ldims, strides, lbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return -1;
+    cuuint64_t sdims[3] = {(cuuint64_t)(fp.nxs > 0 ? fp.nxs : 1), (cuuint64_t)P.ny, (cuuint64_t)qm};
+    cuuint32_t sbox[3] = {(cuuint32_t)wout, 1u, (cuuint32_t)qm};
+    r = enc(&fp.tms[b], dt, 3, (R*)fbuf[b] + XPAD, sdims, strides, sbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return -1;
+  }
+  return 0;
+}
+
 template <int SYS, class R, int CPT>
 inline int fused2d_prepare(FusedPlan& fp, const DevParams& P, void* const* fbuf, int sms) {
   constexpr int M = Fields<SYS, 2>::M, QM = 5 * M;
   using L = Smem2D<M, R, fpref<CPT>(), CPT>;
   fp.cpt = CPT;
   fp.strips = (P.nx + L::WOUT - 1) / L::WOUT;
-  fp.nxs = P.nx - P.nx % (int)(16 / sizeof(R));
   fp.smem = (int)L::total;
   auto kern = k_fused2d<SYS, R, fpref<CPT>(), CPT>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, fp.smem) != cudaSuccess) return -1;
@@ -636,23 +725,7 @@ inline int fused2d_prepare(FusedPlan& fp, const DevParams& P, void* const* fbuf,
   fp.blocks = (int)(slots < cap ? slots : cap);
   long long chunk = (total + fp.blocks - 1) / fp.blocks;
   fp.band = (int)(chunk < 16 ? 16 : (chunk > P.ny ? P.ny : chunk));
-  EncodeTiledFn enc = encode_fn();
-  if (!enc) return -1;
-  for (int b = 0; b < 2; b++) {
-    cuuint64_t strides[2] = {(cuuint64_t)P.pitch * sizeof(R), (cuuint64_t)P.plane * sizeof(R)};
-    cuuint32_t estr[3] = {1u, 1u, 1u};
-    const CUtensorMapDataType dt = sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-    cuuint64_t ldims[3] = {(cuuint64_t)(P.nx + 2 * XPAD), (cuuint64_t)P.ny, (cuuint64_t)QM};
-    cuuint32_t lbox[3] = {(cuuint32_t)L::NC, 1u, (cuuint32_t)QM};
-    CUresult r = enc(&fp.tm[b], dt, 3, fbuf[b], ldims, strides, lbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return -1;
-    cuuint64_t sdims[3] = {(cuuint64_t)(fp.nxs > 0 ? fp.nxs : 1), (cuuint64_t)P.ny, (cuuint64_t)QM};
-    cuuint32_t sbox[3] = {(cuuint32_t)L::WOUT, 1u, (cuuint32_t)QM};
-    r = enc(&fp.tms[b], dt, 3, (R*)fbuf[b] + XPAD, sdims, strides, sbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return -1;
-  }
+  return encode_maps<R>(fp, P, fbuf, QM, L::NC, L::WOUT);
   return 0;
 }
 

@@ -1,0 +1,91 @@
+// Host helpers shared by the entry points: problem validation and the
+// translation of an lbmh_problem into the kernels' DevParams.
+#pragma once
+#include <math.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/lbmh.h"
+#include "common.cuh"
+
+namespace lbmh {
+
+inline int nfields(int sys, int dim) {
+  switch (sys) {
+    case SYS_ADV: return 1;
+    case SYS_EULER: return dim + 2;
+    case SYS_SWE: return dim + 1;
+    case SYS_REACT: return dim + 3;
+  }
+  return -1;
+}
+
+inline int validate(const lbmh_problem* p, std::string& why) {
+  if (!p) { why = "problem is NULL"; return LBMH_ERR_INVALID_ARG; }
+  if (p->system == LBMH_LINEAR) { why = "LBMH_LINEAR is provided by the oracle only"; return LBMH_ERR_UNSUPPORTED; }
+  if (p->system < 0 || p->system > 3) { why = "unknown system"; return LBMH_ERR_INVALID_ARG; }
+  if (p->dim != 1 && p->dim != 2) { why = "dim must be 1 or 2"; return LBMH_ERR_INVALID_ARG; }
+  if (p->nx < 1 || (p->dim == 2 && p->ny < 1)) { why = "grid must have at least one node"; return LBMH_ERR_INVALID_ARG; }
+  if ((long long)p->nx * (p->dim == 2 ? p->ny : 1) > (1ll << 34)) { why = "grid too large"; return LBMH_ERR_INVALID_ARG; }
+  if (!(p->x1 > p->x0)) { why = "x1 must exceed x0"; return LBMH_ERR_INVALID_ARG; }
+  for (int s = 0; s < 4; s++)
+    if (p->bc[s] != LBMH_BC_PERIODIC && p->bc[s] != LBMH_BC_OUTFLOW) { why = "bad boundary condition"; return LBMH_ERR_INVALID_ARG; }
+  if ((p->bc[0] == LBMH_BC_PERIODIC) != (p->bc[1] == LBMH_BC_PERIODIC)) { why = "periodic x boundaries must pair"; return LBMH_ERR_INVALID_ARG; }
+  if (p->dim == 2) {
+    if ((p->bc[2] == LBMH_BC_PERIODIC) != (p->bc[3] == LBMH_BC_PERIODIC)) { why = "periodic y boundaries must pair"; return LBMH_ERR_INVALID_ARG; }
+    double dx = (p->x1 - p->x0) / p->nx, dy = (p->y1 - p->y0) / p->ny;
+    if (!(fabs(dx - dy) <= 1e-12 * dx)) { why = "2D mesh must satisfy dx == dy (Section 2.2.2)"; return LBMH_ERR_INVALID_ARG; }
+  }
+  if (!(p->cfl > 0.0)) { why = "cfl must be positive"; return LBMH_ERR_INVALID_ARG; }
+  if (!(p->eps >= 0.0)) { why = "eps must be non-negative"; return LBMH_ERR_INVALID_ARG; }
+  if (p->precision != LBMH_FP64 && p->precision != LBMH_FP32) { why = "bad precision"; return LBMH_ERR_INVALID_ARG; }
+  if (p->kernel < 0 || p->kernel > 2) { why = "bad kernel choice"; return LBMH_ERR_INVALID_ARG; }
+  if (p->omega_mode != 0 && p->omega_mode != 1) { why = "bad omega mode"; return LBMH_ERR_INVALID_ARG; }
+  if ((p->system == LBMH_EULER || p->system == LBMH_REACTIVE_EULER) && !(p->gamma > 1.0)) { why = "gamma must exceed 1"; return LBMH_ERR_INVALID_ARG; }
+  if (p->system == LBMH_SWE && !(p->g > 0.0)) { why = "g must be positive"; return LBMH_ERR_INVALID_ARG; }
+  if (p->system == LBMH_SWE && p->bed_amp != 0.0 && !(p->bed_w2 > 0.0)) { why = "bed width must be positive"; return LBMH_ERR_INVALID_ARG; }
+  return LBMH_OK;
+}
+
+// DevParams of a problem whose rows have the given pitch (elements)
+inline DevParams make_devparams(const lbmh_problem* p, int pitch) {
+  DevParams P;
+  memset(&P, 0, sizeof P);
+  P.nx = p->nx;
+  P.ny = p->dim == 2 ? p->ny : 1;
+  P.pitch = pitch;
+  P.plane = (long long)P.ny * P.pitch;
+  for (int s = 0; s < 4; s++) P.bc[s] = p->bc[s];
+  if (p->dim == 1) P.bc[2] = P.bc[3] = LBMH_BC_PERIODIC;
+  P.x0 = p->x0;
+  P.y0 = p->dim == 2 ? p->y0 : 0.0;
+  P.dx = (p->x1 - p->x0) / p->nx;
+  P.cfl = p->cfl;
+  P.eps = p->eps;
+  P.T = 0.0;
+  P.max_steps = 0;
+  P.adv[0] = p->adv[0];
+  P.adv[1] = p->adv[1];
+  P.gamma = p->gamma;
+  P.g = p->g;
+  P.h_dry = p->h_dry > 0.0 ? p->h_dry : 1e-8;
+  P.bed_amp = p->bed_amp;
+  P.bed_w2 = p->bed_w2 > 0.0 ? p->bed_w2 : 1.0;
+  P.bed_xc = p->bed_xc;
+  P.bed_yc = p->bed_yc;
+  P.K = p->K;
+  P.Ti = p->Ti;
+  P.q = p->q;
+  P.omega_mode = p->omega_mode;
+  P.omega_fixed = p->omega_fixed;
+  return P;
+}
+
+// elements per row of a padded distribution plane (rows start on 128 bytes)
+inline int padded_pitch(int nx, size_t elem) {
+  int align = 128 / (int)elem;
+  return (nx + 2 * XPAD + align - 1) / align * align;
+}
+
+}  // namespace lbmh

@@ -12,14 +12,14 @@
 #include "../../include/lbmh.h"
 #include "common.cuh"
 #include "fused.cuh"
+#include "host_util.h"
 #include "physics.cuh"
+#include "state.cuh"
 #include "unfused.cuh"
 
 using namespace lbmh;
 
 namespace {
-
-constexpr int kBlock = 256;
 
 struct Ops;
 
@@ -72,208 +72,6 @@ int cuda_fail(lbmh_handle* h, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
   } while (0)
 
-int nfields(int sys, int dim) {
-  switch (sys) {
-    case SYS_ADV: return 1;
-    case SYS_EULER: return dim + 2;
-    case SYS_SWE: return dim + 1;
-    case SYS_REACT: return dim + 3;
-  }
-  return -1;
-}
-
-// ---------------------------------------------------------------------------
-// initial state and diagnostics kernels
-// ---------------------------------------------------------------------------
-
-// speed bound (2.19) of a FP64 state U0 [m][ny][nx] -> ctl->ainit
-template <int SYS, int D>
-__global__ void k_init_speed(DevParams P, const double* U0, Ctl* ctl) {
-  constexpr int M = Fields<SYS, D>::M;
-  long long nn = (long long)P.nx * P.ny;
-  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double s0 = 0.0, s1 = 0.0;
-  if (node < nn) {
-    const Phys<double> K = make_phys<double>(P);
-    double U[M];
-#pragma unroll
-    for (int c = 0; c < M; c++) U[c] = U0[c * nn + node];
-    Prim<double> w = primitives<SYS, D, double>(K, U);
-    s0 = max_speed<SYS, D, double>(K, w, 0);
-    if (D == 2) s1 = max_speed<SYS, D, double>(K, w, 1);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
-    s1 = fmax(s1, __shfl_xor_sync(0xffffffffu, s1, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomic_max_nonneg((unsigned long long*)&ctl->ainit[0], s0);
-    atomic_max_nonneg((unsigned long long*)&ctl->ainit[1], s1);
-  }
-}
-
-// f := f^eq(U0) with alpha^0, lambda^0 from ctl->ainit (Eq. 2.20); the speed
-// bound of the stored state goes to slot 0 for the first step.
-template <int SYS, int D, class R>
-__global__ void k_init_eq(DevParams P, const double* U0, R* f, Ctl* ctl) {
-  constexpr int M = Fields<SYS, D>::M, Q = Fields<SYS, D>::Q;
-  long long nn = (long long)P.nx * P.ny;
-  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double ab0 = ctl->ainit[0], ab1 = D == 2 ? ctl->ainit[1] : 0.0;
-  double dt = P.cfl * P.dx / (D == 2 ? ab0 + ab1 : ab0);
-  double lam = P.dx / dt;
-  double al0 = ab0 + P.eps, al1 = D == 2 ? ab1 + P.eps : 0.0;
-  const R a0 = R(1.0 - (D == 2 ? al0 + al1 : al0) / lam), inv2l = R(1.0 / (2.0 * lam));
-  const R al[2] = {R(al0), R(al1)};
-  double s0 = 0.0, s1 = 0.0;
-  if (node < nn) {
-    int j = (int)(node / P.nx), i = (int)(node % P.nx);
-    R U[M], Us[M];
-#pragma unroll
-    for (int c = 0; c < M; c++) {
-      U[c] = R(U0[c * nn + node]);
-      Us[c] = R(0);
-    }
-    const Phys<R> K = make_phys<R>(P);
-    Prim<R> w = primitives<SYS, D, R>(K, U);
-    long long off = cell(P, i, j);
-#pragma unroll
-    for (int k = 0; k < Q; k++) {
-      R feq[M];
-      if (k == 0) {
-#pragma unroll
-        for (int c = 0; c < M; c++) feq[c] = a0 * U[c];
-      } else {
-        int jd = (k - 1) % D;
-        R F[M];
-        flux<SYS, D, R>(K, U, w, jd, F);
-        R sg = k <= D ? R(1) : R(-1);
-#pragma unroll
-        for (int c = 0; c < M; c++) feq[c] = (al[jd] * U[c] + sg * F[c]) * inv2l;
-      }
-#pragma unroll
-      for (int c = 0; c < M; c++) {
-        f[(long long)(k * M + c) * P.plane + off] = feq[c];
-        Us[c] += feq[c];
-      }
-    }
-    Prim<R> ws = primitives<SYS, D, R>(K, Us);
-    s0 = (double)max_speed<SYS, D, R>(K, ws, 0);
-    if (D == 2) s1 = (double)max_speed<SYS, D, R>(K, ws, 1);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
-    s1 = fmax(s1, __shfl_xor_sync(0xffffffffu, s1, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomic_max_nonneg(&ctl->amax[0][0], s0);
-    atomic_max_nonneg(&ctl->amax[0][1], s1);
-  }
-}
-
-// U = sum_k f_k into FP64 [m][ny][nx]
-template <int M, int Q, class R>
-__global__ void k_moments(DevParams P, R* const* buf, const Ctl* ctl, int slot, double* U) {
-  long long nn = (long long)P.nx * P.ny;
-  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (node >= nn) return;
-  const R* f = buf[ctl->parity[slot]];
-  int j = (int)(node / P.nx), i = (int)(node % P.nx);
-  long long off = cell(P, i, j);
-#pragma unroll
-  for (int c = 0; c < M; c++) {
-    R s = R(0);
-#pragma unroll
-    for (int k = 0; k < Q; k++) s += f[(long long)(k * M + c) * P.plane + off];
-    U[c * nn + node] = (double)s;
-  }
-}
-
-// f <-> FP64 [Q][m][ny][nx] (checkpointing)
-template <class R>
-__global__ void k_get_f(DevParams P, int QM, R* const* buf, const Ctl* ctl, int slot, double* out) {
-  long long nn = (long long)P.nx * P.ny;
-  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= nn * QM) return;
-  const R* f = buf[ctl->parity[slot]];
-  long long q = idx / nn, node = idx % nn;
-  int j = (int)(node / P.nx), i = (int)(node % P.nx);
-  out[idx] = (double)f[q * P.plane + cell(P, i, j)];
-}
-
-template <class R>
-__global__ void k_set_f(DevParams P, int QM, R* f, const double* in) {
-  long long nn = (long long)P.nx * P.ny;
-  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= nn * QM) return;
-  long long q = idx / nn, node = idx % nn;
-  int j = (int)(node / P.nx), i = (int)(node % P.nx);
-  f[q * P.plane + cell(P, i, j)] = R(in[idx]);
-}
-
-// speed bound of the stored distributions -> slot 0 (after lbmh_set_f)
-template <int SYS, int D, class R>
-__global__ void k_speed_of_f(DevParams P, R* const* buf, Ctl* ctl) {
-  constexpr int M = Fields<SYS, D>::M, Q = Fields<SYS, D>::Q;
-  long long nn = (long long)P.nx * P.ny;
-  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double s0 = 0.0, s1 = 0.0;
-  if (node < nn) {
-    const R* f = buf[ctl->parity[0]];
-    int j = (int)(node / P.nx), i = (int)(node % P.nx);
-    long long off = cell(P, i, j);
-    R U[M];
-#pragma unroll
-    for (int c = 0; c < M; c++) {
-      R s = R(0);
-#pragma unroll
-      for (int k = 0; k < Q; k++) s += f[(long long)(k * M + c) * P.plane + off];
-      U[c] = s;
-    }
-    const Phys<R> K = make_phys<R>(P);
-    Prim<R> w = primitives<SYS, D, R>(K, U);
-    s0 = (double)max_speed<SYS, D, R>(K, w, 0);
-    if (D == 2) s1 = (double)max_speed<SYS, D, R>(K, w, 1);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
-    s1 = fmax(s1, __shfl_xor_sync(0xffffffffu, s1, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomic_max_nonneg(&ctl->amax[0][0], s0);
-    atomic_max_nonneg(&ctl->amax[0][1], s1);
-  }
-}
-
-// ghost columns of every row := the wrapped / clamped node (after the
-// distributions were written by something other than a fused 2D step)
-template <class R>
-__global__ void k_fill_pads(DevParams P, int QM, R* f) {
-  long long rows = (long long)P.ny * QM;
-  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= rows * 2 * NGHOST) return;
-  long long row = idx / (2 * NGHOST);
-  int p = (int)(idx % (2 * NGHOST));
-  int x = p < NGHOST ? p - NGHOST : P.nx + (p - NGHOST);
-  int src = map_index(x, P.nx, P.bc[0], P.bc[1]);
-  long long q = row / P.ny, j = row % P.ny;
-  R* base = f + q * P.plane + j * P.pitch + XPAD;
-  base[x] = base[src];
-}
-
-template <class R>
-__global__ void k_extract_interior(DevParams P, ExtGeom G, const R* src_ext, double* out) {
-  long long nn = (long long)P.nx * P.ny;
-  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (node >= nn) return;
-  int j = (int)(node / P.nx), i = (int)(node % P.nx);
-  out[node] = (double)src_ext[G.idx(j + G.gy, i + GH)];
-}
-
-inline unsigned blocks_for(long long n, int bs = kBlock) { return (unsigned)((n + bs - 1) / bs); }
 
 // ---------------------------------------------------------------------------
 // per-(system, dimension, precision) operations
@@ -411,33 +209,6 @@ const Ops* pick_ops(int sys, int dim, int prec) {
   return prec == LBMH_FP32 ? pick_dim<float>(sys, dim) : pick_dim<double>(sys, dim);
 }
 
-int validate(const lbmh_problem* p, std::string& why) {
-  if (!p) { why = "problem is NULL"; return LBMH_ERR_INVALID_ARG; }
-  if (p->system == LBMH_LINEAR) { why = "LBMH_LINEAR is provided by the oracle only"; return LBMH_ERR_UNSUPPORTED; }
-  if (p->system < 0 || p->system > 3) { why = "unknown system"; return LBMH_ERR_INVALID_ARG; }
-  if (p->dim != 1 && p->dim != 2) { why = "dim must be 1 or 2"; return LBMH_ERR_INVALID_ARG; }
-  if (p->nx < 1 || (p->dim == 2 && p->ny < 1)) { why = "grid must have at least one node"; return LBMH_ERR_INVALID_ARG; }
-  if ((long long)p->nx * (p->dim == 2 ? p->ny : 1) > (1ll << 34)) { why = "grid too large"; return LBMH_ERR_INVALID_ARG; }
-  if (!(p->x1 > p->x0)) { why = "x1 must exceed x0"; return LBMH_ERR_INVALID_ARG; }
-  for (int s = 0; s < 4; s++)
-    if (p->bc[s] != LBMH_BC_PERIODIC && p->bc[s] != LBMH_BC_OUTFLOW) { why = "bad boundary condition"; return LBMH_ERR_INVALID_ARG; }
-  if ((p->bc[0] == LBMH_BC_PERIODIC) != (p->bc[1] == LBMH_BC_PERIODIC)) { why = "periodic x boundaries must pair"; return LBMH_ERR_INVALID_ARG; }
-  if (p->dim == 2) {
-    if ((p->bc[2] == LBMH_BC_PERIODIC) != (p->bc[3] == LBMH_BC_PERIODIC)) { why = "periodic y boundaries must pair"; return LBMH_ERR_INVALID_ARG; }
-    double dx = (p->x1 - p->x0) / p->nx, dy = (p->y1 - p->y0) / p->ny;
-    if (!(fabs(dx - dy) <= 1e-12 * dx)) { why = "2D mesh must satisfy dx == dy (Section 2.2.2)"; return LBMH_ERR_INVALID_ARG; }
-  }
-  if (!(p->cfl > 0.0)) { why = "cfl must be positive"; return LBMH_ERR_INVALID_ARG; }
-  if (!(p->eps >= 0.0)) { why = "eps must be non-negative"; return LBMH_ERR_INVALID_ARG; }
-  if (p->precision != LBMH_FP64 && p->precision != LBMH_FP32) { why = "bad precision"; return LBMH_ERR_INVALID_ARG; }
-  if (p->kernel < 0 || p->kernel > 2) { why = "bad kernel choice"; return LBMH_ERR_INVALID_ARG; }
-  if (p->omega_mode != 0 && p->omega_mode != 1) { why = "bad omega mode"; return LBMH_ERR_INVALID_ARG; }
-  if ((p->system == LBMH_EULER || p->system == LBMH_REACTIVE_EULER) && !(p->gamma > 1.0)) { why = "gamma must exceed 1"; return LBMH_ERR_INVALID_ARG; }
-  if (p->system == LBMH_SWE && !(p->g > 0.0)) { why = "g must be positive"; return LBMH_ERR_INVALID_ARG; }
-  if (p->system == LBMH_SWE && p->bed_amp != 0.0 && !(p->bed_w2 > 0.0)) { why = "bed width must be positive"; return LBMH_ERR_INVALID_ARG; }
-  return LBMH_OK;
-}
-
 void free_handle(lbmh_handle* h) {
   if (!h) return;
   cudaFree(h->fbuf[0]);
@@ -529,36 +300,9 @@ int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
   h->has_state = false;
   h->nblocks = 0;
   h->device_bytes = 0;
+  h->P = make_devparams(p, padded_pitch(p->nx, h->elem));
   DevParams& P = h->P;
-  memset(&P, 0, sizeof P);
-  P.nx = p->nx;
-  P.ny = p->dim == 2 ? p->ny : 1;
-  int align = 128 / (int)h->elem;  // rows start on 128-byte boundaries
-  P.pitch = (P.nx + 2 * XPAD + align - 1) / align * align;
-  P.plane = (long long)P.ny * P.pitch;
   h->plane = P.plane;
-  for (int s = 0; s < 4; s++) P.bc[s] = p->bc[s];
-  if (p->dim == 1) { P.bc[2] = P.bc[3] = LBMH_BC_PERIODIC; }
-  P.x0 = p->x0;
-  P.y0 = p->dim == 2 ? p->y0 : 0.0;
-  P.dx = (p->x1 - p->x0) / p->nx;
-  P.cfl = p->cfl;
-  P.eps = p->eps;
-  P.T = 0.0;
-  P.adv[0] = p->adv[0];
-  P.adv[1] = p->adv[1];
-  P.gamma = p->gamma;
-  P.g = p->g;
-  P.h_dry = p->h_dry > 0.0 ? p->h_dry : 1e-8;
-  P.bed_amp = p->bed_amp;
-  P.bed_w2 = p->bed_w2 > 0.0 ? p->bed_w2 : 1.0;
-  P.bed_xc = p->bed_xc;
-  P.bed_yc = p->bed_yc;
-  P.K = p->K;
-  P.Ti = p->Ti;
-  P.q = p->q;
-  P.omega_mode = p->omega_mode;
-  P.omega_fixed = p->omega_fixed;
 
   bool want_fused = p->kernel != LBMH_KERNEL_UNFUSED;
   if (p->kernel == LBMH_KERNEL_FUSED && !h->ops->has_fused) {
@@ -863,33 +607,7 @@ extern "C" int lbmh_step_static(const lbmh_problem* p, const double* f_in, doubl
   if (p->precision != LBMH_FP64) return fail(nullptr, LBMH_ERR_UNSUPPORTED, "lbmh_step_static runs in FP64 only");
   if (!f_in || !f_out || f_in == f_out) return fail(nullptr, LBMH_ERR_INVALID_ARG, "f_in and f_out must be distinct device arrays");
   const int m = nfields(p->system, p->dim), Q = 2 * p->dim + 1;
-  DevParams P;
-  memset(&P, 0, sizeof P);
-  P.nx = p->nx;
-  P.ny = p->dim == 2 ? p->ny : 1;
-  P.pitch = P.nx;  // the caller's arrays are unpadded [Q][m][ny][nx]
-  P.plane = (long long)P.nx * P.ny;
-  for (int s = 0; s < 4; s++) P.bc[s] = p->bc[s];
-  if (p->dim == 1) P.bc[2] = P.bc[3] = LBMH_BC_PERIODIC;
-  P.x0 = p->x0;
-  P.y0 = p->dim == 2 ? p->y0 : 0.0;
-  P.dx = (p->x1 - p->x0) / p->nx;
-  P.cfl = p->cfl;
-  P.eps = p->eps;
-  P.adv[0] = p->adv[0];
-  P.adv[1] = p->adv[1];
-  P.gamma = p->gamma;
-  P.g = p->g;
-  P.h_dry = p->h_dry > 0.0 ? p->h_dry : 1e-8;
-  P.bed_amp = p->bed_amp;
-  P.bed_w2 = p->bed_w2 > 0.0 ? p->bed_w2 : 1.0;
-  P.bed_xc = p->bed_xc;
-  P.bed_yc = p->bed_yc;
-  P.K = p->K;
-  P.Ti = p->Ti;
-  P.q = p->q;
-  P.omega_mode = p->omega_mode;
-  P.omega_fixed = p->omega_fixed;
+  const DevParams P = make_devparams(p, p->nx);  // the caller's arrays are unpadded [Q][m][ny][nx]
   ExtGeom G;
   G.ex = P.nx + 2 * GH;
   G.gy = p->dim == 2 ? GH : 0;

@@ -1,0 +1,203 @@
+// Set-up and diagnostic kernels shared by the single-lattice handles, the
+// allocation-free step and the batch engine: initial equilibrium (Eq. 2.20),
+// speed bounds (Eq. 2.19), moments (Eq. 2.3), checkpoint copies and the ghost
+// columns of padded rows.
+#pragma once
+#include "common.cuh"
+#include "physics.cuh"
+#include "unfused.cuh"
+
+namespace lbmh {
+
+constexpr int kBlock = 256;
+inline unsigned blocks_for(long long n, int bs = kBlock) { return (unsigned)((n + bs - 1) / bs); }
+
+
+// speed bound (2.19) of a FP64 state U0 [m][ny][nx] -> ctl->ainit
+template <int SYS, int D>
+__global__ void k_init_speed(DevParams P, const double* U0, Ctl* ctl) {
+  constexpr int M = Fields<SYS, D>::M;
+  long long nn = (long long)P.nx * P.ny;
+  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double s0 = 0.0, s1 = 0.0;
+  if (node < nn) {
+    const Phys<double> K = make_phys<double>(P);
+    double U[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) U[c] = U0[c * nn + node];
+    Prim<double> w = primitives<SYS, D, double>(K, U);
+    s0 = max_speed<SYS, D, double>(K, w, 0);
+    if (D == 2) s1 = max_speed<SYS, D, double>(K, w, 1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
+    s1 = fmax(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg((unsigned long long*)&ctl->ainit[0], s0);
+    atomic_max_nonneg((unsigned long long*)&ctl->ainit[1], s1);
+  }
+}
+
+// f := f^eq(U0) with alpha^0, lambda^0 from ctl->ainit (Eq. 2.20); the speed
+// bound of the stored state goes to slot 0 for the first step.
+template <int SYS, int D, class R>
+__global__ void k_init_eq(DevParams P, const double* U0, R* f, Ctl* ctl) {
+  constexpr int M = Fields<SYS, D>::M, Q = Fields<SYS, D>::Q;
+  long long nn = (long long)P.nx * P.ny;
+  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double ab0 = ctl->ainit[0], ab1 = D == 2 ? ctl->ainit[1] : 0.0;
+  double dt = P.cfl * P.dx / (D == 2 ? ab0 + ab1 : ab0);
+  double lam = P.dx / dt;
+  double al0 = ab0 + P.eps, al1 = D == 2 ? ab1 + P.eps : 0.0;
+  const R a0 = R(1.0 - (D == 2 ? al0 + al1 : al0) / lam), inv2l = R(1.0 / (2.0 * lam));
+  const R al[2] = {R(al0), R(al1)};
+  double s0 = 0.0, s1 = 0.0;
+  if (node < nn) {
+    int j = (int)(node / P.nx), i = (int)(node % P.nx);
+    R U[M], Us[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) {
+      U[c] = R(U0[c * nn + node]);
+      Us[c] = R(0);
+    }
+    const Phys<R> K = make_phys<R>(P);
+    Prim<R> w = primitives<SYS, D, R>(K, U);
+    long long off = cell(P, i, j);
+#pragma unroll
+    for (int k = 0; k < Q; k++) {
+      R feq[M];
+      if (k == 0) {
+#pragma unroll
+        for (int c = 0; c < M; c++) feq[c] = a0 * U[c];
+      } else {
+        int jd = (k - 1) % D;
+        R F[M];
+        flux<SYS, D, R>(K, U, w, jd, F);
+        R sg = k <= D ? R(1) : R(-1);
+#pragma unroll
+        for (int c = 0; c < M; c++) feq[c] = (al[jd] * U[c] + sg * F[c]) * inv2l;
+      }
+#pragma unroll
+      for (int c = 0; c < M; c++) {
+        f[(long long)(k * M + c) * P.plane + off] = feq[c];
+        Us[c] += feq[c];
+      }
+    }
+    Prim<R> ws = primitives<SYS, D, R>(K, Us);
+    s0 = (double)max_speed<SYS, D, R>(K, ws, 0);
+    if (D == 2) s1 = (double)max_speed<SYS, D, R>(K, ws, 1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
+    s1 = fmax(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(&ctl->amax[0][0], s0);
+    atomic_max_nonneg(&ctl->amax[0][1], s1);
+  }
+}
+
+// U = sum_k f_k into FP64 [m][ny][nx]
+template <int M, int Q, class R>
+__global__ void k_moments(DevParams P, R* const* buf, const Ctl* ctl, int slot, double* U) {
+  long long nn = (long long)P.nx * P.ny;
+  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (node >= nn) return;
+  const R* f = buf[ctl->parity[slot]];
+  int j = (int)(node / P.nx), i = (int)(node % P.nx);
+  long long off = cell(P, i, j);
+#pragma unroll
+  for (int c = 0; c < M; c++) {
+    R s = R(0);
+#pragma unroll
+    for (int k = 0; k < Q; k++) s += f[(long long)(k * M + c) * P.plane + off];
+    U[c * nn + node] = (double)s;
+  }
+}
+
+// f <-> FP64 [Q][m][ny][nx] (checkpointing)
+template <class R>
+__global__ void k_get_f(DevParams P, int QM, R* const* buf, const Ctl* ctl, int slot, double* out) {
+  long long nn = (long long)P.nx * P.ny;
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= nn * QM) return;
+  const R* f = buf[ctl->parity[slot]];
+  long long q = idx / nn, node = idx % nn;
+  int j = (int)(node / P.nx), i = (int)(node % P.nx);
+  out[idx] = (double)f[q * P.plane + cell(P, i, j)];
+}
+
+template <class R>
+__global__ void k_set_f(DevParams P, int QM, R* f, const double* in) {
+  long long nn = (long long)P.nx * P.ny;
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= nn * QM) return;
+  long long q = idx / nn, node = idx % nn;
+  int j = (int)(node / P.nx), i = (int)(node % P.nx);
+  f[q * P.plane + cell(P, i, j)] = R(in[idx]);
+}
+
+// speed bound of the stored distributions -> slot 0 (after lbmh_set_f)
+template <int SYS, int D, class R>
+__global__ void k_speed_of_f(DevParams P, R* const* buf, Ctl* ctl) {
+  constexpr int M = Fields<SYS, D>::M, Q = Fields<SYS, D>::Q;
+  long long nn = (long long)P.nx * P.ny;
+  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double s0 = 0.0, s1 = 0.0;
+  if (node < nn) {
+    const R* f = buf[ctl->parity[0]];
+    int j = (int)(node / P.nx), i = (int)(node % P.nx);
+    long long off = cell(P, i, j);
+    R U[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) {
+      R s = R(0);
+#pragma unroll
+      for (int k = 0; k < Q; k++) s += f[(long long)(k * M + c) * P.plane + off];
+      U[c] = s;
+    }
+    const Phys<R> K = make_phys<R>(P);
+    Prim<R> w = primitives<SYS, D, R>(K, U);
+    s0 = (double)max_speed<SYS, D, R>(K, w, 0);
+    if (D == 2) s1 = (double)max_speed<SYS, D, R>(K, w, 1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
+    s1 = fmax(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(&ctl->amax[0][0], s0);
+    atomic_max_nonneg(&ctl->amax[0][1], s1);
+  }
+}
+
+// ghost columns of every row := the wrapped / clamped node (after the
+// distributions were written by something other than a fused 2D step)
+template <class R>
+__global__ void k_fill_pads(DevParams P, int QM, R* f) {
+  long long rows = (long long)P.ny * QM;
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= rows * 2 * NGHOST) return;
+  long long row = idx / (2 * NGHOST);
+  int p = (int)(idx % (2 * NGHOST));
+  int x = p < NGHOST ? p - NGHOST : P.nx + (p - NGHOST);
+  int src = map_index(x, P.nx, P.bc[0], P.bc[1]);
+  long long q = row / P.ny, j = row % P.ny;
+  R* base = f + q * P.plane + j * P.pitch + XPAD;
+  base[x] = base[src];
+}
+
+template <class R>
+__global__ void k_extract_interior(DevParams P, ExtGeom G, const R* src_ext, double* out) {
+  long long nn = (long long)P.nx * P.ny;
+  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (node >= nn) return;
+  int j = (int)(node / P.nx), i = (int)(node % P.nx);
+  out[node] = (double)src_ext[G.idx(j + G.gy, i + GH)];
+}
+
+}  // namespace lbmh

@@ -109,8 +109,19 @@ __device__ __forceinline__ void lattice_vel(int k, int& ex, int& ey) {
 // Block-level reduction of the side outputs: max speeds -> control slot,
 // FP64 sums of U^{n+1} -> per-block partials (fixed order, reproducible)
 template <int M>
+__device__ __forceinline__ void block_side_outputs_to(double sp0, double sp1, const double* usum, Ctl* ctl,
+                                                      int slot1, double* dst, unsigned st);
+
+template <int M>
 __device__ __forceinline__ void block_side_outputs(double sp0, double sp1, const double* usum, Ctl* ctl, int slot1,
                                                    double* partials, unsigned st) {
+  block_side_outputs_to<M>(sp0, sp1, usum, ctl, slot1, partials + (long long)blockIdx.x * M, st);
+}
+
+// as block_side_outputs, the block's FP64 sums going to dst[0..M)
+template <int M>
+__device__ __forceinline__ void block_side_outputs_to(double sp0, double sp1, const double* usum, Ctl* ctl,
+                                                      int slot1, double* dst, unsigned st) {
   __shared__ double s_red[32][M + 2];
   __shared__ unsigned s_st;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -147,7 +158,7 @@ __device__ __forceinline__ void block_side_outputs(double sp0, double sp1, const
     atomic_max_nonneg(&ctl->amax[slot1][0], m0);
     atomic_max_nonneg(&ctl->amax[slot1][1], m1);
 #pragma unroll
-    for (int c = 0; c < M; c++) partials[(long long)blockIdx.x * M + c] = acc[c];
+    for (int c = 0; c < M; c++) dst[c] = acc[c];
     if (s_st) atomicOr(&ctl->status, s_st);
   }
 }

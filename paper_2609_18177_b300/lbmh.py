@@ -85,6 +85,21 @@ SIGNATURES = [
     ("lbmh_get_info", ctypes.c_int, [_H, ctypes.POINTER(Info)]),
     ("lbmh_destroy", ctypes.c_int, [_H]),
     ("lbmh_step_static", ctypes.c_int, [ctypes.POINTER(_Problem), _DP, _DP, ctypes.POINTER(ctypes.c_double)]),
+    ("lbmh_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    ("lbmh_batch_footprint", ctypes.c_int64, [ctypes.POINTER(_Problem)]),
+    ("lbmh_batch_add", ctypes.c_int, [_H, ctypes.POINTER(_Problem), _DP, ctypes.c_int, ctypes.c_int64,
+                                      ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
+    ("lbmh_batch_remove", ctypes.c_int, [_H, ctypes.c_int]),
+    ("lbmh_batch_step", ctypes.c_int, [_H, ctypes.c_int64]),
+    ("lbmh_batch_autotune", ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    ("lbmh_batch_poll", ctypes.c_int, [_H, _DP, _DP, _DP, _DP]),
+    ("lbmh_batch_moments", ctypes.c_int, [_H, ctypes.c_int, _DP, ctypes.c_int]),
+    ("lbmh_batch_info", ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int)]),
+    ("lbmh_batch_destroy", ctypes.c_int, [_H]),
+    ("lbmh_batch_last_error", ctypes.c_char_p, [_H]),
     ("lbmh_last_error", ctypes.c_char_p, [_H]),
     ("lbmh_version", ctypes.c_char_p, []),
 ]
@@ -248,6 +263,96 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Many 2D lattices of one system and precision advanced together (a batch
+    of the C ABI).  Lattices are admitted into a fixed device arena."""
+
+    def __init__(self, system, precision=FP32, capacity_bytes=1 << 30, max_instances=1024, stream=None):
+        lib = load()
+        self._stream = _current_stream() if stream is None else stream
+        h = ctypes.c_void_p()
+        rc = lib.lbmh_batch_create(int(system), int(precision), int(capacity_bytes), int(max_instances),
+                                   self._stream, ctypes.byref(h))
+        if rc != OK:
+            raise LbmhError(rc, lib.lbmh_batch_last_error(None).decode())
+        self._h = h
+        self.system, self.precision, self.max_instances = system, precision, max_instances
+        self.problems = {}
+
+    def _check(self, rc):
+        if rc != OK:
+            raise LbmhError(rc, load().lbmh_batch_last_error(self._h).decode())
+
+    @staticmethod
+    def footprint(pb, precision=FP32):
+        s = _c_problem(pb, precision, KERNEL_AUTO, None)
+        return int(load().lbmh_batch_footprint(ctypes.byref(s)))
+
+    def add(self, pb, U0, max_steps=0, T=0.0):
+        """Admit a lattice; returns its slot, or None if the arena or the slots are full."""
+        s = _c_problem(pb, self.precision, KERNEL_AUTO, self._stream)
+        if isinstance(U0, np.ndarray):
+            U0 = np.ascontiguousarray(U0, dtype=np.float64)
+        p, dev = _ptr(U0)
+        slot = ctypes.c_int(-1)
+        rc = load().lbmh_batch_add(self._h, ctypes.byref(s), p, dev, int(max_steps), float(T), ctypes.byref(slot))
+        if rc == ERR_OOM:
+            return None
+        self._check(rc)
+        self.problems[slot.value] = pb
+        return slot.value
+
+    def remove(self, slot):
+        self._check(load().lbmh_batch_remove(self._h, int(slot)))
+        self.problems.pop(slot, None)
+
+    def step(self, n=1):
+        self._check(load().lbmh_batch_step(self._h, int(n)))
+        return self
+
+    def autotune(self, steps_per_candidate=3):
+        ms = ctypes.c_double(0.0)
+        self._check(load().lbmh_batch_autotune(self._h, int(steps_per_candidate), ctypes.byref(ms)))
+        return ms.value
+
+    def poll(self):
+        n = self.max_instances
+        done = np.zeros(n, dtype=np.int32)
+        t = np.zeros(n)
+        steps = np.zeros(n, dtype=np.int64)
+        status = np.zeros(n, dtype=np.uint32)
+        self._check(load().lbmh_batch_poll(self._h, done.ctypes.data, t.ctypes.data, steps.ctypes.data,
+                                           status.ctypes.data))
+        return done, t, steps, status
+
+    def moments(self, slot, out=None):
+        pb = self.problems[slot]
+        if out is None:
+            out = np.empty((pb.nfields,) + pb.shape())
+        p, dev = _ptr(out)
+        self._check(load().lbmh_batch_moments(self._h, int(slot), p, dev))
+        return out
+
+    def info(self):
+        used, cap = ctypes.c_int64(), ctypes.c_int64()
+        act, grid, var = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(load().lbmh_batch_info(self._h, ctypes.byref(used), ctypes.byref(cap), ctypes.byref(act),
+                                           ctypes.byref(grid), ctypes.byref(var)))
+        return {"used_bytes": used.value, "capacity_bytes": cap.value, "active": act.value,
+                "grid": grid.value, "variant": var.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lbmh_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def step_static(pb, f_in, f_out, stream=None, want_dt=True):
