@@ -46,6 +46,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-n", type=int, default=384)
+    ap.add_argument("--workload", default="riemann2d", choices=["riemann2d", "batched", "served"])
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--sample", type=int, default=16)
+    ap.add_argument("--requests", type=int, default=60)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--sustained-rate", type=float, default=8.0)
     return ap.parse_args()
 
 
@@ -186,10 +192,152 @@ def run_reference(args):
     return 0
 
 
+def rel_l1(a, b):
+    """max over fields of sum|a-b| / sum|b|"""
+    m = b.shape[0]
+    a2, b2 = a.reshape(m, -1), b.reshape(m, -1)
+    den = np.abs(b2).sum(axis=1)
+    return float(np.max(np.abs(a2 - b2).sum(axis=1) / np.where(den > 0, den, 1.0)))
+
+
+def fp64_per_grid(pb, U0, T=None, steps=None):
+    """The plain per-grid FP64 GPU path: one fused FP64 handle per lattice."""
+    import torch
+    from paper_2609_18177_b300 import lbmh
+    s = lbmh.Solver(pb.with_(precision=0), precision=lbmh.FP64, kernel=lbmh.KERNEL_FUSED)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_state(U0)
+    if T is not None:
+        s.advance_to(T)
+    else:
+        s.step(steps)
+    U = s.moments(check=False)
+    el = time.perf_counter() - t0
+    nsteps = s.nsteps
+    s.close()
+    return U, el, nsteps
+
+
+def run_batched(args):
+    """Many shallow-water dam breaks over a bump (wet-dry, bed source) of uneven
+    sizes n ~ U{64..1024}, each to T = 0.1, in one FP32 batch."""
+    import torch
+    from paper_2609_18177_b300 import lbmh
+    from paper_2609_18177_b300 import workloads as W
+    import oracle
+    rng = np.random.default_rng(args.seed)
+    sizes = [int(v) for v in rng.integers(64, 1025, args.instances)]
+    T = 0.1
+    cases = [W.dam_break_bump(n) for n in sizes]
+    cap = sum(lbmh.Batch.footprint(pb, lbmh.FP32) for pb, _ in cases) + (64 << 20)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = lbmh.Batch(W.SWE, precision=lbmh.FP32, capacity_bytes=cap, max_instances=len(cases))
+    slots = [b.add(pb.with_(precision=1), U0, T=T) for pb, U0 in cases]
+    t_admit = time.perf_counter() - t0
+    b.autotune(steps_per_candidate=2)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    device_ms = 0.0
+    while True:
+        b.step(30)
+        done, t, steps, status = b.poll()
+        if all(done[s] == 1 for s in slots):
+            break
+    e1.record(stream)
+    torch.cuda.synchronize()
+    device_ms = e0.elapsed_time(e1)
+    results = {s: b.moments(s) for s in slots}
+    wall = time.perf_counter() - t0
+    node_steps = sum(pb.nodes * int(steps[s]) for (pb, _), s in zip(cases, slots))
+    info = b.info()
+    b.close()
+    # plain per-grid FP64 GPU path on a seeded sample, and FP32 accuracy against it
+    pick = rng.choice(len(cases), size=min(args.sample, len(cases)), replace=False)
+    t64, errs = 0.0, []
+    for i in pick:
+        pb, U0 = cases[i]
+        U64, el, _n = fp64_per_grid(pb, U0, T=T)
+        t64 += el
+        errs.append(rel_l1(results[slots[i]], U64))
+    # the FP64 GPU path against the CPU oracle on the smallest sampled lattice
+    small = min(pick, key=lambda i: sizes[i])
+    pb, U0 = cases[small]
+    r = oracle.Run(pb, U0)
+    while r.t < T:
+        r.step(1)
+    U64, _el, n64 = fp64_per_grid(pb, U0, T=T)
+    solves = len(cases) / wall
+    fp64_solves = len(pick) / t64
+    return {
+        "metric": METRIC, "workload": "batched", "value": solves, "unit": "solves/s",
+        "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{len(cases)} shallow-water dam breaks over a Gaussian bump, n ~ U{{64..1024}} "
+                               f"(seed {args.seed}), T = {T}, CFL 0.4, outflow, FP32 batch, one persistent launch "
+                               "per step + 3-step CUDA graphs, autotuned", "instances": len(cases)},
+        "wall_s": wall, "admission_s": t_admit, "device_s_stepping": device_ms / 1e3,
+        "mlups_stepping": node_steps / (device_ms / 1e3) / 1e6,
+        "hbm_gbs_stepping": node_steps * 2 * 15 * 4 / (device_ms / 1e3) / 1e9,
+        "batch_variant": info["variant"], "grid": info["grid"],
+        "fp64_per_grid_solves_per_s": fp64_solves, "fp64_sample": len(pick),
+        "speedup_vs_fp64_per_grid": solves / fp64_solves,
+        "l1_err_vs_fp64": {"max": max(errs), "median": float(np.median(errs)), "tolerance": 1e-3},
+        "fp64_gpu_vs_oracle": {"n": sizes[small], "steps": n64, "rel_l1": rel_l1(U64, r.moments()),
+                               "oracle_steps": r.nsteps},
+    }
+
+
+def run_served(args):
+    """Poisson arrivals of mixed solves (2D Euler Riemann, shallow-water dam
+    break, reactive Euler circle), n ~ U{128..2048}, 200..5000 steps."""
+    import torch
+    from paper_2609_18177_b300 import lbmh
+    from paper_2609_18177_b300 import serve as S
+    out = {}
+    for label, rate, nreq in (("offered", args.rate, args.requests),
+                              ("sustained", args.sustained_rate, max(8, args.requests // 3))):
+        trace = S.poisson_trace(nreq, rate, seed=args.seed + (0 if label == "offered" else 1))
+        inputs = {r.rid: S.make_problem(r) for r in trace}
+        srv = S.Server(capacity_bytes=24 << 30, max_instances=256, chunk=32, keep_results=(label == "offered"))
+        results, stats = srv.run(trace, inputs=inputs)
+        srv.close()
+        stats["rate_req_per_s"] = rate
+        if label == "offered":
+            # accuracy of the served FP32 results against the FP64 per-grid path
+            by = {r.rid: r for r in results}
+            smallest = sorted(trace, key=lambda r: r.n * r.n * r.steps)[:4]
+            errs = []
+            for req in smallest:
+                pb, U0 = inputs[req.rid]
+                U64, _el, _n = fp64_per_grid(pb, U0, steps=req.steps)
+                errs.append({"kind": req.kind, "n": req.n, "steps": req.steps,
+                             "rel_l1": rel_l1(by[req.rid].U, U64)})
+            stats["l1_err_vs_fp64"] = errs
+        out[label] = stats
+        del inputs
+    off = out["offered"]
+    return {
+        "metric": METRIC, "workload": "served", "value": off["solves_per_s"], "unit": "solves/s",
+        "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "Poisson arrivals of mixed 2D Euler Riemann / shallow-water dam break / reactive "
+                               "Euler solves, n ~ U{128..2048}, steps ~ U{200..5000}, FP32, continuous batching "
+                               "(one batch per system, admission by arena footprint)",
+                   "requests": args.requests, "rate": args.rate},
+        "p50_latency_s": off["p50_latency_s"], "p99_latency_s": off["p99_latency_s"],
+        "offered": off, "sustained": out["sustained"],
+    }
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in ("batched", "served"):
+        line = run_batched(args) if args.workload == "batched" else run_served(args)
+        print(json.dumps(line), flush=True)
+        return 0
     import torch
     import torch.distributed as dist
 

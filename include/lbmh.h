@@ -95,7 +95,7 @@ typedef struct lbmh_problem {
   const double *A;     /* LBMH_LINEAR only */
   int omega_mode;      /* lbmh_omega_mode */
   double omega_fixed;
-  double h_dry;        /* shallow water: h < h_dry is dry (u = v = 0); 1e-8 if 0 */
+  double h_dry;        /* shallow water: h < h_dry is dry (u = v = 0); 1e-5 if 0 */
   int precision;       /* lbmh_precision */
   int kernel;          /* lbmh_kernel */
   void *cuda_stream;   /* cudaStream_t to enqueue on */

@@ -69,7 +69,7 @@ inline DevParams make_devparams(const lbmh_problem* p, int pitch) {
   P.adv[1] = p->adv[1];
   P.gamma = p->gamma;
   P.g = p->g;
-  P.h_dry = p->h_dry > 0.0 ? p->h_dry : 1e-8;
+  P.h_dry = p->h_dry > 0.0 ? p->h_dry : 1e-5;
   P.bed_amp = p->bed_amp;
   P.bed_w2 = p->bed_w2 > 0.0 ? p->bed_w2 : 1.0;
   P.bed_xc = p->bed_xc;

@@ -1,0 +1,175 @@
+"""Continuous-batching solve server on top of the batch C ABI.
+
+Requests of mixed systems (2D Euler Riemann, shallow-water dam break over a
+bump, reactive Euler circle) and sizes arrive over time.  The server keeps one
+batch per system, each on its own CUDA stream so the three persistent launches
+overlap on the device.  A request is admitted as soon as it has arrived and its
+lattice fits in its system's arena (first fit, by footprint); admitted lattices
+stay resident on the device until they finish, and finished ones are harvested
+(moments copied to the host) and removed between step chunks, which frees
+space for the next admissions.  Latency = harvest time - arrival time.
+
+The scheduling logic is plain host code; every step runs in the CUDA library.
+"""
+import time
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional
+
+import numpy as np
+
+from . import lbmh
+from . import workloads as W
+
+KINDS = ("euler", "swe", "reactive")
+KIND_SYSTEM = {"euler": W.EULER, "swe": W.SWE, "reactive": W.REACTIVE}
+
+
+@dataclass
+class Request:
+    rid: int
+    kind: str
+    n: int
+    steps: int
+    seed: int
+    arrival: float  # seconds after the start of the run
+
+
+def make_problem(req: Request):
+    """Problem and initial state of a request (seeded, synthetic)."""
+    if req.kind == "euler":
+        pb, U0 = W.riemann_2d_seeded(req.n, seed=req.seed, cfl=0.9)
+    elif req.kind == "swe":
+        pb, U0 = W.dam_break_bump(req.n)
+    else:
+        pb, U0 = W.reactive_circle(req.n)
+    return pb.with_(precision=lbmh.FP32), U0
+
+
+def poisson_trace(nreq, rate, seed=0, n_range=(128, 2048), steps_range=(200, 5000), kinds=KINDS):
+    """Arrivals of a Poisson process of `rate` requests/s with seeded kinds,
+    grid sizes (uniform in n_range) and step counts (uniform in steps_range)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(nreq):
+        t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+        kind = kinds[int(rng.integers(len(kinds)))]
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        steps = int(rng.integers(steps_range[0], steps_range[1] + 1))
+        out.append(Request(i, kind, n, steps, int(rng.integers(1 << 30)), t))
+    return out
+
+
+@dataclass
+class Result:
+    rid: int
+    kind: str
+    n: int
+    steps: int
+    arrival: float
+    admitted: float
+    finished: float
+    U: Optional[np.ndarray] = None
+
+    @property
+    def latency(self):
+        return self.finished - self.arrival
+
+
+class Server:
+    """One batch per system; requests are admitted by footprint and stepped
+    together in chunks of `chunk` steps."""
+
+    def __init__(self, capacity_bytes=8 << 30, max_instances=256, chunk=32, autotune=False, keep_results=False):
+        import torch
+        self.torch = torch
+        self.streams = {k: torch.cuda.Stream() for k in KINDS}
+        self.batches = {k: lbmh.Batch(KIND_SYSTEM[k], precision=lbmh.FP32, capacity_bytes=capacity_bytes,
+                                      max_instances=max_instances, stream=self.streams[k].cuda_stream)
+                        for k in KINDS}
+        self.chunk = chunk
+        self.autotune = autotune
+        self.keep_results = keep_results
+        self.tuned = set()
+
+    def close(self):
+        for b in self.batches.values():
+            b.close()
+
+    def run(self, trace: List[Request], inputs: Optional[Dict[int, tuple]] = None, max_seconds=1e9):
+        """Serve `trace` in real time; `inputs` may hold pre-built (problem, U0)
+        per request id.  Returns the list of results and summary statistics."""
+        pending = sorted(trace, key=lambda r: r.arrival)
+        queue: Dict[str, List[Request]] = {k: [] for k in KINDS}
+        live: Dict[str, Dict[int, tuple]] = {k: {} for k in KINDS}  # slot -> (request, admitted time)
+        results: List[Result] = []
+        node_steps = 0
+        t0 = time.perf_counter()
+        nxt = 0
+        while True:
+            now = time.perf_counter() - t0
+            while nxt < len(pending) and pending[nxt].arrival <= now:
+                queue[pending[nxt].kind].append(pending[nxt])
+                nxt += 1
+            # admission: first fit by footprint, in arrival order
+            for k in KINDS:
+                kept = []
+                for req in queue[k]:
+                    pb, U0 = inputs[req.rid] if inputs and req.rid in inputs else make_problem(req)
+                    slot = self.batches[k].add(pb, U0, max_steps=req.steps)
+                    if slot is None:
+                        kept.append(req)
+                    else:
+                        live[k][slot] = (req, time.perf_counter() - t0)
+                queue[k] = kept
+            active = [k for k in KINDS if live[k]]
+            if not active:
+                if nxt >= len(pending) and not any(queue.values()):
+                    break
+                if nxt < len(pending):
+                    time.sleep(max(0.0, min(0.01, pending[nxt].arrival - (time.perf_counter() - t0))))
+                continue
+            # one chunk of steps on every live batch, the three streams overlapping
+            for k in active:
+                if self.autotune and k not in self.tuned and len(live[k]) >= 2:
+                    self.batches[k].autotune(steps_per_candidate=2)
+                    self.tuned.add(k)
+                self.batches[k].step(self.chunk)
+            # harvest finished lattices
+            for k in active:
+                done, t, steps, status = self.batches[k].poll()
+                for slot in list(live[k].keys()):
+                    if done[slot] == 1:
+                        req, adm = live[k].pop(slot)
+                        U = self.batches[k].moments(slot)
+                        fin = time.perf_counter() - t0
+                        self.batches[k].remove(slot)
+                        node_steps += req.n * req.n * int(steps[slot])
+                        results.append(Result(req.rid, k, req.n, int(steps[slot]), req.arrival, adm, fin,
+                                              U if self.keep_results else None))
+            if time.perf_counter() - t0 > max_seconds:
+                break
+        makespan = time.perf_counter() - t0
+        lat = np.array([r.latency for r in results]) if results else np.zeros(1)
+        stats = {
+            "completed": len(results),
+            "submitted": len(trace),
+            "makespan_s": makespan,
+            "solves_per_s": len(results) / makespan if makespan > 0 else 0.0,
+            "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)),
+            "node_updates_per_s": node_steps / makespan if makespan > 0 else 0.0,
+        }
+        return results, stats
+
+
+def run_alone(req: Request, pb, U0):
+    """The request's lattice in a batch of its own (the reference for the
+    alone-versus-mix identity)."""
+    b = lbmh.Batch(pb.system, precision=lbmh.FP32, capacity_bytes=lbmh.Batch.footprint(pb, lbmh.FP32) + (1 << 20),
+                   max_instances=1)
+    slot = b.add(pb, U0, max_steps=req.steps)
+    b.step(req.steps)
+    U = b.moments(slot)
+    b.close()
+    return U

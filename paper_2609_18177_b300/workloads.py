@@ -47,7 +47,7 @@ class Problem:
     A: Optional[np.ndarray] = None
     omega_mode: int = 0           # 0: adaptive (2.12)/(2.16); 1: fixed omega_fixed
     omega_fixed: float = 1.0
-    h_dry: float = 1e-8
+    h_dry: float = 1e-5           # depth below which a node is dry (u = v = 0)
     precision: int = 0            # 0: FP64, 1: FP32 distributions (CUDA path only)
 
     @property
