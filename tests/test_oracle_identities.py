@@ -361,3 +361,23 @@ def test_dry_bed_dam_break_converges_to_ritter():
         errs.append(np.mean(np.abs(h - h_ex)))
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] < 0.01
+
+
+def test_dry_threshold_keeps_front_speeds_physical():
+    """Wet-dry dam break over the bump (reading A10): with the dry threshold
+    1e-5 the speed bound stays at the physical front speed, and a perturbation
+    at FP32 rounding level (1e-7) barely moves the depth."""
+    pb, U0 = W.dam_break_bump(96)
+    rng = np.random.default_rng(0)
+    U1 = U0 * (1 + 1e-7 * rng.standard_normal(U0.shape))
+    a, b = oracle.Run(pb, U0), oracle.Run(pb, U1)
+    amax = 0.0
+    while a.t < 0.1:
+        a.step(1)
+        amax = max(amax, a.info[0], a.info[1])
+    while b.t < 0.1:
+        b.step(1)
+    assert amax < 6.0  # 2 sqrt(g h0) = 6.26 bounds the dry-bed front speed
+    Ua, Ub = a.moments(), b.moments()
+    l1_h = np.abs(Ua[0] - Ub[0]).sum() / np.abs(Ua[0]).sum()
+    assert l1_h < 1e-5
