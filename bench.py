@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--sample", type=int, default=16)
     ap.add_argument("--requests", type=int, default=60)
     ap.add_argument("--rate", type=float, default=200.0)
-    ap.add_argument("--sustained-rate", type=float, default=8.0)
+    ap.add_argument("--sweep-rates", default="16,8,4",
+                    help="served: lower offered rates (req/s) of the load sweep, comma-separated")
     return ap.parse_args()
 
 
@@ -192,12 +193,33 @@ def run_reference(args):
     return 0
 
 
-def rel_l1(a, b):
-    """max over fields of sum|a-b| / sum|b|"""
+def rel_l1_fields(a, b):
+    """per field: sum|a-b| / sum|b|"""
     m = b.shape[0]
     a2, b2 = a.reshape(m, -1), b.reshape(m, -1)
     den = np.abs(b2).sum(axis=1)
-    return float(np.max(np.abs(a2 - b2).sum(axis=1) / np.where(den > 0, den, 1.0)))
+    return [float(v) for v in np.abs(a2 - b2).sum(axis=1) / np.where(den > 0, den, 1.0)]
+
+
+def rel_l1(a, b):
+    """max over fields of sum|a-b| / sum|b|"""
+    return max(rel_l1_fields(a, b))
+
+
+def perturbed_input(U0, seed=12345):
+    """U0 with every value moved by a relative 2^-24 (half an FP32 ulp) in a
+    seeded random direction: the FP64 solve from it measures how far the
+    problem itself moves under an FP32-sized input change (zeros stay zero)."""
+    rng = np.random.default_rng(seed)
+    return U0 * (1.0 + 2.0 ** -24 * rng.choice([-1.0, 1.0], size=U0.shape))
+
+
+def rel_max_fields(a, b):
+    """per field: max|a-b| / max|b| (the parity norm)"""
+    m = b.shape[0]
+    a2, b2 = a.reshape(m, -1), b.reshape(m, -1)
+    den = np.abs(b2).max(axis=1)
+    return [float(v) for v in np.abs(a2 - b2).max(axis=1) / np.where(den > 0, den, 1.0)]
 
 
 def fp64_per_grid(pb, U0, T=None, steps=None):
@@ -256,16 +278,21 @@ def run_batched(args):
     b.close()
     # plain per-grid FP64 GPU path on a seeded sample, and FP32 accuracy against it
     pick = rng.choice(len(cases), size=min(args.sample, len(cases)), replace=False)
-    t64, errs = 0.0, []
+    t64, errs, floor = 0.0, [], []
     for i in pick:
         pb, U0 = cases[i]
         U64, el, _n = fp64_per_grid(pb, U0, T=T)
         t64 += el
-        errs.append(rel_l1(results[slots[i]], U64))
+        errs.append(rel_l1_fields(results[slots[i]], U64))
+        # conditioning floor: the FP64 solve from an FP32-sized input perturbation
+        U64r, _el, _n = fp64_per_grid(pb, perturbed_input(U0), T=T)
+        floor.append(rel_l1_fields(U64r, U64))
     # the FP64 GPU path against the CPU oracle on the smallest sampled lattice
     small = min(pick, key=lambda i: sizes[i])
     pb, U0 = cases[small]
-    r = oracle.Run(pb, U0)
+    r = oracle.Run(pb, U0).step(20)
+    U64_20, _el, _n = fp64_per_grid(pb, U0, steps=20)
+    oracle_20 = rel_max_fields(U64_20, r.moments())
     while r.t < T:
         r.step(1)
     U64, _el, n64 = fp64_per_grid(pb, U0, T=T)
@@ -283,8 +310,16 @@ def run_batched(args):
         "batch_variant": info["variant"], "grid": info["grid"],
         "fp64_per_grid_solves_per_s": fp64_solves, "fp64_sample": len(pick),
         "speedup_vs_fp64_per_grid": solves / fp64_solves,
-        "l1_err_vs_fp64": {"max": max(errs), "median": float(np.median(errs)), "tolerance": 1e-3},
-        "fp64_gpu_vs_oracle": {"n": sizes[small], "steps": n64, "rel_l1": rel_l1(U64, r.moments()),
+        "l1_err_vs_fp64": {"fields": "h, hu, hv", "max": float(np.max(errs)),
+                           "median": float(np.median(np.max(errs, axis=1))),
+                           "per_field_max": [float(v) for v in np.max(errs, axis=0)],
+                           "per_field_median": [float(v) for v in np.median(errs, axis=0)],
+                           "floor_fp64_input_perturbed_2^-24_per_field_max":
+                               [float(v) for v in np.max(floor, axis=0)],
+                           "floor_per_field_median": [float(v) for v in np.median(floor, axis=0)],
+                           "tolerance": 1e-3},
+        "fp64_gpu_vs_oracle": {"n": sizes[small], "rel_max_per_field_after_20_steps": oracle_20,
+                               "steps_to_T": n64, "rel_l1_per_field_at_T": rel_l1_fields(U64, r.moments()),
                                "oracle_steps": r.nsteps},
     }
 
@@ -296,9 +331,11 @@ def run_served(args):
     from paper_2609_18177_b300 import lbmh
     from paper_2609_18177_b300 import serve as S
     out = {}
-    for label, rate, nreq in (("offered", args.rate, args.requests),
-                              ("sustained", args.sustained_rate, max(8, args.requests // 3))):
-        trace = S.poisson_trace(nreq, rate, seed=args.seed + (0 if label == "offered" else 1))
+    plan = [("offered", args.rate, args.requests)]
+    plan += [(f"rate_{r:g}", r, max(8, int(round(4 * r)))) for r in
+             (float(v) for v in args.sweep_rates.split(",") if v.strip())]
+    for idx, (label, rate, nreq) in enumerate(plan):
+        trace = S.poisson_trace(nreq, rate, seed=args.seed + idx)
         inputs = {r.rid: S.make_problem(r) for r in trace}
         srv = S.Server(capacity_bytes=24 << 30, max_instances=256, chunk=32, keep_results=(label == "offered"))
         results, stats = srv.run(trace, inputs=inputs)
@@ -312,8 +349,10 @@ def run_served(args):
             for req in smallest:
                 pb, U0 = inputs[req.rid]
                 U64, _el, _n = fp64_per_grid(pb, U0, steps=req.steps)
+                U64r, _el, _n = fp64_per_grid(pb, perturbed_input(U0), steps=req.steps)
                 errs.append({"kind": req.kind, "n": req.n, "steps": req.steps,
-                             "rel_l1": rel_l1(by[req.rid].U, U64)})
+                             "rel_l1_per_field": rel_l1_fields(by[req.rid].U, U64),
+                             "floor_fp64_input_perturbed_2^-24": rel_l1_fields(U64r, U64)})
             stats["l1_err_vs_fp64"] = errs
         out[label] = stats
         del inputs
@@ -326,7 +365,7 @@ def run_served(args):
                                "(one batch per system, admission by arena footprint)",
                    "requests": args.requests, "rate": args.rate},
         "p50_latency_s": off["p50_latency_s"], "p99_latency_s": off["p99_latency_s"],
-        "offered": off, "sustained": out["sustained"],
+        "offered": off, "load_sweep": [v for k, v in out.items() if k != "offered"],
     }
 
 

@@ -423,8 +423,8 @@ int init_instance(lbmh_batch* b, int i, const double* U0dev) {
   Ctl* ctl = b->d_ctl + i;
   R* f0 = (R*)(b->arena + ih.off[0]);
   BCK(b, cudaMemsetAsync(ctl, 0, sizeof(Ctl), b->stream));
-  k_init_speed<SYS, 2><<<blocks_for(nn), kBlock, 0, b->stream>>>(P, U0dev, ctl);
-  k_init_eq<SYS, 2, R><<<blocks_for(nn), kBlock, 0, b->stream>>>(P, U0dev, f0, ctl);
+  k_init_speed<SYS, 2><<<reduce_blocks_for(nn), kBlock, 0, b->stream>>>(P, U0dev, ctl);
+  k_init_eq<SYS, 2, R><<<reduce_blocks_for(nn), kBlock, 0, b->stream>>>(P, U0dev, f0, ctl);
   long long npad = (long long)P.ny * b->Q * b->m * 2 * NGHOST;
   k_fill_pads<R><<<blocks_for(npad), kBlock, 0, b->stream>>>(P, b->Q * b->m, f0);
   k_ctl_to_slot<<<1, 1, 0, b->stream>>>(ctl, (int)(b->launched % 3));

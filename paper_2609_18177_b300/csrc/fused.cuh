@@ -270,7 +270,11 @@ __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml
         nu1[j] = nu2[j] = nu3[j] = R(0);
       }
 
-  #pragma unroll 2
+  // not unrolled: the copies of an unrolled body compile to different FMA
+  // contractions, and a row's rounding would then depend on its parity
+  // relative to the segment start, i.e. on the work split (a lattice would
+  // no longer give the same bits alone and in a batch)
+  #pragma unroll 1
       for (int r = r0; r <= r1; r++) {
         const unsigned sidx = seq0 + (unsigned)(r - r0);
         cur = sidx;
@@ -380,6 +384,9 @@ __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml
         const int y = r - 3;
         const bool row_out = y >= yb && y < ye;
         const R* p13r = p13 + (((r - 3) & 1) * 2) * M * FT;
+        // rows of the pipeline fill (before the chunk's first output row)
+        // hold no streamed values yet: their stage E is skipped (CTA-uniform)
+        if (row_out) {
   #pragma unroll
         for (int j = 0; j < CPT; j++) {
           R Fk[Q][M], Ubar[M];
@@ -399,8 +406,17 @@ __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml
           if constexpr (SRC) {
             R Un[M], Sn[M];
             const R yr = K.yb + R(y) * K.dx;
-            unsigned stn = implicit_moment<SYS, 2, R>(K, Ubar, xr_out[j], yr, cc.dt, hdt, Un);
-            source<SYS, 2, R>(K, Un, xr_out[j], yr, Sn);
+            unsigned stn = 0u;
+            if (outc[j]) {
+              stn = implicit_moment<SYS, 2, R>(K, Ubar, xr_out[j], yr, cc.dt, hdt, Un);
+              source<SYS, 2, R>(K, Un, xr_out[j], yr, Sn);
+            } else {  // halo column: its result is not stored
+  #pragma unroll
+              for (int c = 0; c < M; c++) {
+                Un[c] = Ubar[c];
+                Sn[c] = R(0);
+              }
+            }
   #pragma unroll
             for (int c = 0; c < M; c++) Us[c] = R(0);
   #pragma unroll
@@ -437,6 +453,7 @@ __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml
             for (int c = 0; c < M; c++) acc[c].add(Us[c]);
             st |= state_status<SYS, 2, R>(Us, wn);
           }
+        }
         }
         fence_proxy_async();  // staged row visible to the TMA store
   #pragma unroll

@@ -50,6 +50,12 @@ struct lbmh_handle {
   long long device_bytes;
   const Ops* ops;
   FusedPlan fp;
+  // runs of kGraphSteps launches replayed as one CUDA graph (captured on a
+  // private stream, keyed by the end time T the launches carry)
+  cudaStream_t cap_stream;
+  cudaGraphExec_t graph;
+  double graph_T;
+  bool graph_failed;
   std::string err;
 };
 
@@ -137,7 +143,7 @@ struct Impl {
 
   static int init(lbmh_handle* h, const double* U0dev) {
     long long nn = (long long)h->P.nx * h->P.ny;
-    unsigned nb = blocks_for(nn);
+    unsigned nb = reduce_blocks_for(nn);
     k_init_speed<SYS, D><<<nb, kBlock, 0, h->stream>>>(h->P, U0dev, h->ctl);
     k_init_eq<SYS, D, R><<<nb, kBlock, 0, h->stream>>>(h->P, U0dev, (R*)h->fbuf[0], h->ctl);
     fill_pads(h, (R*)h->fbuf[0]);
@@ -166,7 +172,7 @@ struct Impl {
     long long n = (long long)h->P.nx * h->P.ny * Q * M;
     k_set_f<R><<<blocks_for(n), kBlock, 0, h->stream>>>(h->P, Q * M, (R*)h->fbuf[0], dev);
     fill_pads(h, (R*)h->fbuf[0]);
-    k_speed_of_f<SYS, D, R><<<blocks_for((long long)h->P.nx * h->P.ny), kBlock, 0, h->stream>>>(
+    k_speed_of_f<SYS, D, R><<<reduce_blocks_for((long long)h->P.nx * h->P.ny), kBlock, 0, h->stream>>>(
         h->P, (R* const*)h->dbuf, h->ctl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "set_f launch");
@@ -220,6 +226,8 @@ void free_handle(lbmh_handle* h) {
   cudaFree(h->partials);
   cudaFree(h->ctl);
   cudaFree(h->Utmp);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
 
@@ -265,6 +273,71 @@ int sync(lbmh_handle* h) {
 
 int current_slot(const lbmh_handle* h) { return (int)(h->launched % 3); }
 
+// launches per graph: a multiple of 3 so that a replay starting at slot 0
+// ends at slot 0 (the control block rotates through three slots)
+constexpr int kGraphSteps = 24;
+
+// capture kGraphSteps launches starting at slot 0 with end time T
+int capture_steps(lbmh_handle* h, double T) {
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t user = h->stream;
+  h->stream = h->cap_stream;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+  int rc = LBMH_OK;
+  if (e == cudaSuccess) {
+    for (int s = 0; s < kGraphSteps && rc == LBMH_OK; s++) rc = h->ops->launch_step(h, s % 3, T);
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  h->stream = user;
+  if (e == cudaSuccess && rc == LBMH_OK) e = cudaGraphInstantiate(&h->graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess || rc != LBMH_OK) {
+    cudaGetLastError();
+    h->graph = nullptr;
+    h->graph_failed = true;  // fall back to single launches from now on
+    h->err.clear();
+    return LBMH_OK;
+  }
+  h->graph_T = T;
+  return LBMH_OK;
+}
+
+// n step launches with end time T (0 = none): single launches up to the next
+// multiple of 3, graph replays of kGraphSteps launches, single launches for
+// the rest
+int run_steps(lbmh_handle* h, int64_t n, double T) {
+  int64_t s = 0;
+  auto single = [&](int64_t upto) -> int {
+    for (; s < upto; s++) {
+      int rc = h->ops->launch_step(h, current_slot(h), T);
+      if (rc) return rc;
+      h->launched++;
+    }
+    return LBMH_OK;
+  };
+  if (n >= 2 * kGraphSteps && !h->graph_failed) {
+    int rc = single((3 - current_slot(h)) % 3);
+    if (rc) return rc;
+    if (!h->graph || h->graph_T != T) {
+      rc = capture_steps(h, T);
+      if (rc) return rc;
+    }
+    if (h->graph) {
+      for (; s + kGraphSteps <= n; s += kGraphSteps) {
+        CK(h, cudaGraphLaunch(h->graph, h->stream));
+        h->launched += kGraphSteps;
+      }
+    }
+  }
+  return single(n);
+}
+
 int read_ctl(lbmh_handle* h, Ctl* out) {
   CK(h, cudaMemcpyAsync(out, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
   return sync(h);
@@ -287,6 +360,7 @@ int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
   lbmh_handle* h = new lbmh_handle();
   memset(h->fbuf, 0, sizeof h->fbuf);
   h->dbuf = nullptr; h->Ue = h->nue = h->ome = nullptr; h->partials = nullptr; h->ctl = nullptr; h->Utmp = nullptr;
+  h->cap_stream = nullptr; h->graph = nullptr; h->graph_T = 0.0; h->graph_failed = false;
   h->prob = *p;
   h->dim = p->dim;
   h->sys = p->system;
@@ -395,12 +469,7 @@ int lbmh_step(lbmh_handle* h, int64_t n) {
   if (!h->has_state) return fail(h, LBMH_ERR_INVALID_ARG, "no state: call lbmh_set_state first");
   if (n < 0) return fail(h, LBMH_ERR_INVALID_ARG, "negative step count");
   h->err.clear();
-  for (int64_t s = 0; s < n; s++) {
-    int rc = h->ops->launch_step(h, current_slot(h), 0.0);
-    if (rc) return rc;
-    h->launched++;
-  }
-  return LBMH_OK;
+  return run_steps(h, n, 0.0);
 }
 
 int lbmh_advance_to(lbmh_handle* h, double T, int64_t max_steps) {
@@ -422,11 +491,8 @@ int lbmh_advance_to(lbmh_handle* h, double T, int64_t max_steps) {
     int64_t est = (int64_t)((T - t) / dt_est) + 1;
     int64_t chunk = est < 8 ? 8 : (est > 256 ? 256 : est);
     if (chunk > max_steps - done) chunk = max_steps - done;
-    for (int64_t s = 0; s < chunk; s++) {
-      rc = h->ops->launch_step(h, current_slot(h), T);
-      if (rc) return rc;
-      h->launched++;
-    }
+    rc = run_steps(h, chunk, T);
+    if (rc) return rc;
     rc = read_ctl(h, &c);
     if (rc) return rc;
     done = c.nsteps[current_slot(h)] - start;

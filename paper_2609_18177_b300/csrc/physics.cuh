@@ -4,8 +4,9 @@
 // smoothness indicator, the source S(U) and the implicit moment of Eq. (2.8).
 //
 // All constants arrive pre-converted to R in a Phys<R> block built once per
-// thread, so the FP32 path issues no FP64 instruction per node except in the
-// Arrhenius source and its implicit update (kept in FP64 on purpose).
+// thread, so the FP32 path issues no FP64 instruction per node; its Arrhenius
+// root falls back to FP64 only where the FP32 Newton iteration does not
+// converge.
 #pragma once
 #include "common.cuh"
 
@@ -38,6 +39,7 @@ struct Phys {
   R bed_amp, bed_inv_w2, bed_m2_inv_w2;  // amp, 1/w2, -2/w2
   R xb, yb;                              // x0 + dx/2 - xc, y0 + dx/2 - yc: node i sits at xb + i dx
   double gamma_d, q_d, K, Ti;            // Arrhenius, FP64
+  R Kr, Tir;                             // Arrhenius in the path's precision
   bool bed, react;
 };
 
@@ -63,6 +65,8 @@ __device__ __forceinline__ Phys<R> make_phys(const DevParams& P) {
   k.q_d = P.q;
   k.K = P.K;
   k.Ti = P.Ti;
+  k.Kr = R(P.K);
+  k.Tir = R(P.Ti);
   k.bed = P.bed_amp != 0.0;
   k.react = P.K != 0.0;
   return k;
@@ -226,8 +230,17 @@ __device__ __forceinline__ double arrhenius(const Phys<R>& K, double rho, double
   return K.K * z * exp(-K.Ti / (pres / rho));
 }
 
+// The same rate in FP32: T = p/rho, exp(-Ti rho / p) with the accurate expf
+// (the FP32 mode's explicit half-source; its relative error is that of the
+// FP32 state it is computed from)
+__device__ __forceinline__ float arrhenius_f32(const Phys<float>& K, float rho, float momsq, float E, float z) {
+  float pres = K.gm1 * (E - 0.5f * fdiv(momsq, rho) - K.q * z);
+  return K.Kr * z * expf(-fdiv(K.Tir * rho, pres));
+}
+
 // Source S(U) at a node whose position relative to the bump centre is
-// (xr, yr).  Shallow water: bed slope; reactive: Arrhenius (FP64).
+// (xr, yr).  Shallow water: bed slope; reactive: Arrhenius (FP64 in the FP64
+// mode, FP32 in the FP32 mode).
 template <int SYS, int D, class R>
 __device__ __forceinline__ void source(const Phys<R>& K, const R* U, R xr, R yr, R* S) {
   constexpr int M = Fields<SYS, D>::M;
@@ -242,17 +255,65 @@ __device__ __forceinline__ void source(const Phys<R>& K, const R* U, R xr, R yr,
     }
   } else if constexpr (SYS == SYS_REACT) {
     if (K.react) {
-      double rho = (double)U[0], m1 = (double)U[1], m2 = D == 2 ? (double)U[2] : 0.0;
-      S[D + 2] = R(-arrhenius(K, rho, m1 * m1 + m2 * m2, (double)U[D + 1], (double)U[D + 2]));
+      if constexpr (sizeof(R) == 4) {
+        const float m2 = D == 2 ? U[2] : 0.0f;
+        S[D + 2] = -arrhenius_f32(K, U[0], U[1] * U[1] + m2 * m2, U[D + 1], U[D + 2]);
+      } else {
+        double rho = (double)U[0], m1 = (double)U[1], m2 = D == 2 ? (double)U[2] : 0.0;
+        S[D + 2] = R(-arrhenius(K, rho, m1 * m1 + m2 * m2, (double)U[D + 1], (double)U[D + 2]));
+      }
     }
   }
 }
 
+// FP32 root of g(z) = z - zbar + dt/2 K z exp(-Ti/T(z)) (see implicit_moment):
+// the same safeguarded Newton iteration in FP32, stopped when the Newton step
+// falls below 2^-22 |zbar| (about two FP32 ulps of zbar; the iterate is then
+// rounded to FP32 storage anyway).  Returns 0 (converged), 1 (no convergence
+// in 30 iterations: the caller solves in FP64) or 2 (non-finite state: no
+// root is sought).
+template <int D>
+__device__ __forceinline__ int react_root_f32(const Phys<float>& K, const float* Ubar, double dt, float* zout) {
+  const float zbar = Ubar[D + 2], rho = Ubar[0], E = Ubar[D + 1];
+  const float m2 = D == 2 ? Ubar[2] : 0.0f;
+  const float momsq = Ubar[1] * Ubar[1] + m2 * m2;
+  const float irho = frcp(rho);
+  const float hk = float(0.5 * dt * K.K);
+  const float dTdz = -K.gm1 * K.q * irho;
+  const float e0 = K.gm1 * (E - 0.5f * momsq * irho) * irho;
+  float lo = zbar < 0.0f ? zbar : 0.0f, hi = zbar < 0.0f ? 0.0f : zbar;
+  float z = fdiv(zbar, 1.0f + hk * expf(-fdiv(K.Tir, e0 + dTdz * zbar)));
+  if (!(fabsf(z) <= 3.0e38f)) return 2;
+  const float tol = 0x1p-22f * fabsf(zbar);
+  for (int it = 0; it < 30; it++) {
+    const float T = e0 + dTdz * z;
+    const float a = fdiv(K.Tir, T);
+    const float ex = expf(-a);
+    const float gz = z - zbar + hk * z * ex;
+    if (gz == 0.0f) {
+      *zout = z;
+      return 0;
+    }
+    if (gz > 0.0f) hi = z; else lo = z;
+    const float dg = 1.0f + hk * ex * (1.0f + z * fdiv(a, T) * dTdz);
+    float zn = z - fdiv(gz, dg);
+    if (fabsf(zn - z) <= tol) {
+      *zout = zn;
+      return 0;
+    }
+    if (!(zn > lo && zn < hi)) zn = 0.5f * (lo + hi);
+    z = zn;
+  }
+  return 1;
+}
+
 // Eq. (2.8): U^{n+1} = Ubar + dt/2 S(U^{n+1}).  Shallow water: no mass source,
 // so the momentum update is explicit in h^{n+1} = hbar.  Reactive: a scalar
-// equation g(z) = z - zbar + dt/2 R(z) = 0 in z = rho*Y, solved in FP64 by
-// Newton's method safeguarded by bisection on the bracket between 0 and zbar.
-// Returns status bits.
+// equation g(z) = z - zbar + dt/2 R(z) = 0 in z = rho*Y, solved by Newton's
+// method safeguarded by bisection on the bracket between 0 and zbar, from the
+// frozen-temperature guess: in FP64 in the FP64 mode; in the FP32 mode in FP32
+// first, in FP64 where the FP32 iteration does not converge.  Returns status
+// bits.
 template <int SYS, int D, class R>
 __device__ __forceinline__ unsigned implicit_moment(const Phys<R>& K, const R* Ubar, R xr, R yr, double dt, R hdt,
                                                     R* Un) {
@@ -269,8 +330,17 @@ __device__ __forceinline__ unsigned implicit_moment(const Phys<R>& K, const R* U
     return 0u;
   } else if constexpr (SYS == SYS_REACT) {
     if (!K.react) return 0u;
+    if (Ubar[D + 2] == R(0)) return 0u;
+    if constexpr (sizeof(R) == 4) {
+      float zf;
+      const int rc = react_root_f32<D>(K, Ubar, dt, &zf);
+      if (rc == 0) {
+        Un[D + 2] = zf;
+        return 0u;
+      }
+      if (rc == 2) return ST_NOROOT;  // z = zbar, as the FP64 path leaves it
+    }
     const double zbar = (double)Ubar[D + 2];
-    if (zbar == 0.0) return 0u;
     const double rho = (double)Ubar[0], E = (double)Ubar[D + 1];
     const double m1 = (double)Ubar[1], m2 = D == 2 ? (double)Ubar[2] : 0.0;
     const double momsq = m1 * m1 + m2 * m2;
@@ -280,6 +350,7 @@ __device__ __forceinline__ unsigned implicit_moment(const Phys<R>& K, const R* U
     double lo = zbar < 0.0 ? zbar : 0.0, hi = zbar < 0.0 ? 0.0 : zbar;
     double z = zbar / (1.0 + hk * exp(-K.Ti / (e0 + dTdz * zbar)));
     unsigned st = ST_NOROOT;
+    if (z != z) return ST_NOROOT;  // non-finite state: z = zbar, flagged (no iteration)
     for (int it = 0; it < 60; it++) {
       double T = e0 + dTdz * z;
       double ex = exp(-K.Ti / T);
@@ -288,9 +359,11 @@ __device__ __forceinline__ unsigned implicit_moment(const Phys<R>& K, const R* U
       if (gz > 0.0) hi = z; else lo = z;
       double dg = 1.0 + hk * ex * (1.0 + z * K.Ti / (T * T) * dTdz);
       double zn = z - gz / dg;
+      // converged when the Newton step is below the tolerance; tested before
+      // the bracket guard, since z itself has just become a bracket end and a
+      // sub-resolution step lands on it
+      if (fabs(zn - z) <= 1e-15 * fabs(zbar)) { z = zn; st = 0u; break; }
       if (!(zn > lo && zn < hi)) zn = 0.5 * (lo + hi);
-      double tol = 1e-15 * fmax(fabs(zbar), 1e-300);
-      if (fabs(zn - z) <= tol) { z = zn; st = 0u; break; }
       z = zn;
     }
     Un[D + 2] = R(z);

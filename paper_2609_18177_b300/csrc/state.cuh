@@ -12,49 +12,81 @@ namespace lbmh {
 constexpr int kBlock = 256;
 inline unsigned blocks_for(long long n, int bs = kBlock) { return (unsigned)((n + bs - 1) / bs); }
 
+// grid of the node loops that end in a maximum (speed bounds): grid-stride
+// loops over at most 2048 blocks, so that the maximum costs one atomic per
+// block instead of one per warp (contended atomics on one address serialise)
+inline unsigned reduce_blocks_for(long long n) {
+  unsigned b = blocks_for(n);
+  return b < 2048u ? (b ? b : 1u) : 2048u;
+}
 
-// speed bound (2.19) of a FP64 state U0 [m][ny][nx] -> ctl->ainit
-template <int SYS, int D>
-__global__ void k_init_speed(DevParams P, const double* U0, Ctl* ctl) {
-  constexpr int M = Fields<SYS, D>::M;
-  long long nn = (long long)P.nx * P.ny;
-  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double s0 = 0.0, s1 = 0.0;
-  if (node < nn) {
-    const Phys<double> K = make_phys<double>(P);
-    double U[M];
-#pragma unroll
-    for (int c = 0; c < M; c++) U[c] = U0[c * nn + node];
-    Prim<double> w = primitives<SYS, D, double>(K, U);
-    s0 = max_speed<SYS, D, double>(K, w, 0);
-    if (D == 2) s1 = max_speed<SYS, D, double>(K, w, 1);
-  }
+// (s0, s1) := their maxima over the block (kBlock threads); thread 0 folds
+// them into d0, d1
+__device__ __forceinline__ void block_max2_to(double s0, double s1, unsigned long long* d0,
+                                              unsigned long long* d1) {
+  __shared__ double red[2][kBlock / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
     s1 = fmax(s1, __shfl_xor_sync(0xffffffffu, s1, o));
   }
-  if ((threadIdx.x & 31) == 0) {
-    atomic_max_nonneg((unsigned long long*)&ctl->ainit[0], s0);
-    atomic_max_nonneg((unsigned long long*)&ctl->ainit[1], s1);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][w] = s0;
+    red[1][w] = s1;
   }
+  __syncthreads();
+  if (w == 0) {
+    s0 = lane < kBlock / 32 ? red[0][lane] : 0.0;
+    s1 = lane < kBlock / 32 ? red[1][lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
+      s1 = fmax(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+    }
+    if (lane == 0) {
+      atomic_max_nonneg(d0, s0);
+      atomic_max_nonneg(d1, s1);
+    }
+  }
+}
+
+
+// speed bound (2.19) of a FP64 state U0 [m][ny][nx] -> ctl->ainit
+template <int SYS, int D>
+__global__ void __launch_bounds__(kBlock) k_init_speed(DevParams P, const double* U0, Ctl* ctl) {
+  constexpr int M = Fields<SYS, D>::M;
+  const long long nn = (long long)P.nx * P.ny;
+  const Phys<double> K = make_phys<double>(P);
+  double s0 = 0.0, s1 = 0.0;
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < nn;
+       node += (long long)gridDim.x * blockDim.x) {
+    double U[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) U[c] = U0[c * nn + node];
+    Prim<double> w = primitives<SYS, D, double>(K, U);
+    s0 = fmax(s0, max_speed<SYS, D, double>(K, w, 0));
+    if (D == 2) s1 = fmax(s1, max_speed<SYS, D, double>(K, w, 1));
+  }
+  block_max2_to(s0, s1, (unsigned long long*)&ctl->ainit[0], (unsigned long long*)&ctl->ainit[1]);
 }
 
 // f := f^eq(U0) with alpha^0, lambda^0 from ctl->ainit (Eq. 2.20); the speed
 // bound of the stored state goes to slot 0 for the first step.
 template <int SYS, int D, class R>
-__global__ void k_init_eq(DevParams P, const double* U0, R* f, Ctl* ctl) {
+__global__ void __launch_bounds__(kBlock) k_init_eq(DevParams P, const double* U0, R* f, Ctl* ctl) {
   constexpr int M = Fields<SYS, D>::M, Q = Fields<SYS, D>::Q;
-  long long nn = (long long)P.nx * P.ny;
-  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nn = (long long)P.nx * P.ny;
   double ab0 = ctl->ainit[0], ab1 = D == 2 ? ctl->ainit[1] : 0.0;
   double dt = P.cfl * P.dx / (D == 2 ? ab0 + ab1 : ab0);
   double lam = P.dx / dt;
   double al0 = ab0 + P.eps, al1 = D == 2 ? ab1 + P.eps : 0.0;
   const R a0 = R(1.0 - (D == 2 ? al0 + al1 : al0) / lam), inv2l = R(1.0 / (2.0 * lam));
   const R al[2] = {R(al0), R(al1)};
+  const Phys<R> K = make_phys<R>(P);
   double s0 = 0.0, s1 = 0.0;
-  if (node < nn) {
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < nn;
+       node += (long long)gridDim.x * blockDim.x) {
     int j = (int)(node / P.nx), i = (int)(node % P.nx);
     R U[M], Us[M];
 #pragma unroll
@@ -62,7 +94,6 @@ __global__ void k_init_eq(DevParams P, const double* U0, R* f, Ctl* ctl) {
       U[c] = R(U0[c * nn + node]);
       Us[c] = R(0);
     }
-    const Phys<R> K = make_phys<R>(P);
     Prim<R> w = primitives<SYS, D, R>(K, U);
     long long off = cell(P, i, j);
 #pragma unroll
@@ -86,18 +117,10 @@ __global__ void k_init_eq(DevParams P, const double* U0, R* f, Ctl* ctl) {
       }
     }
     Prim<R> ws = primitives<SYS, D, R>(K, Us);
-    s0 = (double)max_speed<SYS, D, R>(K, ws, 0);
-    if (D == 2) s1 = (double)max_speed<SYS, D, R>(K, ws, 1);
+    s0 = fmax(s0, (double)max_speed<SYS, D, R>(K, ws, 0));
+    if (D == 2) s1 = fmax(s1, (double)max_speed<SYS, D, R>(K, ws, 1));
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
-    s1 = fmax(s1, __shfl_xor_sync(0xffffffffu, s1, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomic_max_nonneg(&ctl->amax[0][0], s0);
-    atomic_max_nonneg(&ctl->amax[0][1], s1);
-  }
+  block_max2_to(s0, s1, &ctl->amax[0][0], &ctl->amax[0][1]);
 }
 
 // U = sum_k f_k into FP64 [m][ny][nx]
@@ -142,13 +165,14 @@ __global__ void k_set_f(DevParams P, int QM, R* f, const double* in) {
 
 // speed bound of the stored distributions -> slot 0 (after lbmh_set_f)
 template <int SYS, int D, class R>
-__global__ void k_speed_of_f(DevParams P, R* const* buf, Ctl* ctl) {
+__global__ void __launch_bounds__(kBlock) k_speed_of_f(DevParams P, R* const* buf, Ctl* ctl) {
   constexpr int M = Fields<SYS, D>::M, Q = Fields<SYS, D>::Q;
-  long long nn = (long long)P.nx * P.ny;
-  long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nn = (long long)P.nx * P.ny;
+  const Phys<R> K = make_phys<R>(P);
+  const R* f = buf[ctl->parity[0]];
   double s0 = 0.0, s1 = 0.0;
-  if (node < nn) {
-    const R* f = buf[ctl->parity[0]];
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < nn;
+       node += (long long)gridDim.x * blockDim.x) {
     int j = (int)(node / P.nx), i = (int)(node % P.nx);
     long long off = cell(P, i, j);
     R U[M];
@@ -159,20 +183,11 @@ __global__ void k_speed_of_f(DevParams P, R* const* buf, Ctl* ctl) {
       for (int k = 0; k < Q; k++) s += f[(long long)(k * M + c) * P.plane + off];
       U[c] = s;
     }
-    const Phys<R> K = make_phys<R>(P);
     Prim<R> w = primitives<SYS, D, R>(K, U);
-    s0 = (double)max_speed<SYS, D, R>(K, w, 0);
-    if (D == 2) s1 = (double)max_speed<SYS, D, R>(K, w, 1);
+    s0 = fmax(s0, (double)max_speed<SYS, D, R>(K, w, 0));
+    if (D == 2) s1 = fmax(s1, (double)max_speed<SYS, D, R>(K, w, 1));
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
-    s1 = fmax(s1, __shfl_xor_sync(0xffffffffu, s1, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomic_max_nonneg(&ctl->amax[0][0], s0);
-    atomic_max_nonneg(&ctl->amax[0][1], s1);
-  }
+  block_max2_to(s0, s1, &ctl->amax[0][0], &ctl->amax[0][1]);
 }
 
 // ghost columns of every row := the wrapped / clamped node (after the

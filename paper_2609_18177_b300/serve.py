@@ -104,6 +104,7 @@ class Server:
         live: Dict[str, Dict[int, tuple]] = {k: {} for k in KINDS}  # slot -> (request, admitted time)
         results: List[Result] = []
         node_steps = 0
+        deferred = set()  # requests refused admission at least once (arena full)
         t0 = time.perf_counter()
         nxt = 0
         while True:
@@ -119,6 +120,7 @@ class Server:
                     slot = self.batches[k].add(pb, U0, max_steps=req.steps)
                     if slot is None:
                         kept.append(req)
+                        deferred.add(req.rid)
                     else:
                         live[k][slot] = (req, time.perf_counter() - t0)
                 queue[k] = kept
@@ -159,6 +161,7 @@ class Server:
             "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)),
             "node_updates_per_s": node_steps / makespan if makespan > 0 else 0.0,
+            "deferred_admissions": len(deferred),
         }
         return results, stats
 

@@ -21,7 +21,8 @@ def _cuda():
 
 
 def test_served_results_equal_alone_and_queueing_happens():
-    trace = S.poisson_trace(12, rate=400.0, seed=3, n_range=(64, 160), steps_range=(20, 70))
+    # every request arrives at t = 0, so the small arena must defer some of them
+    trace = S.poisson_trace(12, rate=0.0, seed=3, n_range=(64, 160), steps_range=(20, 70))
     inputs = {r.rid: S.make_problem(r) for r in trace}
     biggest = max(lbmh.Batch.footprint(pb, lbmh.FP32) for pb, _ in inputs.values())
     srv = S.Server(capacity_bytes=int(2.2 * biggest), max_instances=8, chunk=8, keep_results=True)
@@ -30,11 +31,9 @@ def test_served_results_equal_alone_and_queueing_happens():
     assert stats["completed"] == len(trace)
     assert stats["p50_latency_s"] <= stats["p99_latency_s"]
     by_id = {r.rid: r for r in results}
-    waited = 0
     for req in trace:
         res = by_id[req.rid]
         assert res.steps == req.steps
-        waited += res.admitted - res.arrival > 0.005
         pb, U0 = inputs[req.rid]
         assert np.array_equal(res.U, S.run_alone(req, pb, U0)), req
-    assert waited > 0  # the small arena made some requests queue for space
+    assert stats["deferred_admissions"] > 0  # some requests queued for arena space
