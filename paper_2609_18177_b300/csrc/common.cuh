@@ -39,6 +39,8 @@ struct DevParams {
   double gamma, g, h_dry;
   double bed_amp, bed_w2, bed_xc, bed_yc;
   double K, Ti, q;
+  int has_bed;       // bed_amp != 0 (flags set on the host: a device test of
+  int has_react;     // K != 0           a double would be an FP64 instruction)
   int omega_mode;    // 0 adaptive, 1 fixed
   double omega_fixed;
 };

@@ -77,6 +77,8 @@ inline DevParams make_devparams(const lbmh_problem* p, int pitch) {
   P.K = p->K;
   P.Ti = p->Ti;
   P.q = p->q;
+  P.has_bed = p->bed_amp != 0.0;
+  P.has_react = p->K != 0.0;
   P.omega_mode = p->omega_mode;
   P.omega_fixed = p->omega_fixed;
   return P;

@@ -67,8 +67,8 @@ __device__ __forceinline__ Phys<R> make_phys(const DevParams& P) {
   k.Ti = P.Ti;
   k.Kr = R(P.K);
   k.Tir = R(P.Ti);
-  k.bed = P.bed_amp != 0.0;
-  k.react = P.K != 0.0;
+  k.bed = P.has_bed != 0;
+  k.react = P.has_react != 0;
   return k;
 }
 
@@ -273,12 +273,12 @@ __device__ __forceinline__ void source(const Phys<R>& K, const R* U, R xr, R yr,
 // in 30 iterations: the caller solves in FP64) or 2 (non-finite state: no
 // root is sought).
 template <int D>
-__device__ __forceinline__ int react_root_f32(const Phys<float>& K, const float* Ubar, double dt, float* zout) {
+__device__ __forceinline__ int react_root_f32(const Phys<float>& K, const float* Ubar, float hdt, float* zout) {
   const float zbar = Ubar[D + 2], rho = Ubar[0], E = Ubar[D + 1];
   const float m2 = D == 2 ? Ubar[2] : 0.0f;
   const float momsq = Ubar[1] * Ubar[1] + m2 * m2;
   const float irho = frcp(rho);
-  const float hk = float(0.5 * dt * K.K);
+  const float hk = hdt * K.Kr;  // dt/2 K
   const float dTdz = -K.gm1 * K.q * irho;
   const float e0 = K.gm1 * (E - 0.5f * momsq * irho) * irho;
   float lo = zbar < 0.0f ? zbar : 0.0f, hi = zbar < 0.0f ? 0.0f : zbar;
@@ -307,6 +307,48 @@ __device__ __forceinline__ int react_root_f32(const Phys<float>& K, const float*
   return 1;
 }
 
+struct RootF64 {
+  double z;
+  unsigned st;
+};
+
+// FP64 root of g(z) = z - zbar + hk z exp(-Ti/T(z)), T(z) = e0 + dTdz z,
+// hk = dt/2 K (see implicit_moment): Newton from the frozen-temperature guess,
+// safeguarded by bisection on the bracket between 0 and zbar, until the step
+// is below 1e-15 |zbar|.  A non-finite state returns z = zbar with ST_NOROOT.
+__device__ __forceinline__ RootF64 react_root_f64(double rho, double momsq, double E, double zbar, double hk,
+                                                  double gm1, double q, double Ti) {
+  const double dTdz = -gm1 * q / rho;
+  const double e0 = gm1 * (E - 0.5 * momsq / rho) / rho;  // T at z = 0
+  double lo = zbar < 0.0 ? zbar : 0.0, hi = zbar < 0.0 ? 0.0 : zbar;
+  double z = zbar / (1.0 + hk * exp(-Ti / (e0 + dTdz * zbar)));
+  if (z != z) return RootF64{zbar, ST_NOROOT};
+  for (int it = 0; it < 60; it++) {
+    double T = e0 + dTdz * z;
+    double ex = exp(-Ti / T);
+    double gz = z - zbar + hk * z * ex;
+    if (gz == 0.0) return RootF64{z, 0u};
+    if (gz > 0.0) hi = z; else lo = z;
+    double dg = 1.0 + hk * ex * (1.0 + z * Ti / (T * T) * dTdz);
+    double zn = z - gz / dg;
+    // converged when the Newton step is below the tolerance; tested before
+    // the bracket guard, since z itself has just become a bracket end and a
+    // sub-resolution step lands on it
+    if (fabs(zn - z) <= 1e-15 * fabs(zbar)) return RootF64{zn, 0u};
+    if (!(zn > lo && zn < hi)) zn = 0.5 * (lo + hi);
+    z = zn;
+  }
+  return RootF64{z, ST_NOROOT};
+}
+
+// The FP32 mode's fallback, out of line so that none of its FP64 work is
+// scheduled into the FP32 path.
+static __device__ __noinline__ RootF64 react_root_f64_fallback(float rho, float m1, float m2, float E, float zbar, double dt,
+                                                               double Kc, double gamma, double q, double Ti) {
+  const double d1 = (double)m1, d2 = (double)m2;
+  return react_root_f64((double)rho, d1 * d1 + d2 * d2, (double)E, (double)zbar, 0.5 * dt * Kc, gamma - 1.0, q, Ti);
+}
+
 // Eq. (2.8): U^{n+1} = Ubar + dt/2 S(U^{n+1}).  Shallow water: no mass source,
 // so the momentum update is explicit in h^{n+1} = hbar.  Reactive: a scalar
 // equation g(z) = z - zbar + dt/2 R(z) = 0 in z = rho*Y, solved by Newton's
@@ -333,41 +375,24 @@ __device__ __forceinline__ unsigned implicit_moment(const Phys<R>& K, const R* U
     if (Ubar[D + 2] == R(0)) return 0u;
     if constexpr (sizeof(R) == 4) {
       float zf;
-      const int rc = react_root_f32<D>(K, Ubar, dt, &zf);
+      const int rc = react_root_f32<D>(K, Ubar, hdt, &zf);
       if (rc == 0) {
         Un[D + 2] = zf;
         return 0u;
       }
       if (rc == 2) return ST_NOROOT;  // z = zbar, as the FP64 path leaves it
     }
-    const double zbar = (double)Ubar[D + 2];
-    const double rho = (double)Ubar[0], E = (double)Ubar[D + 1];
-    const double m1 = (double)Ubar[1], m2 = D == 2 ? (double)Ubar[2] : 0.0;
-    const double momsq = m1 * m1 + m2 * m2;
-    const double hk = 0.5 * dt * K.K;
-    const double dTdz = -(K.gamma_d - 1.0) * K.q_d / rho;
-    const double e0 = (K.gamma_d - 1.0) * (E - 0.5 * momsq / rho) / rho;  // T at z = 0
-    double lo = zbar < 0.0 ? zbar : 0.0, hi = zbar < 0.0 ? 0.0 : zbar;
-    double z = zbar / (1.0 + hk * exp(-K.Ti / (e0 + dTdz * zbar)));
-    unsigned st = ST_NOROOT;
-    if (z != z) return ST_NOROOT;  // non-finite state: z = zbar, flagged (no iteration)
-    for (int it = 0; it < 60; it++) {
-      double T = e0 + dTdz * z;
-      double ex = exp(-K.Ti / T);
-      double gz = z - zbar + hk * z * ex;
-      if (gz == 0.0) { st = 0u; break; }
-      if (gz > 0.0) hi = z; else lo = z;
-      double dg = 1.0 + hk * ex * (1.0 + z * K.Ti / (T * T) * dTdz);
-      double zn = z - gz / dg;
-      // converged when the Newton step is below the tolerance; tested before
-      // the bracket guard, since z itself has just become a bracket end and a
-      // sub-resolution step lands on it
-      if (fabs(zn - z) <= 1e-15 * fabs(zbar)) { z = zn; st = 0u; break; }
-      if (!(zn > lo && zn < hi)) zn = 0.5 * (lo + hi);
-      z = zn;
+    RootF64 rt;
+    if constexpr (sizeof(R) == 4) {
+      rt = react_root_f64_fallback(Ubar[0], Ubar[1], D == 2 ? Ubar[2] : 0.0f, Ubar[D + 1], Ubar[D + 2], dt, K.K,
+                                   K.gamma_d, K.q_d, K.Ti);
+    } else {
+      const double m1 = (double)Ubar[1], m2 = D == 2 ? (double)Ubar[2] : 0.0;
+      rt = react_root_f64((double)Ubar[0], m1 * m1 + m2 * m2, (double)Ubar[D + 1], (double)Ubar[D + 2],
+                          0.5 * dt * K.K, K.gamma_d - 1.0, K.q_d, K.Ti);
     }
-    Un[D + 2] = R(z);
-    return st;
+    Un[D + 2] = R(rt.z);
+    return rt.st;
   } else {
     return 0u;
   }
