@@ -26,6 +26,16 @@ constexpr int XPAD = 8;
 constexpr int NGHOST = 4;
 
 // Problem constants, passed by value to every kernel.
+// FP32 copies of the physical constants, rounded once on the host: the FP32
+// path reads them as they are (a conversion from the double fields on the
+// device is an FP64-pipe instruction, and the compiler may repeat it per row
+// instead of keeping the value in a register)
+struct PhysConstF {
+  float gamma, gm1, g, half_g, h_dry, cmin, q, adv0, adv1, dx;
+  float bed_amp, bed_inv_w2, bed_m2_inv_w2, xb, yb, K, Ti;
+  float omega_fixed;
+};
+
 struct DevParams {
   int nx, ny;        // ny = 1 in 1D
   int pitch;         // elements between rows of one distribution plane (>= nx + 2*XPAD)
@@ -43,6 +53,7 @@ struct DevParams {
   int has_react;     // K != 0           a double would be an FP64 instruction)
   int omega_mode;    // 0 adaptive, 1 fixed
   double omega_fixed;
+  PhysConstF pf;
 };
 
 // Step-control block in device memory.  Step n reads slot n % 3, folds the

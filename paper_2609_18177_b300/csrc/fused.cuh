@@ -142,7 +142,10 @@ __device__ __forceinline__ Coef2D<R> make_coef2d(const StepCoef& cf, const DevPa
   c.akk[0] = R(cf.a0);
   c.akk[1] = c.akk[3] = R(cf.aj[0]);
   c.akk[2] = c.akk[4] = R(cf.aj[1]);
-  c.om_fixed = R(P.omega_fixed);
+  if constexpr (sizeof(R) == 4)
+    c.om_fixed = P.pf.omega_fixed;
+  else
+    c.om_fixed = P.omega_fixed;
   c.dt = cf.dt;
   c.fixed_omega = P.omega_mode == 1;
   return c;

@@ -81,6 +81,25 @@ inline DevParams make_devparams(const lbmh_problem* p, int pitch) {
   P.has_react = p->K != 0.0;
   P.omega_mode = p->omega_mode;
   P.omega_fixed = p->omega_fixed;
+  PhysConstF& f = P.pf;
+  f.gamma = (float)P.gamma;
+  f.gm1 = (float)(P.gamma - 1.0);
+  f.g = (float)P.g;
+  f.half_g = (float)(0.5 * P.g);
+  f.h_dry = (float)P.h_dry;
+  f.cmin = (float)sqrt(P.g * P.h_dry);
+  f.q = (float)P.q;
+  f.adv0 = (float)P.adv[0];
+  f.adv1 = (float)P.adv[1];
+  f.dx = (float)P.dx;
+  f.bed_amp = (float)P.bed_amp;
+  f.bed_inv_w2 = (float)(1.0 / P.bed_w2);
+  f.bed_m2_inv_w2 = (float)(-2.0 / P.bed_w2);
+  f.xb = (float)(P.x0 + 0.5 * P.dx - P.bed_xc);
+  f.yb = (float)(P.y0 + 0.5 * P.dx - P.bed_yc);
+  f.K = (float)P.K;
+  f.Ti = (float)P.Ti;
+  f.omega_fixed = (float)P.omega_fixed;
   return P;
 }
 

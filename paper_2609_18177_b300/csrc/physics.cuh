@@ -46,27 +46,48 @@ struct Phys {
 template <class R>
 __device__ __forceinline__ Phys<R> make_phys(const DevParams& P) {
   Phys<R> k;
-  k.gamma = R(P.gamma);
-  k.gm1 = R(P.gamma - 1.0);
-  k.g = R(P.g);
-  k.half_g = R(0.5 * P.g);
-  k.h_dry = R(P.h_dry);
-  k.cmin = R(sqrt(P.g * P.h_dry));
-  k.q = R(P.q);
-  k.adv0 = R(P.adv[0]);
-  k.adv1 = R(P.adv[1]);
-  k.dx = R(P.dx);
-  k.bed_amp = R(P.bed_amp);
-  k.bed_inv_w2 = R(1.0 / P.bed_w2);
-  k.bed_m2_inv_w2 = R(-2.0 / P.bed_w2);
-  k.xb = R(P.x0 + 0.5 * P.dx - P.bed_xc);
-  k.yb = R(P.y0 + 0.5 * P.dx - P.bed_yc);
+  if constexpr (sizeof(R) == 4) {  // the host-rounded FP32 constants
+    const PhysConstF& f = P.pf;
+    k.gamma = f.gamma;
+    k.gm1 = f.gm1;
+    k.g = f.g;
+    k.half_g = f.half_g;
+    k.h_dry = f.h_dry;
+    k.cmin = f.cmin;
+    k.q = f.q;
+    k.adv0 = f.adv0;
+    k.adv1 = f.adv1;
+    k.dx = f.dx;
+    k.bed_amp = f.bed_amp;
+    k.bed_inv_w2 = f.bed_inv_w2;
+    k.bed_m2_inv_w2 = f.bed_m2_inv_w2;
+    k.xb = f.xb;
+    k.yb = f.yb;
+    k.Kr = f.K;
+    k.Tir = f.Ti;
+  } else {
+    k.gamma = P.gamma;
+    k.gm1 = P.gamma - 1.0;
+    k.g = P.g;
+    k.half_g = 0.5 * P.g;
+    k.h_dry = P.h_dry;
+    k.cmin = sqrt(P.g * P.h_dry);
+    k.q = P.q;
+    k.adv0 = P.adv[0];
+    k.adv1 = P.adv[1];
+    k.dx = P.dx;
+    k.bed_amp = P.bed_amp;
+    k.bed_inv_w2 = 1.0 / P.bed_w2;
+    k.bed_m2_inv_w2 = -2.0 / P.bed_w2;
+    k.xb = P.x0 + 0.5 * P.dx - P.bed_xc;
+    k.yb = P.y0 + 0.5 * P.dx - P.bed_yc;
+    k.Kr = P.K;
+    k.Tir = P.Ti;
+  }
   k.gamma_d = P.gamma;
   k.q_d = P.q;
   k.K = P.K;
   k.Ti = P.Ti;
-  k.Kr = R(P.K);
-  k.Tir = R(P.Ti);
   k.bed = P.has_bed != 0;
   k.react = P.has_react != 0;
   return k;
