@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-n", type=int, default=384)
-    ap.add_argument("--workload", default="riemann2d", choices=["riemann2d", "batched", "served"])
+    ap.add_argument("--workload", default="riemann2d", choices=["riemann2d", "batched", "served", "lines1d"])
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--sample", type=int, default=16)
     ap.add_argument("--requests", type=int, default=60)
@@ -369,12 +369,58 @@ def run_served(args):
     }
 
 
+def run_lines1d(args):
+    """The 1D lattices: linear advection of a square pulse (N = 400, periodic,
+    CFL 0.5, FP64, the 800 steps to T = 1) and the Sod and Shu-Osher shock tubes
+    (CFL 0.3, N = 2^12 .. 2^18, FP64 and FP32 distributions).  They fit in L2
+    (<= 18.9 MB per copy), so the bound is launch latency and L2 bandwidth, not
+    HBM: each case reports MLUPS and the algorithmic bytes per second
+    (2 Q m sizeof(real) per node update) as L2 GB/s."""
+    import torch
+    from paper_2609_18177_b300 import lbmh
+    from paper_2609_18177_b300 import workloads as W
+    cases = [("advection pulse", W.advection_1d(400, profile="pulse", cfl=0.5), lbmh.FP64, 800)]
+    for n in (1 << 12, 1 << 14, 1 << 16, 1 << 18):
+        for name, gen in (("sod", W.sod), ("shu-osher", W.shu_osher)):
+            for prec in (lbmh.FP64, lbmh.FP32):
+                cases.append((name, gen(n), prec, args.steps))
+    out = []
+    stream = torch.cuda.current_stream()
+    for name, (pb, U0), prec, steps in cases:
+        s = lbmh.Solver(pb.with_(precision=prec), precision=prec, kernel=lbmh.KERNEL_FUSED).set_state(U0)
+        s.step(max(3, args.warmup))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = s.info()["status"]
+        s.close()
+        elem = 4 if prec == lbmh.FP32 else 8
+        bytes_step = 2 * 3 * pb.nfields * elem * pb.nodes
+        out.append({"case": name, "n": pb.nx, "dtype": "f32" if prec == lbmh.FP32 else "f64", "steps": steps,
+                    "us_per_step": ms * 1e3 / steps, "mlups": pb.nodes * steps / (ms / 1e3) / 1e6,
+                    "l2_gbs": bytes_step * steps / (ms / 1e3) / 1e9, "status": st})
+    head = [c for c in out if c["case"] == "sod" and c["n"] == 1 << 18 and c["dtype"] == "f32"][0]
+    return {
+        "metric": METRIC, "workload": "lines1d", "value": head["mlups"], "unit": "MLUPS",
+        "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "1D lattices (D1Q3): advection pulse N=400 FP64 800 steps; Sod and Shu-Osher "
+                               "N=2^12..2^18, CFL 0.3, FP64 and FP32; value = Sod 2^18 FP32",
+                   "l2": "L2-resident (<= 18.9 MB per copy): reported as L2 GB/s, not an HBM fraction",
+                   "launch": "one launch per step, runs of 24 steps replayed as a CUDA graph"},
+        "cases": out,
+    }
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in ("batched", "served"):
-        line = run_batched(args) if args.workload == "batched" else run_served(args)
+    if args.workload in ("batched", "served", "lines1d"):
+        line = {"batched": run_batched, "served": run_served, "lines1d": run_lines1d}[args.workload](args)
         print(json.dumps(line), flush=True)
         return 0
     import torch
