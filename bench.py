@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-n", type=int, default=384)
     ap.add_argument("--workload", default="riemann2d", choices=["riemann2d", "batched", "served", "lines1d"])
+    ap.add_argument("--lattice", default="riemann2d", choices=["riemann2d", "reactive", "dambreak"],
+                    help="single-lattice line: the lattice stepped (default: the 2D Riemann roofline run)")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--sample", type=int, default=16)
     ap.add_argument("--requests", type=int, default=60)
@@ -78,9 +80,9 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-def recorded_traffic(kernel_name):
+def recorded_traffic(kernel_name, lattice, n, precision):
     """dram bytes per launch from a committed ncu capture, valid only for the
-    kernel source it was taken on."""
+    kernel source, lattice, size and precision it was taken on."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -88,6 +90,8 @@ def recorded_traffic(kernel_name):
         d = json.load(fh)
     ent = d.get(kernel_name)
     if not ent or ent.get("source_hash") != source_hash():
+        return None
+    if (ent.get("lattice", "riemann2d"), ent.get("n", 8192), ent.get("precision", "fp32")) != (lattice, n, precision):
         return None
     return ent.get("bytes_per_launch")
 
@@ -135,9 +139,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload(n, seed, precision):
+LATTICES = {
+    "riemann2d": "2D Euler seeded 4-quadrant Riemann {n}x{n}, outflow, CFL 0.9",
+    "reactive": "2D reactive Euler circle (Example 5.12 states and constants) {n}x{n}, outflow, CFL 0.9",
+    "dambreak": "2D shallow-water dam break over a Gaussian bump {n}x{n}, outflow, CFL 0.4",
+}
+
+
+def workload(n, seed, precision, lattice="riemann2d"):
     from paper_2609_18177_b300 import workloads as W
-    pb, U0 = W.riemann_2d_seeded(n, seed=seed, cfl=0.9)
+    if lattice == "reactive":
+        pb, U0 = W.reactive_circle(n)
+    elif lattice == "dambreak":
+        pb, U0 = W.dam_break_bump(n)
+    else:
+        pb, U0 = W.riemann_2d_seeded(n, seed=seed, cfl=0.9)
     pb = pb.with_(precision=1 if precision == "fp32" else 0)
     return pb, U0
 
@@ -146,7 +162,7 @@ def cpu_baseline(args, seconds):
     """The FP64 oracle as it stands, on a bounded sample of the same workload."""
     import oracle
     n = args.ref_n
-    pb, U0 = workload(n, args.seed, "fp64")
+    pb, U0 = workload(n, args.seed, "fp64", args.lattice)
     r = oracle.Run(pb, U0)
     r.step(1)
     steps = 0
@@ -160,7 +176,7 @@ def cpu_baseline(args, seconds):
     mlups = pb.nodes * steps / el / 1e6
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n}x{n} grid of the same seeded 2D Riemann workload, FP64, {steps} steps "
+            "sample": f"{n}x{n} grid of the same workload ({args.lattice}), FP64, {steps} steps "
                       f"({el:.1f} s), OpenMP over rows"}
 
 
@@ -170,7 +186,7 @@ def run_reference(args):
         return 0
     import oracle
     n = args.ref_n
-    pb, U0 = workload(n, args.seed, "fp64")
+    pb, U0 = workload(n, args.seed, "fp64", args.lattice)
     r = oracle.Run(pb, U0)
     r.step(args.warmup)
     t0 = time.perf_counter()
@@ -436,7 +452,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    pb, U0 = workload(args.n, args.seed, args.precision)
+    pb, U0 = workload(args.n, args.seed, args.precision, args.lattice)
     kernel = {"auto": lbmh.KERNEL_AUTO, "fused": lbmh.KERNEL_FUSED, "unfused": lbmh.KERNEL_UNFUSED}[args.kernel]
     prec = lbmh.FP32 if args.precision == "fp32" else lbmh.FP64
     U0_dev = torch.from_numpy(U0).to(dev)
@@ -521,15 +537,14 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == lbmh.FP32 else "f64", "data": "synthetic",
-            "config": {"workload": f"2D Euler seeded 4-quadrant Riemann {args.n}x{args.n}, outflow, "
-                                   f"CFL 0.9, D2Q5 {args.precision} distributions",
+            "config": {"workload": LATTICES[args.lattice].format(n=args.n) + f", D2Q5 {args.precision} distributions",
                        "n": args.n, "seed": args.seed, "kernel": kernel_used,
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (no flush needed)",
                        "hbm_gbs_step": achieved},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": recorded_traffic(kname),
+                         "traffic": recorded_traffic(kname, args.lattice, args.n, args.precision),
                          "algorithmic_bytes_per_launch": bytes_per_launch},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
