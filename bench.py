@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--workload", default="riemann2d", choices=["riemann2d", "batched", "served", "lines1d"])
     ap.add_argument("--lattice", default="riemann2d", choices=["riemann2d", "reactive", "dambreak"],
                     help="single-lattice line: the lattice stepped (default: the 2D Riemann roofline run)")
+    ap.add_argument("--case", default=None,
+                    help="lines1d: run one case only, NAME:N:DTYPE (e.g. sod:262144:f32)")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--sample", type=int, default=16)
     ap.add_argument("--requests", type=int, default=60)
@@ -400,6 +402,10 @@ def run_lines1d(args):
         for name, gen in (("sod", W.sod), ("shu-osher", W.shu_osher)):
             for prec in (lbmh.FP64, lbmh.FP32):
                 cases.append((name, gen(n), prec, args.steps))
+    if args.case:
+        cname, cn, cdt = args.case.split(":")
+        cases = [c for c in cases if c[0].startswith(cname) and c[1][0].nx == int(cn)
+                 and (c[2] == lbmh.FP32) == (cdt == "f32")]
     out = []
     stream = torch.cuda.current_stream()
     for name, (pb, U0), prec, steps in cases:
@@ -419,7 +425,7 @@ def run_lines1d(args):
         out.append({"case": name, "n": pb.nx, "dtype": "f32" if prec == lbmh.FP32 else "f64", "steps": steps,
                     "us_per_step": ms * 1e3 / steps, "mlups": pb.nodes * steps / (ms / 1e3) / 1e6,
                     "l2_gbs": bytes_step * steps / (ms / 1e3) / 1e9, "status": st})
-    head = [c for c in out if c["case"] == "sod" and c["n"] == 1 << 18 and c["dtype"] == "f32"][0]
+    head = ([c for c in out if c["case"] == "sod" and c["n"] == 1 << 18 and c["dtype"] == "f32"] or out)[0]
     return {
         "metric": METRIC, "workload": "lines1d", "value": head["mlups"], "unit": "MLUPS",
         "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",

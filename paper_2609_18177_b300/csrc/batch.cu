@@ -82,10 +82,7 @@ __global__ void __launch_bounds__(FT) k_batch2d(const BatchInst* insts, const Ba
       if (pp.aborted) st |= ST_TIMEOUT;
     }
     // this segment's side outputs: speed bound of its instance, FP64 sums
-    double usum[M];
-#pragma unroll
-    for (int c = 0; c < M; c++) usum[c] = acc[c].value();
-    block_side_outputs_to<M>((double)sp0, (double)sp1, usum, ctl, (slot + 1) % 3, seg_sums + (long long)i * M, st);
+    fused_side_outputs_to<M, R>(sp0, sp1, acc, ctl, (slot + 1) % 3, seg_sums + (long long)i * M, st);
     if (sg.owner && t == 0) advance_ctl<2>(ctl, slot, cf);
   }
   pipe2d_drain<SYS, R, PREF, 1>(pp);

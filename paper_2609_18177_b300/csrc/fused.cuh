@@ -22,6 +22,8 @@
 #include <cuda.h>
 #include <stdlib.h>
 
+#include <algorithm>
+
 #include "physics.cuh"
 #include "unfused.cuh"
 
@@ -111,15 +113,86 @@ __device__ __forceinline__ void tma_load_row(const CUtensorMap* tm, uint32_t dst
       : "memory");
 }
 
-// Block-level reduction of the fused kernels' side outputs (max speeds in R,
-// compensated sums already converted to FP64 per thread).
+// Block-level reduction of the fused kernels' side outputs: the speed
+// bounds (NaN-propagating maxima: a NaN speed marks a non-physical state) go
+// to the control block's slot slot1, the block's FP64-quality sums of U to
+// dst[0..M), the status bits to the control block.  In FP32 the compensated
+// (hi, lo) pairs are reduced across the warp with FP32 TwoSum steps and only
+// thread 0 works in FP64 (the FP64 pipe runs 2 lanes/clock/SM on B300, so a
+// warp-wide FP64 shuffle reduction costs more than the step's other per-block
+// work).
+__device__ __forceinline__ float nanmax_f(float a, float b) { return (a > b || a != a) ? a : b; }
+__device__ __forceinline__ double nanmax_d(double a, double b) { return (a > b || a != a) ? a : b; }
+
+template <int M, class R>
+__device__ __forceinline__ void fused_side_outputs_to(R sp0, R sp1, const Acc<R>* acc, Ctl* ctl, int slot1,
+                                                      double* dst, unsigned st) {
+  if constexpr (sizeof(R) == 8) {
+    double usum[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) usum[c] = acc[c].value();
+    block_side_outputs_to<M>((double)sp0, (double)sp1, usum, ctl, slot1, dst, st);
+  } else {
+    __shared__ float s_hi[32][M], s_lo[32][M], s_sp[32][2];
+    __shared__ unsigned s_st;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (threadIdx.x == 0) s_st = 0u;
+    float hi[M], lo[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) {
+      hi[c] = acc[c].hi;
+      lo[c] = acc[c].lo;
+    }
+    float m0 = sp0, m1 = sp1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      m0 = nanmax_f(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+      m1 = nanmax_f(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+#pragma unroll
+      for (int c = 0; c < M; c++) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi[c], o);
+        const float ol = __shfl_xor_sync(0xffffffffu, lo[c], o);
+        const float sum = hi[c] + oh, bp = sum - hi[c];
+        const float err = (hi[c] - (sum - bp)) + (oh - bp);
+        hi[c] = sum;
+        lo[c] += ol + err;
+      }
+    }
+    __syncthreads();
+    if (st) atomicOr(&s_st, st);
+    if (lane == 0) {
+      s_sp[wid][0] = m0;
+      s_sp[wid][1] = m1;
+#pragma unroll
+      for (int c = 0; c < M; c++) {
+        s_hi[wid][c] = hi[c];
+        s_lo[wid][c] = lo[c];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double d0 = 0.0, d1 = 0.0, a[M];
+#pragma unroll
+      for (int c = 0; c < M; c++) a[c] = 0.0;
+      for (int w2 = 0; w2 < nw; w2++) {
+        d0 = nanmax_d(d0, (double)s_sp[w2][0]);
+        d1 = nanmax_d(d1, (double)s_sp[w2][1]);
+#pragma unroll
+        for (int c = 0; c < M; c++) a[c] += (double)s_hi[w2][c] + (double)s_lo[w2][c];
+      }
+      atomic_max_nonneg(&ctl->amax[slot1][0], d0);
+      atomic_max_nonneg(&ctl->amax[slot1][1], d1);
+#pragma unroll
+      for (int c = 0; c < M; c++) dst[c] = a[c];
+      if (s_st) atomicOr(&ctl->status, s_st);
+    }
+  }
+}
+
 template <int M, class R>
 __device__ __forceinline__ void fused_side_outputs(R sp0, R sp1, const Acc<R>* acc, Ctl* ctl, int slot1,
                                                    double* partials, unsigned st) {
-  double usum[M];
-#pragma unroll
-  for (int c = 0; c < M; c++) usum[c] = acc[c].value();
-  block_side_outputs<M>((double)sp0, (double)sp1, usum, ctl, slot1, partials, st);
+  fused_side_outputs_to<M, R>(sp0, sp1, acc, ctl, slot1, partials + (long long)blockIdx.x * M, st);
 }
 
 // Coefficients of one step of one lattice, in the arithmetic type of the path
@@ -571,6 +644,17 @@ __global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensor
 }
 
 // 1D: one CTA per chunk of FW nodes; lane t holds node x0 - 4 + t
+// Coefficients of one 1D step in the path's type, computed by one thread
+template <class R>
+struct Coef1D {
+  R a0, a1, inv2l, hdt, al0, om_fixed;
+  double dt;
+};
+
+// One CTA of 128 threads works through chunks of 120 output nodes (lane t
+// holds node chunk*120 - 4 + t), chunk = blockIdx.x, blockIdx.x + gridDim.x, ...:
+// the step coefficients (FP64, one thread) and the side-output reduction are
+// paid once per CTA, not once per chunk.
 template <int SYS, class R>
 __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl* ctl, int slot, double* partials) {
   constexpr int M = Fields<SYS, 1>::M, Q = 3;
@@ -578,104 +662,125 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
   __shared__ R Us[M][FT];
   __shared__ R nus[FT];
   __shared__ R p1s[M][FT], p2s[M][FT];
+  __shared__ Coef1D<R> s_cf;
+  __shared__ int s_active, s_par;
   const int t = threadIdx.x;
-  const StepCoef cf = step_coef<1>(P, ctl, slot);
-  if (!cf.active) {
-    if (blockIdx.x == 0 && t == 0) advance_ctl<1>(ctl, slot, cf);
-    return;
+  if (t == 0) {
+    const StepCoef cf = step_coef<1>(P, ctl, slot);
+    s_active = cf.active;
+    if (!cf.active) {
+      if (blockIdx.x == 0) advance_ctl<1>(ctl, slot, cf);
+    } else {
+      s_cf.a0 = R(cf.a0);
+      s_cf.a1 = R(cf.aj[0]);
+      s_cf.inv2l = R(1.0 / (2.0 * cf.lam));
+      s_cf.hdt = R(0.5 * cf.dt);
+      s_cf.al0 = R(cf.alpha[0]);
+      if constexpr (sizeof(R) == 4)
+        s_cf.om_fixed = P.pf.omega_fixed;
+      else
+        s_cf.om_fixed = P.omega_fixed;
+      s_cf.dt = cf.dt;
+      s_par = ctl->parity[slot];
+      if (blockIdx.x == 0) advance_ctl<1>(ctl, slot, cf);
+    }
   }
+  __syncthreads();
+  if (!s_active) return;
+  const Coef1D<R> cf = s_cf;
   const Phys<R> K = make_phys<R>(P);
-  const int par = ctl->parity[slot];
-  const R* fin = buf[par];
-  R* fout = buf[par ^ 1];
-  const int gx = blockIdx.x * FW - 4 + t;
-  const int mx = map_index(gx, P.nx, P.bc[0], P.bc[1]);
-  R f[Q][M], U[M];
-#pragma unroll
-  for (int c = 0; c < M; c++) {
-    R s = R(0);
-#pragma unroll
-    for (int k = 0; k < Q; k++) {
-      f[k][c] = fin[(long long)(k * M + c) * P.plane + mx + XPAD];
-      s += f[k][c];
-    }
-    U[c] = s;
-    Us[c][t] = s;
-  }
-  __syncthreads();
-  Prim<R> w = primitives<SYS, 1, R>(K, U);
-  R nu = R(0);
-  if (t >= 1 && t < FT - 1) {
-    R dm[M], dp[M];
-#pragma unroll
-    for (int c = 0; c < M; c++) {
-      dm[c] = U[c] - Us[c][t - 1];
-      dp[c] = Us[c][t + 1] - U[c];
-    }
-    nu = theta_sum<SYS, 1, R>(K, w, 0, dm, dp);
-  }
-  nus[t] = nu;
-  __syncthreads();
-  R om = R(P.omega_fixed);
-  if (P.omega_mode != 1 && t >= 1 && t < FT - 1) om = R(1) + fdiv(R(1), R(1) + (nus[t - 1] + nus[t] + nus[t + 1]));
-  const R a0 = R(cf.a0), a1 = R(cf.aj[0]), inv2l = R(1.0 / (2.0 * cf.lam)), hdt = R(0.5 * cf.dt);
-  const R al0 = R(cf.alpha[0]);
-  R F[M], S[M], post0[M];
-  flux<SYS, 1, R>(K, U, w, 0, F);
-  if constexpr (SRC) source<SYS, 1, R>(K, U, K.xb + R(mx) * K.dx, R(0), S);
-#pragma unroll
-  for (int c = 0; c < M; c++) {
-    R feq0 = a0 * U[c], feq1 = (al0 * U[c] + F[c]) * inv2l, feq2 = (al0 * U[c] - F[c]) * inv2l;
-    post0[c] = f[0][c] - om * (f[0][c] - feq0);
-    R q1 = f[1][c] - om * (f[1][c] - feq1), q2 = f[2][c] - om * (f[2][c] - feq2);
-    if constexpr (SRC) {
-      post0[c] += hdt * a0 * S[c];
-      q1 += hdt * a1 * S[c];
-      q2 += hdt * a1 * S[c];
-    }
-    p1s[c][t] = q1;
-    p2s[c][t] = q2;
-  }
-  __syncthreads();
+  const R* fin = buf[s_par];
+  R* fout = buf[s_par ^ 1];
+  const R a0 = cf.a0, a1 = cf.a1, inv2l = cf.inv2l, hdt = cf.hdt, al0 = cf.al0;
+  const bool fixed_omega = P.omega_mode == 1;
   R sp0 = R(0);
   Acc<R> acc[M];
 #pragma unroll
   for (int c = 0; c < M; c++) acc[c].init();
   unsigned st = 0u;
-  if (t >= 4 && t < FT - 4 && gx < P.nx) {
-    R Fk[Q][M], Ubar[M], Un[M], Sn[M], Uo[M];
+  const int nchunks = (P.nx + FW - 1) / FW;
+  for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int gx = ch * FW - 4 + t;
+    const int mx = map_index(gx, P.nx, P.bc[0], P.bc[1]);
+    R f[Q][M], U[M];
 #pragma unroll
     for (int c = 0; c < M; c++) {
-      Fk[0][c] = post0[c];
-      Fk[1][c] = p1s[c][t - 1];
-      Fk[2][c] = p2s[c][t + 1];
-      Ubar[c] = Fk[0][c] + Fk[1][c] + Fk[2][c];
-    }
-    const R xo = K.xb + R(gx) * K.dx;
-    if constexpr (SRC) {
-      st |= implicit_moment<SYS, 1, R>(K, Ubar, xo, R(0), cf.dt, hdt, Un);
-      source<SYS, 1, R>(K, Un, xo, R(0), Sn);
-    }
-    const R ak[3] = {a0, a1, a1};
+      R sum = R(0);
 #pragma unroll
-    for (int c = 0; c < M; c++) Uo[c] = R(0);
-#pragma unroll
-    for (int k = 0; k < Q; k++)
+      for (int k = 0; k < Q; k++) {
+        f[k][c] = fin[(long long)(k * M + c) * P.plane + mx + XPAD];
+        sum += f[k][c];
+      }
+      U[c] = sum;
+      Us[c][t] = sum;
+    }
+    __syncthreads();
+    Prim<R> w = primitives<SYS, 1, R>(K, U);
+    R nu = R(0);
+    if (t >= 1 && t < FT - 1) {
+      R dm[M], dp[M];
 #pragma unroll
       for (int c = 0; c < M; c++) {
-        R v = Fk[k][c];
-        if constexpr (SRC) v += hdt * ak[k] * Sn[c];
-        fout[(long long)(k * M + c) * P.plane + gx + XPAD] = v;
-        Uo[c] += v;
+        dm[c] = U[c] - Us[c][t - 1];
+        dp[c] = Us[c][t + 1] - U[c];
       }
-    Prim<R> wn = primitives<SYS, 1, R>(K, Uo);
-    sp0 = max_speed<SYS, 1, R>(K, wn, 0);
+      nu = theta_sum<SYS, 1, R>(K, w, 0, dm, dp);
+    }
+    nus[t] = nu;
+    __syncthreads();
+    R om = cf.om_fixed;
+    if (!fixed_omega && t >= 1 && t < FT - 1) om = R(1) + fdiv(R(1), R(1) + (nus[t - 1] + nus[t] + nus[t + 1]));
+    R F[M], S[M], post0[M];
+    flux<SYS, 1, R>(K, U, w, 0, F);
+    if constexpr (SRC) source<SYS, 1, R>(K, U, K.xb + R(mx) * K.dx, R(0), S);
 #pragma unroll
-    for (int c = 0; c < M; c++) acc[c].add(Uo[c]);
-    st |= state_status<SYS, 1, R>(Uo, wn);
+    for (int c = 0; c < M; c++) {
+      R feq0 = a0 * U[c], feq1 = (al0 * U[c] + F[c]) * inv2l, feq2 = (al0 * U[c] - F[c]) * inv2l;
+      post0[c] = f[0][c] - om * (f[0][c] - feq0);
+      R q1 = f[1][c] - om * (f[1][c] - feq1), q2 = f[2][c] - om * (f[2][c] - feq2);
+      if constexpr (SRC) {
+        post0[c] += hdt * a0 * S[c];
+        q1 += hdt * a1 * S[c];
+        q2 += hdt * a1 * S[c];
+      }
+      p1s[c][t] = q1;
+      p2s[c][t] = q2;
+    }
+    __syncthreads();
+    if (t >= 4 && t < FT - 4 && gx < P.nx) {
+      R Fk[Q][M], Ubar[M], Un[M], Sn[M], Uo[M];
+#pragma unroll
+      for (int c = 0; c < M; c++) {
+        Fk[0][c] = post0[c];
+        Fk[1][c] = p1s[c][t - 1];
+        Fk[2][c] = p2s[c][t + 1];
+        Ubar[c] = Fk[0][c] + Fk[1][c] + Fk[2][c];
+      }
+      const R xo = K.xb + R(gx) * K.dx;
+      if constexpr (SRC) {
+        st |= implicit_moment<SYS, 1, R>(K, Ubar, xo, R(0), cf.dt, hdt, Un);
+        source<SYS, 1, R>(K, Un, xo, R(0), Sn);
+      }
+      const R ak[3] = {a0, a1, a1};
+#pragma unroll
+      for (int c = 0; c < M; c++) Uo[c] = R(0);
+#pragma unroll
+      for (int k = 0; k < Q; k++)
+#pragma unroll
+        for (int c = 0; c < M; c++) {
+          R v = Fk[k][c];
+          if constexpr (SRC) v += hdt * ak[k] * Sn[c];
+          fout[(long long)(k * M + c) * P.plane + gx + XPAD] = v;
+          Uo[c] += v;
+        }
+      Prim<R> wn = primitives<SYS, 1, R>(K, Uo);
+      sp0 = rmax(sp0, max_speed<SYS, 1, R>(K, wn, 0));
+#pragma unroll
+      for (int c = 0; c < M; c++) acc[c].add(Uo[c]);
+      st |= state_status<SYS, 1, R>(Uo, wn);
+    }
   }
   fused_side_outputs<M, R>(sp0, R(0), acc, ctl, (slot + 1) % 3, partials, st);
-  if (blockIdx.x == 0 && t == 0) advance_ctl<1>(ctl, slot, cf);
 }
 
 // ---------------------------------------------------------------------------
@@ -768,7 +873,8 @@ inline int fused_setup(FusedPlan& fp, const DevParams& P, void* const* fbuf) {
     fp.cpt = 1;
     fp.strips = 1;
     fp.smem = 0;
-    fp.blocks = (P.nx + FW - 1) / FW;
+    // at most 4 CTAs per SM: chunks beyond that loop inside the CTAs
+    fp.blocks = std::min((P.nx + FW - 1) / FW, 4 * (sms > 0 ? sms : 148));
     return 0;
   }
   return default_cpt<R>() == 2 ? fused2d_prepare<SYS, R, 2>(fp, P, fbuf, sms)
