@@ -98,6 +98,23 @@ def recorded_traffic(kernel_name, lattice, n, precision):
     return ent.get("bytes_per_launch")
 
 
+def max_over_ranks(ms, world, device=None):
+    """The slowest rank's time (all ranks get it); identity for one rank."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, ms):
+    """Whole-job MLUPS of `world` replicas that each updated units_per_rank
+    nodes, timed by the slowest rank (weak scaling)."""
+    return units_per_rank * world / (ms / 1e3) / 1e6
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -487,14 +504,10 @@ def main():
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     info = solver.info()
     nodes = pb.nodes
-    value = nodes * args.steps * world / (ms / 1e3) / 1e6
+    value = replica_throughput(nodes * args.steps, world, ms)
     elem = 4 if prec == lbmh.FP32 else 8
     Q, m = 2 * pb.dim + 1, pb.nfields
     bytes_per_launch = 2 * Q * m * elem * nodes
@@ -522,13 +535,9 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        ms_e2e = max(e0.elapsed_time(e1), wall * 1e3)
-        if world > 1:
-            t = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
+        ms_e2e = max_over_ranks(max(e0.elapsed_time(e1), wall * 1e3), world, dev)
         ubytes = U0.nbytes
-        e2e = {"value": nodes * args.steps * world / (ms_e2e / 1e3) / 1e6, "unit": UNIT,
+        e2e = {"value": replica_throughput(nodes * args.steps, world, ms_e2e), "unit": UNIT,
                "h2d_bytes_per_step": ubytes / args.steps, "d2h_bytes_per_step": ubytes / args.steps,
                "note": "per solve: set_state from pinned host U0, K steps, moments to pinned host; "
                        "bytes are per step averaged over the K steps of one solve"}
