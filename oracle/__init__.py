@@ -18,7 +18,7 @@ import numpy as np
 from . import build as _build
 
 ADVECTION, EULER, SWE, REACTIVE, LINEAR = 0, 1, 2, 3, 4
-PERIODIC, OUTFLOW = 0, 1
+PERIODIC, OUTFLOW, REFLECT, INFLOW = 0, 1, 2, 3
 FLAG_NONPHYSICAL, FLAG_NOROOT = 1, 2
 
 
@@ -39,6 +39,8 @@ class _Problem(ctypes.Structure):
         ("A", ctypes.POINTER(ctypes.c_double)),
         ("omega_mode", ctypes.c_int), ("omega_fixed", ctypes.c_double),
         ("h_dry", ctypes.c_double),
+        ("sponge_width", ctypes.c_double),
+        ("u_in", ctypes.c_double * 8),
     ]
 
 
@@ -105,6 +107,9 @@ def _c_problem(pb):
     s.omega_mode = int(pb.omega_mode)
     s.omega_fixed = float(pb.omega_fixed)
     s.h_dry = float(pb.h_dry)
+    s.sponge_width = float(getattr(pb, "sponge_width", 0.0))
+    for i, v in enumerate(tuple(getattr(pb, "u_in", ()))[:8]):
+        s.u_in[i] = float(v)
     return s, keep
 
 

@@ -30,6 +30,16 @@
  *     index; U, nu, omega and post at a ghost node are then computed from those
  *     ghost distributions exactly as at an interior node.  A ghost node takes
  *     the position of the interior node it copies (relevant only to the bed).
+ *   - reflective wall (Example 5.13, y = +-15): a ghost node holds the
+ *     distributions of its mirror node with the velocities normal to the wall
+ *     exchanged (e_j <-> -e_j) and the normal momentum negated in every
+ *     distribution, so its U is the mirror state with the normal velocity
+ *     reversed; it sits at its own (mirrored) position.
+ *   - fixed inflow (Example 5.13, x = 40): a ghost node holds f^eq(U_in)
+ *     with the step's alpha and lambda.
+ *   - sponge (Example 5.13, 0 <= x <= 6; the paper gives no formula): omega
+ *     is blended toward 1, omega' = 1 + (omega - 1)(1 - sigma(x)), sigma =
+ *     (1 + cos(pi (x - x0)/L))/2 on [x0, x0 + L], 1 to the left, 0 to the right.
  *   - L = R^{-1} with right eigenvectors normalised as in Toro's textbook
  *     (first component 1 for acoustic/entropy waves, unit tangential velocity
  *     for shear waves, unit Y for the species wave); this oracle inverts R
@@ -54,6 +64,8 @@
 
 #define ORC_BC_PERIODIC 0
 #define ORC_BC_OUTFLOW 1
+#define ORC_BC_REFLECT 2
+#define ORC_BC_INFLOW 3
 
 #define ORC_OK 0
 #define ORC_ERR_ARG (-1)
@@ -81,6 +93,8 @@ typedef struct {
     int omega_mode;  /* 0 adaptive (paper), 1 fixed */
     double omega_fixed;
     double h_dry;
+    double sponge_width;  /* > 0: sponge layer of this width at x-lo */
+    double u_in[MAXM];    /* conservative state held by inflow ghost nodes */
 } orc_problem;
 
 /* ------------------------------------------------------------------ */
@@ -107,6 +121,12 @@ static int check_problem(const orc_problem *p) {
     if (p->nx < 1 || (p->dim == 2 && p->ny < 1)) return ORC_ERR_ARG;
     int m = orc_nfields(p);
     if (m < 1 || m > MAXM) return ORC_ERR_ARG;
+    for (int b = 0; b < 2 * p->dim; b++)
+        if (p->bc[b] < ORC_BC_PERIODIC || p->bc[b] > ORC_BC_INFLOW) return ORC_ERR_ARG;
+    if ((p->bc[0] == ORC_BC_REFLECT || p->bc[1] == ORC_BC_REFLECT || p->bc[2] == ORC_BC_REFLECT ||
+         p->bc[3] == ORC_BC_REFLECT) && (p->system == ORC_LINEAR || p->nx < GHOST || (p->dim == 2 && p->ny < GHOST)))
+        return ORC_ERR_ARG;
+    if (p->sponge_width < 0.0) return ORC_ERR_ARG;
     if ((p->bc[0] == ORC_BC_PERIODIC) != (p->bc[1] == ORC_BC_PERIODIC)) return ORC_ERR_ARG;
     if (p->dim == 2 && (p->bc[2] == ORC_BC_PERIODIC) != (p->bc[3] == ORC_BC_PERIODIC)) return ORC_ERR_ARG;
     if (p->dim == 2) {
@@ -119,9 +139,39 @@ static int check_problem(const orc_problem *p) {
 
 /* index of an extended (ghost) coordinate mapped back into the domain */
 static int map_index(int e, int n, int bc_lo, int bc_hi) {
-    if (e < 0) return bc_lo == ORC_BC_PERIODIC ? ((e % n) + n) % n : 0;
-    if (e >= n) return bc_hi == ORC_BC_PERIODIC ? e % n : n - 1;
+    if (e < 0) {
+        if (bc_lo == ORC_BC_PERIODIC) return ((e % n) + n) % n;
+        if (bc_lo == ORC_BC_REFLECT) return -1 - e;
+        return 0;
+    }
+    if (e >= n) {
+        if (bc_hi == ORC_BC_PERIODIC) return e % n;
+        if (bc_hi == ORC_BC_REFLECT) return 2 * n - 1 - e;
+        return n - 1;
+    }
     return e;
+}
+
+/* the boundary type a ghost coordinate e lies across (-1: interior) */
+static int ghost_side(int e, int n, int bc_lo, int bc_hi) {
+    if (e < 0) return bc_lo;
+    if (e >= n) return bc_hi;
+    return -1;
+}
+
+/* index of the momentum component along direction dir, -1 if none */
+static int momentum_index(const orc_problem *p, int dir) {
+    if (p->system == ORC_EULER || p->system == ORC_SWE || p->system == ORC_REACTIVE) return 1 + dir;
+    return -1;
+}
+
+/* sponge weight sigma(x): 1 left of x0, 0 beyond x0 + width */
+static double sponge_sigma(const orc_problem *p, double x) {
+    if (!(p->sponge_width > 0.0)) return 0.0;
+    double r = (x - p->x0) / p->sponge_width;
+    if (r <= 0.0) return 1.0;
+    if (r >= 1.0) return 0.0;
+    return 0.5 * (1.0 + cos(3.14159265358979323846 * r));
 }
 
 static double node_x(const orc_problem *p, int i) { return p->x0 + (i + 0.5) * mesh_dx(p); }
@@ -627,16 +677,40 @@ int orc_step(const orc_problem *p, const double *f, double *fn, double dt_cap, c
 #define EU(c, j, i) (((size_t)(c) * ey + (j)) * ex + (i))
     for (int ei = 0; ei < ex; ei++) srci[ei] = map_index(ei - G, nx, p->bc[0], p->bc[1]);
     for (int ej = 0; ej < ey; ej++) srcj[ej] = d == 2 ? map_index(ej - gy, ny, p->bc[2], p->bc[3]) : 0;
+    /* node positions of the extended grid: a periodic or outflow ghost sits
+     * where the node it copies sits, a reflecting ghost at its own position */
+    double *posx = malloc(sizeof(double) * ex), *posy = malloc(sizeof(double) * ey);
+    if (!posx || !posy) {
+        free(fe); free(Ue); free(nu); free(om); free(post); free(srcj); free(srci); free(posx); free(posy);
+        return ORC_ERR_MEM;
+    }
+    for (int ei = 0; ei < ex; ei++)
+        posx[ei] = ghost_side(ei - G, nx, p->bc[0], p->bc[1]) == ORC_BC_REFLECT ? node_x(p, ei - G) : node_x(p, srci[ei]);
+    for (int ej = 0; ej < ey; ej++)
+        posy[ej] = d == 2 && ghost_side(ej - gy, ny, p->bc[2], p->bc[3]) == ORC_BC_REFLECT ? node_y(p, ej - gy)
+                                                                                           : node_y(p, srcj[ej]);
 
-    /* 1. ghost-extended distributions and moments U = sum_k f_k */
+    /* 1. ghost-extended distributions and moments U = sum_k f_k; across a
+     * reflecting boundary the mirror node's distributions with the normal
+     * velocities exchanged and the normal momentum negated */
 #pragma omp parallel for
     for (int ej = 0; ej < ey; ej++)
         for (int ei = 0; ei < ex; ei++) {
             int j = srcj[ej], i = srci[ei];
+            int refl[2] = {ghost_side(ei - G, nx, p->bc[0], p->bc[1]) == ORC_BC_REFLECT,
+                           d == 2 && ghost_side(ej - gy, ny, p->bc[2], p->bc[3]) == ORC_BC_REFLECT};
             for (int c = 0; c < m; c++) {
                 double s = 0.0;
                 for (int k = 0; k < Q; k++) {
-                    double v = f[FIDX(k, c, j, i)];
+                    int ks = k;  /* the velocity read from the mirror node */
+                    double sign = 1.0;
+                    for (int dir = 0; dir < d; dir++) {
+                        if (!refl[dir]) continue;
+                        if (ks == 1 + dir) ks = 1 + d + dir;
+                        else if (ks == 1 + d + dir) ks = 1 + dir;
+                        if (c == momentum_index(p, dir)) sign = -sign;
+                    }
+                    double v = sign * f[FIDX(ks, c, j, i)];
                     fe[EF(k, c, ej, ei)] = v;
                     s += v;
                 }
@@ -665,6 +739,25 @@ int orc_step(const orc_problem *p, const double *f, double *fn, double dt_cap, c
     for (int j = 0; j < d; j++) alpha[j] = abar[j] + p->eps;
     double a[5];
     weights_a(d, alpha, lam, a);
+
+    /* 3b. ghost nodes across an inflow boundary: f^eq(U_in) with this step's
+     * alpha and lambda */
+    {
+        double feq_in[5 * MAXM];
+        orc_equilibrium(p, p->u_in, alpha, lam, feq_in);
+        for (int ej = 0; ej < ey; ej++)
+            for (int ei = 0; ei < ex; ei++) {
+                int in = ghost_side(ei - G, nx, p->bc[0], p->bc[1]) == ORC_BC_INFLOW ||
+                         (d == 2 && ghost_side(ej - gy, ny, p->bc[2], p->bc[3]) == ORC_BC_INFLOW);
+                if (!in) continue;
+                for (int c = 0; c < m; c++) {
+                    for (int k = 0; k < Q; k++) fe[EF(k, c, ej, ei)] = feq_in[k * m + c];
+                    double s = 0.0;
+                    for (int k = 0; k < Q; k++) s += feq_in[k * m + c];
+                    Ue[EU(c, ej, ei)] = s;
+                }
+            }
+    }
 
     /* 4. smoothness indicator nu on nodes one layer inside the extension */
     for (size_t e = 0; e < next; e++) nu[e] = 0.0;
@@ -700,6 +793,7 @@ int orc_step(const orc_problem *p, const double *f, double *fn, double dt_cap, c
                     for (int bi = -1; bi <= 1; bi++) nt += nu[E1(ej + bj, ei + bi)];
                 w = 1.0 + 1.0 / (1.0 + nt);
             }
+            if (p->sponge_width > 0.0) w = 1.0 + (w - 1.0) * (1.0 - sponge_sigma(p, node_x(p, ei - G)));
             om[E1(ej, ei)] = w;
         }
 
@@ -710,7 +804,7 @@ int orc_step(const orc_problem *p, const double *f, double *fn, double dt_cap, c
             double Ui[MAXM], feq[5 * MAXM], S[MAXM];
             for (int c = 0; c < m; c++) Ui[c] = Ue[EU(c, ej, ei)];
             orc_equilibrium(p, Ui, alpha, lam, feq);
-            orc_source(p, Ui, node_x(p, srci[ei]), node_y(p, srcj[ej]), S);
+            orc_source(p, Ui, posx[ei], posy[ej], S);
             double w = om[E1(ej, ei)];
             for (int k = 0; k < Q; k++)
                 for (int c = 0; c < m; c++) {
@@ -753,7 +847,7 @@ int orc_step(const orc_problem *p, const double *f, double *fn, double dt_cap, c
         info[2] = dt;
         info[3] = lam;
     }
-    free(fe); free(Ue); free(nu); free(om); free(post); free(srcj); free(srci);
+    free(fe); free(Ue); free(nu); free(om); free(post); free(srcj); free(srci); free(posx); free(posy);
     return flags;
 #undef E1
 #undef EF

@@ -14,7 +14,7 @@ from typing import Optional, Tuple
 import numpy as np
 
 ADVECTION, EULER, SWE, REACTIVE, LINEAR = 0, 1, 2, 3, 4
-PERIODIC, OUTFLOW = 0, 1
+PERIODIC, OUTFLOW, REFLECT, INFLOW = 0, 1, 2, 3
 SYSTEM_NAMES = {ADVECTION: "advection", EULER: "euler", SWE: "shallow_water",
                 REACTIVE: "reactive_euler", LINEAR: "linear"}
 
@@ -48,6 +48,8 @@ class Problem:
     omega_mode: int = 0           # 0: adaptive (2.12)/(2.16); 1: fixed omega_fixed
     omega_fixed: float = 1.0
     h_dry: float = 1e-5           # depth below which a node is dry (u = v = 0)
+    sponge_width: float = 0.0     # > 0: sponge layer of this width at x-lo (omega blended toward 1)
+    u_in: Tuple[float, ...] = ()  # conservative state held by inflow ghost nodes
     precision: int = 0            # 0: FP64, 1: FP32 distributions (CUDA path only)
 
     @property

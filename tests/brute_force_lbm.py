@@ -134,23 +134,48 @@ def step(pb, f):
 
     def mp(e, n, lo, hi):
         if e < 0:
-            return e % n if lo == 0 else 0
+            return e % n if lo == 0 else (-1 - e if lo == 2 else 0)
         if e >= n:
-            return e % n if hi == 0 else n - 1
+            return e % n if hi == 0 else (2 * n - 1 - e if hi == 2 else n - 1)
         return e
+
+    def side(e, n, lo, hi):  # boundary type across which e lies, None inside
+        return lo if e < 0 else (hi if e >= n else None)
 
     def src(ei, ej):
         i = mp(ei - G, nx, pb.bc[0], pb.bc[1])
         j = mp(ej - G, ny, pb.bc[2], pb.bc[3]) if d == 2 else 0
         return i, j
 
+    def sides(p):
+        sx = side(p[0], nx, pb.bc[0], pb.bc[1])
+        sy = side(p[1], ny, pb.bc[2], pb.bc[3]) if d == 2 else None
+        return sx, sy
+
+    momentum = pb.system in (EULER, SWE, REACTIVE)
     jrange = range(-G, ny + G) if d == 2 else range(0, 1)
     Ue, fe = {}, {}
     for ej in jrange:
         for ei in range(-G, nx + G):
             i, j = src(ei + G, ej + G if d == 2 else G)
-            fe[(ei, ej)] = [[f[k, c, j, i] for c in range(m)] for k in range(Q)]
-            Ue[(ei, ej)] = [sum(f[k, c, j, i] for k in range(Q)) for c in range(m)]
+            vals = [[f[k, c, j, i] for c in range(m)] for k in range(Q)]
+            # a reflecting ghost: velocity e mirrored across the wall, normal
+            # momentum reversed
+            for dirn, sd in enumerate(sides((ei, ej))[:d]):
+                if sd != 2:
+                    continue
+                mirrored = []
+                for k in range(Q):
+                    e = list(evel[k])
+                    e[dirn] = -e[dirn]
+                    kk = evel.index(tuple(e))
+                    row = list(vals[kk])
+                    if momentum:
+                        row[1 + dirn] = -row[1 + dirn]
+                    mirrored.append(row)
+                vals = mirrored
+            fe[(ei, ej)] = vals
+            Ue[(ei, ej)] = [sum(vals[k][c] for k in range(Q)) for c in range(m)]
     abar = [0.0, 0.0]
     for j in range(ny):
         for i in range(nx):
@@ -160,6 +185,22 @@ def step(pb, f):
     lam = dx / dt
     alpha = [abar[j] + pb.eps for j in range(d)]
     a = [1 - sum(alpha) / lam] + [alpha[j] / (2 * lam) for j in range(d)] * 2
+
+    def equilibrium(U):
+        Fs = [flux(pb, j, U) for j in range(d)]
+        feq = [[(1 - sum(alpha) / lam) * U[c] for c in range(m)]]
+        for j in range(d):
+            feq.append([(alpha[j] * U[c] + Fs[j][c]) / (2 * lam) for c in range(m)])
+        for j in range(d):
+            feq.append([(alpha[j] * U[c] - Fs[j][c]) / (2 * lam) for c in range(m)])
+        return feq
+
+    # an inflow ghost holds the equilibrium of the fixed inflow state
+    for p in list(fe.keys()):
+        if 3 in sides(p):
+            Uin = [float(v) for v in pb.u_in[:m]]
+            fe[p] = equilibrium(Uin)
+            Ue[p] = [sum(fe[p][k][c] for k in range(Q)) for c in range(m)]
 
     def nu_at(p):
         tot = 0.0
@@ -176,12 +217,24 @@ def step(pb, f):
 
     def omega_at(p):
         if pb.omega_mode == 1:
-            return pb.omega_fixed
-        box = [(bi, bj) for bi in (-1, 0, 1) for bj in ((-1, 0, 1) if d == 2 else (0,))]
-        return 1.0 + 1.0 / (1.0 + sum(nu_at((p[0] + bi, p[1] + bj)) for bi, bj in box))
+            w = pb.omega_fixed
+        else:
+            box = [(bi, bj) for bi in (-1, 0, 1) for bj in ((-1, 0, 1) if d == 2 else (0,))]
+            w = 1.0 + 1.0 / (1.0 + sum(nu_at((p[0] + bi, p[1] + bj)) for bi, bj in box))
+        L = getattr(pb, "sponge_width", 0.0)
+        if L > 0.0:
+            r = (p[0] + 0.5) * dx / L
+            sigma = 1.0 if r <= 0 else (0.0 if r >= 1 else 0.5 * (1 + math.cos(math.pi * r)))
+            w = 1.0 + (w - 1.0) * (1.0 - sigma)
+        return w
 
     def coords(p):
         i, j = src(p[0] + G, p[1] + G if d == 2 else G)
+        sx, sy = sides(p)
+        if sx == 2:
+            i = p[0]
+        if sy == 2:
+            j = p[1]
         x = pb.x0 + (i + 0.5) * dx
         y = pb.y0 + (j + 0.5) * dx if d == 2 else 0.0
         return x, y
@@ -193,12 +246,7 @@ def step(pb, f):
             p = (ei, ej)
             U = Ue[p]
             om = omega_at(p)
-            Fs = [flux(pb, j, U) for j in range(d)]
-            feq = [[(1 - sum(alpha) / lam) * U[c] for c in range(m)]]
-            for j in range(d):
-                feq.append([(alpha[j] * U[c] + Fs[j][c]) / (2 * lam) for c in range(m)])
-            for j in range(d):
-                feq.append([(alpha[j] * U[c] - Fs[j][c]) / (2 * lam) for c in range(m)])
+            feq = equilibrium(U)
             S = source(pb, U, *coords(p))
             for k in range(Q):
                 tgt = (ei + evel[k][0], ej + evel[k][1])

@@ -47,3 +47,43 @@ def test_push_form_wet_dry():
         f, dt = BF.step(pb, f)
         r.step(1)
         assert np.all(np.abs(f - r.f) <= 1e-13 * np.abs(r.f).max())
+
+
+def boundary_cases():
+    """Reflecting walls, fixed inflow and the sponge layer (Example 5.13's
+    boundaries) on every system, including corners where two kinds meet."""
+    out = []
+    combos = {
+        1: [((W.REFLECT, W.INFLOW, 0, 0), 0.35), ((W.INFLOW, W.REFLECT, 0, 0), 0.0),
+            ((W.OUTFLOW, W.REFLECT, 0, 0), 0.5)],
+        2: [((W.OUTFLOW, W.INFLOW, W.REFLECT, W.REFLECT), 0.3),
+            ((W.REFLECT, W.REFLECT, W.PERIODIC, W.PERIODIC), 0.0),
+            ((W.INFLOW, W.OUTFLOW, W.INFLOW, W.REFLECT), 0.45)],
+    }
+    for dim in (1, 2):
+        nx, ny = (9, 1) if dim == 1 else (7, 6)
+        y1 = ny / nx if dim == 2 else 1.0
+        for bc, sponge in combos[dim]:
+            base = dict(dim=dim, nx=nx, ny=ny, y1=y1, bc=bc, cfl=0.8, sponge_width=sponge)
+            tag = f"{dim}d-" + "".join("POR I"[b] for b in bc[:2 * dim]) + (f"-s{sponge}" if sponge else "")
+            for name, pb in (("adv", W.Problem(system=W.ADVECTION, adv=(0.8, -0.5), **base)),
+                             ("euler", W.Problem(system=W.EULER, **base)),
+                             ("swe", W.Problem(system=W.SWE, bed_amp=0.4, bed_w2=0.05, bed_xc=0.4, bed_yc=0.3,
+                                               **base)),
+                             ("react", W.Problem(system=W.REACTIVE, gamma=1.2, q=5.0, K=40.0, Ti=2.0, **base))):
+                u_in = tuple(W.random_state(pb, seed=5).reshape(pb.nfields, -1)[:, 0])
+                out.append((f"{name}{tag}", pb.with_(u_in=u_in)))
+    return out
+
+
+@pytest.mark.parametrize("name,pb", boundary_cases(), ids=[c[0] for c in boundary_cases()])
+def test_push_form_matches_oracle_reflect_inflow_sponge(name, pb):
+    U0 = W.random_state(pb, seed=13)
+    r = oracle.Run(pb, U0)
+    f = r.f.copy()
+    for _ in range(3):
+        f, dt = BF.step(pb, f)
+        r.step(1)
+        assert r.info[2] == pytest.approx(dt, rel=1e-14)
+        scale = np.abs(r.f).max(axis=(0, 2, 3), keepdims=True)
+        assert np.all(np.abs(f - r.f) <= 1e-13 * scale), np.abs(f - r.f).max()

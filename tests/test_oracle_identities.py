@@ -381,3 +381,42 @@ def test_dry_threshold_keeps_front_speeds_physical():
     Ua, Ub = a.moments(), b.moments()
     l1_h = np.abs(Ua[0] - Ub[0]).sum() / np.abs(Ua[0]).sum()
     assert l1_h < 1e-5
+
+
+def test_reflective_wall_equals_mirrored_full_domain():
+    """A reflecting wall at y = 0 gives the upper half of the solution on the
+    doubled domain whose initial data are the mirror image (v -> -v) below y = 0."""
+    n = 12
+    half = W.Problem(system=W.EULER, dim=2, nx=n, ny=n // 2, x0=0.0, x1=1.0, y0=0.0, y1=0.5, cfl=0.8,
+                     bc=(W.PERIODIC, W.PERIODIC, W.REFLECT, W.OUTFLOW))
+    full = half.with_(ny=n, y0=-0.5, bc=(W.PERIODIC, W.PERIODIC, W.OUTFLOW, W.OUTFLOW))
+    Uh = W.random_state(half, seed=21)
+    lower = Uh[:, ::-1, :].copy()
+    lower[2] = -lower[2]
+    Uf = np.concatenate([lower, Uh], axis=1)
+    rh, rf = oracle.Run(half, Uh), oracle.Run(full, Uf)
+    for _ in range(6):
+        rh.step(1)
+        rf.step(1)
+        assert rh.info[2] == pytest.approx(rf.info[2], rel=1e-14)
+    a, b = rh.moments(), rf.moments()[:, n // 2:, :]
+    scale = np.abs(b).reshape(4, -1).max(axis=1)
+    assert np.all(np.abs(a - b).reshape(4, -1).max(axis=1) <= 1e-12 * scale)
+
+
+def test_sponge_blends_omega_toward_one():
+    """omega' = 1 + (omega - 1)(1 - sigma(x)) with sigma = (1 + cos(pi x / L))/2
+    on the sponge [x0, x0 + L]; unchanged beyond it."""
+    pb = W.Problem(system=W.EULER, dim=1, nx=64, x0=0.0, x1=1.0, cfl=0.8, bc=(W.OUTFLOW,) * 4)
+    U0 = W.random_state(pb, seed=4)
+    f1 = oracle.Run(pb, U0).step(2).f  # a state off equilibrium; both runs step from it
+    a = oracle.Run(pb, U0)
+    a.f[...] = f1
+    b = oracle.Run(pb.with_(sponge_width=0.25), U0)
+    b.f[...] = f1
+    a.step(1, want_omega=True)
+    b.step(1, want_omega=True)
+    x = (np.arange(64) + 0.5) / 64
+    sigma = np.where(x < 0.25, 0.5 * (1 + np.cos(np.pi * x / 0.25)), 0.0)
+    assert np.allclose(b.omega.ravel(), 1 + (a.omega.ravel() - 1) * (1 - sigma), rtol=0, atol=1e-14)
+    assert np.array_equal(b.omega.ravel()[x >= 0.25], a.omega.ravel()[x >= 0.25])
