@@ -320,6 +320,81 @@ def detonation_1d(nx=None, dx=1.0 / 150, L=100.0, cfl=0.9):
     return pb, euler_conservative(pb, rho, u, p, Y=Yf)
 
 
+def d_cj(gamma, q):
+    """Chapman-Jouguet detonation speed of Example 5.13 (upstream rho = p = 1)."""
+    a = (gamma * gamma - 1.0) * q
+    return float(np.sqrt(gamma + a + np.sqrt(a * (2.0 * gamma + a))))
+
+
+def znd_state(Y, D, gamma, q):
+    """Steady 1D ZND state at reaction progress Y behind a shock moving at D
+    into (rho, u, p, Y) = (1, 0, 1, 1), in the shock-attached frame where the
+    upstream gas arrives with u = -D: mass, momentum and energy fluxes equal
+    the upstream ones, and of the two specific volumes they allow the shocked
+    (smaller) one is taken.  Returns rho, u, p and the discriminant of the
+    quadratic for the specific volume (zero at a sonic point)."""
+    m = -D
+    P = 1.0 + D * D
+    H = gamma / (gamma - 1.0) + 0.5 * D * D + q
+    a = m * m * (gamma + 1.0) / (2.0 * (gamma - 1.0))
+    b = gamma * P / (gamma - 1.0)
+    c = H - q * np.asarray(Y, dtype=np.float64)
+    disc = b * b - 4.0 * a * c
+    V = (b - np.sqrt(np.maximum(disc, 0.0))) / (2.0 * a)
+    return 1.0 / V, m * V, P - m * m * V, disc
+
+
+def znd_profile(xi, D, gamma, q, Ti, K):
+    """Reaction progress Y at distances xi >= 0 behind the shock: the steady
+    rate equation u dY/dx = -K Y exp(-Ti/T), T = p/rho, integrated from Y = 1
+    at the shock (scipy LSODA, rtol 1e-10)."""
+    from scipy.integrate import solve_ivp
+
+    def rhs(_x, y):
+        rho, u, p, _d = znd_state(y[0], D, gamma, q)
+        return [K * y[0] * np.exp(-Ti * rho / p) / u]
+
+    xi = np.asarray(xi, dtype=np.float64)
+    top = float(xi.max()) if xi.size else 0.0
+    if top <= 0.0:
+        return np.ones_like(xi)
+    sol = solve_ivp(rhs, [0.0, top], [1.0], method="LSODA", rtol=1e-10, atol=1e-14, dense_output=True)
+    return np.clip(sol.sol(np.clip(xi, 0.0, top))[0], 0.0, 1.0)
+
+
+DETONATION_5_13 = dict(gamma=1.2, q=2.0, Ti=20.0, K=1.13436364e6)
+
+
+def cellular_detonation(nx=1200, ny=900, overdrive=1.1, k=6, x_front=30.0, cfl=0.3, sponge=6.0):
+    """Example 5.13: [0,40] x [-15,15] (1200 x 900 nodes, dx = 1/30 at full
+    size), gamma = 1.2, q = 2, Ti = 20, K = 1.13436364e6, shock-attached frame
+    moving at D = sqrt(overdrive) D_CJ.  Unreacted (1, -D, 0, 1, 1) ahead of
+    the front at x_front, the ZND profile behind it, v = 0.1 sin(2 pi k y / 30)
+    in x_front - 1 <= x <= x_front.  Reflecting walls at y = +-15, fixed
+    inflow of the unreacted state at x = 40, zero-gradient outflow at x = 0
+    with a sponge over 0 <= x <= sponge."""
+    c = DETONATION_5_13
+    D = float(np.sqrt(overdrive)) * d_cj(c["gamma"], c["q"])
+    pb = Problem(system=REACTIVE, dim=2, nx=nx, ny=ny, x0=0.0, x1=40.0, y0=-15.0, y1=15.0, cfl=cfl,
+                 gamma=c["gamma"], K=c["K"], Ti=c["Ti"], q=c["q"], bc=(OUTFLOW, INFLOW, REFLECT, REFLECT),
+                 sponge_width=sponge)
+    unreacted = euler_conservative(pb, np.ones(1), -D, np.ones(1), v=0.0, Y=np.ones(1))[:, 0]
+    pb = pb.with_(u_in=tuple(float(v) for v in unreacted))
+    X, Yc = cell_centres(pb)
+    xs = X[0]
+    behind = xs <= x_front
+    Yz = np.ones_like(xs)
+    Yz[behind] = znd_profile(x_front - xs[behind], D, c["gamma"], c["q"], c["Ti"], c["K"])
+    rho1, u1, p1, _d = znd_state(Yz, D, c["gamma"], c["q"])
+    ones = np.ones_like(X)
+    rho = np.where(behind, rho1, 1.0)[None, :] * ones
+    u = np.where(behind, u1, -D)[None, :] * ones
+    p = np.where(behind, p1, 1.0)[None, :] * ones
+    Yf = np.where(behind, Yz, 1.0)[None, :] * ones
+    v = np.where((X >= x_front - 1.0) & (X <= x_front), 0.1 * np.sin(2.0 * np.pi * k * Yc / 30.0), 0.0)
+    return pb, euler_conservative(pb, rho, u, p, v=v, Y=Yf)
+
+
 # --------------------------------------------------------------------------
 # Section 4: linear symmetric systems (acoustics), oracle-side stability tests
 # --------------------------------------------------------------------------

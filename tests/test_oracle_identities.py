@@ -420,3 +420,44 @@ def test_sponge_blends_omega_toward_one():
     sigma = np.where(x < 0.25, 0.5 * (1 + np.cos(np.pi * x / 0.25)), 0.0)
     assert np.allclose(b.omega.ravel(), 1 + (a.omega.ravel() - 1) * (1 - sigma), rtol=0, atol=1e-14)
     assert np.array_equal(b.omega.ravel()[x >= 0.25], a.omega.ravel()[x >= 0.25])
+
+
+def test_znd_profile_of_example_5_13():
+    """The ZND generator of Example 5.13's initial data: (a) at the printed
+    D_CJ the flow leaves the reaction zone sonic (Mach 1 at Y = 0 in the shock
+    frame), (b) the states satisfy the three flux conservations, (c) the
+    Rankine-Hugoniot von Neumann state is the strong shock of the upstream
+    state, and (d) with the printed K the half-reaction length of the f = 1.1
+    overdriven detonation is 1 (the normalisation K was chosen for)."""
+    c = W.DETONATION_5_13
+    g, q = c["gamma"], c["q"]
+    Dcj = W.d_cj(g, q)
+    rho, u, p, disc = W.znd_state(0.0, Dcj, g, q)
+    assert abs(u) / np.sqrt(g * p / rho) == pytest.approx(1.0, abs=1e-6)
+    D = np.sqrt(1.1) * Dcj
+    Y = np.linspace(0.0, 1.0, 11)
+    rho, u, p, disc = W.znd_state(Y, D, g, q)
+    assert np.allclose(rho * u, -D, rtol=1e-13)
+    assert np.allclose(p + rho * u * u, 1.0 + D * D, rtol=1e-13)
+    assert np.allclose(g / (g - 1) * p / rho + 0.5 * u * u + q * Y, g / (g - 1) + 0.5 * D * D + q, rtol=1e-13)
+    # normal-shock relations at Y = 1 (no reaction yet): rho2/rho1 = (g+1)M^2 / ((g-1)M^2 + 2)
+    M2 = D * D / g
+    assert rho[-1] == pytest.approx((g + 1) * M2 / ((g - 1) * M2 + 2), rel=1e-12)
+    assert np.all(disc > 0)
+    xi = np.linspace(0.0, 3.0, 3001)
+    Yx = W.znd_profile(xi, D, g, q, c["Ti"], c["K"])
+    half = np.interp(0.5, Yx[::-1], xi[::-1])
+    assert half == pytest.approx(1.0, abs=2e-3)
+
+
+def test_cellular_detonation_initial_data():
+    pb, U0 = W.cellular_detonation(nx=120, ny=90)
+    assert pb.bc == (W.OUTFLOW, W.INFLOW, W.REFLECT, W.REFLECT) and pb.sponge_width == 6.0
+    assert pb.dx == pytest.approx(1.0 / 3.0) and pb.u_in[0] == 1.0 and pb.u_in[4] == 1.0
+    X, Yc = W.cell_centres(pb)
+    ahead = X > 30.0
+    assert np.allclose(U0[0][ahead], 1.0) and np.allclose(U0[4][ahead], 1.0)
+    Yf = U0[4] / U0[0]
+    assert np.all(Yf[~ahead] < 1.0) and np.all(Yf >= 0.0)
+    strip = (X >= 29.0) & (X <= 30.0)
+    assert np.abs(U0[2][strip]).max() > 0 and np.all(U0[2][~strip] == 0.0)
