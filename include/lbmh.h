@@ -64,11 +64,24 @@ typedef enum {
   LBMH_LINEAR = 4
 } lbmh_system;
 
-typedef enum { LBMH_BC_PERIODIC = 0, LBMH_BC_OUTFLOW = 1 } lbmh_bc;
+/* Boundary of each side (Section 5; the reading of each in the lattice is a
+ * read of f^n at ghost nodes beyond the side):
+ *   PERIODIC  wrapped node (must pair with the opposite side);
+ *   OUTFLOW   zero gradient: the nearest interior node;
+ *   REFLECT   reflecting wall (Example 5.13, y = +-15): the mirror node's
+ *             distributions with the velocities normal to the wall exchanged
+ *             and the normal momentum negated (needs >= 4 nodes across);
+ *   INFLOW    fixed state (Example 5.13, x = 40): f^eq(u_in) with the step's
+ *             alpha and lambda.
+ * REFLECT and INFLOW are implemented by the fused kernels (and the batch
+ * engine); the unfused path and lbmh_step_static return
+ * LBMH_ERR_UNSUPPORTED for them. */
+typedef enum { LBMH_BC_PERIODIC = 0, LBMH_BC_OUTFLOW = 1, LBMH_BC_REFLECT = 2, LBMH_BC_INFLOW = 3 } lbmh_bc;
 
 /* LBMH_FP64: distributions stored and collided in FP64.
- * LBMH_FP32: distributions stored and collided in FP32; the conservation sums
- * and the Arrhenius source and its implicit update stay in FP64. */
+ * LBMH_FP32: distributions stored and collided in FP32; the step control and
+ * the conservation sums stay in FP64; the Arrhenius root of Eq. (2.8) is found
+ * in FP32 (it is stored in FP32) and in FP64 where that does not converge. */
 typedef enum { LBMH_FP64 = 0, LBMH_FP32 = 1 } lbmh_precision;
 
 typedef enum { LBMH_OMEGA_ADAPTIVE = 0, LBMH_OMEGA_FIXED = 1 } lbmh_omega_mode;
@@ -99,6 +112,10 @@ typedef struct lbmh_problem {
   int precision;       /* lbmh_precision */
   int kernel;          /* lbmh_kernel */
   void *cuda_stream;   /* cudaStream_t to enqueue on */
+  double sponge_width; /* > 0: sponge layer over [x0, x0 + sponge_width] (Example 5.13): omega is
+                          blended toward 1, omega' = 1 + (omega - 1)(1 - sigma(x)),
+                          sigma = (1 + cos(pi (x - x0) / sponge_width)) / 2; 0: none */
+  double u_in[8];      /* conservative state (first m entries) held by INFLOW sides */
 } lbmh_problem;
 
 typedef struct lbmh_handle lbmh_handle;

@@ -7,7 +7,7 @@
 namespace lbmh {
 
 enum { SYS_ADV = 0, SYS_EULER = 1, SYS_SWE = 2, SYS_REACT = 3 };
-enum { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECT = 2, BC_INFLOW = 3 };
 
 // number of conserved fields m of each system in d dimensions
 template <int SYS, int D>
@@ -34,6 +34,8 @@ struct PhysConstF {
   float gamma, gm1, g, half_g, h_dry, cmin, q, adv0, adv1, dx;
   float bed_amp, bed_inv_w2, bed_m2_inv_w2, xb, yb, K, Ti;
   float omega_fixed;
+  float sponge_dx_over_w;
+  float u_in[8];
 };
 
 struct DevParams {
@@ -53,6 +55,10 @@ struct DevParams {
   int has_react;     // K != 0           a double would be an FP64 instruction)
   int omega_mode;    // 0 adaptive, 1 fixed
   double omega_fixed;
+  double sponge_width;      // > 0: sponge over [x0, x0 + sponge_width] (omega blended toward 1)
+  double sponge_dx_over_w;  // dx / sponge_width
+  double u_in[8];           // conservative state of INFLOW ghost nodes
+  int has_special_bc;       // some side is REFLECT or INFLOW
   PhysConstF pf;
 };
 
@@ -152,9 +158,20 @@ __host__ __device__ __forceinline__ long long cell(const DevParams& P, int i, in
 // wraps, outflow clamps (every read of f^n outside the domain is a read of the
 // nearest interior node, or of the wrapped node)
 __device__ __forceinline__ int map_index(int e, int n, int bc_lo, int bc_hi) {
-  if (e < 0) return bc_lo == BC_PERIODIC ? (e % n + n) % n : 0;
-  if (e >= n) return bc_hi == BC_PERIODIC ? e % n : n - 1;
+  if (e < 0) return bc_lo == BC_PERIODIC ? (e % n + n) % n : (bc_lo == BC_REFLECT ? -1 - e : 0);
+  if (e >= n) return bc_hi == BC_PERIODIC ? e % n : (bc_hi == BC_REFLECT ? 2 * n - 1 - e : n - 1);
   return e;
+}
+
+// boundary type across which coordinate e lies (-1 inside [0, n))
+__device__ __forceinline__ int ghost_side(int e, int n, int bc_lo, int bc_hi) {
+  return e < 0 ? bc_lo : (e >= n ? bc_hi : -1);
+}
+
+// index of the position of extended coordinate e: a periodic or outflow ghost
+// sits where the node it copies sits, a reflecting ghost at its own position
+__device__ __forceinline__ int pos_index(int e, int n, int bc_lo, int bc_hi) {
+  return ghost_side(e, n, bc_lo, bc_hi) == BC_REFLECT ? e : map_index(e, n, bc_lo, bc_hi);
 }
 
 }  // namespace lbmh

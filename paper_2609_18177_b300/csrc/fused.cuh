@@ -195,6 +195,76 @@ __device__ __forceinline__ void fused_side_outputs(R sp0, R sp1, const Acc<R>* a
   fused_side_outputs_to<M, R>(sp0, sp1, acc, ctl, slot1, partials + (long long)blockIdx.x * M, st);
 }
 
+// A column of f^n loaded at a ghost node across a REFLECT or INFLOW side
+// (cs: side of the node's column, rs: side of its row; anything else: not a
+// special side).  INFLOW (on either side) gives f^eq(u_in) with the step's
+// coefficients (Eq. 2.20); REFLECT exchanges the velocities normal to the wall
+// (e_j <-> -e_j) and negates the normal momentum, the mirror node's values
+// having been loaded.  fc points at plane 0 of the column, planes `stride`
+// elements apart.
+template <int SYS, int D, class R>
+__device__ __forceinline__ void ghost_fixup(R* fc, int stride, int cs, int rs, const Phys<R>& K, const R* uin, R a0,
+                                            R al0, R al1, R inv2l) {
+  constexpr int M = Fields<SYS, D>::M;
+  if (cs == BC_INFLOW || rs == BC_INFLOW) {
+    R U[M], Fx[M], Fy[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) U[c] = uin[c];
+    const Prim<R> w = primitives<SYS, D, R>(K, U);
+    flux<SYS, D, R>(K, U, w, 0, Fx);
+    if constexpr (D == 2) flux<SYS, D, R>(K, U, w, 1, Fy);
+#pragma unroll
+    for (int c = 0; c < M; c++) {
+      fc[(0 * M + c) * stride] = a0 * U[c];
+      fc[(1 * M + c) * stride] = (al0 * U[c] + Fx[c]) * inv2l;
+      if constexpr (D == 2) {
+        fc[(2 * M + c) * stride] = (al1 * U[c] + Fy[c]) * inv2l;
+        fc[(3 * M + c) * stride] = (al0 * U[c] - Fx[c]) * inv2l;
+        fc[(4 * M + c) * stride] = (al1 * U[c] - Fy[c]) * inv2l;
+      } else {
+        fc[(2 * M + c) * stride] = (al0 * U[c] - Fx[c]) * inv2l;
+      }
+    }
+    return;
+  }
+  constexpr bool momentum = SYS == SYS_EULER || SYS == SYS_SWE || SYS == SYS_REACT;
+#pragma unroll
+  for (int dir = 0; dir < D; dir++) {
+    if ((dir == 0 ? cs : rs) != BC_REFLECT) continue;
+    const int kp = 1 + dir, km = 1 + D + dir;
+#pragma unroll
+    for (int c = 0; c < M; c++) {
+      const R tmp = fc[(kp * M + c) * stride];
+      fc[(kp * M + c) * stride] = fc[(km * M + c) * stride];
+      fc[(km * M + c) * stride] = tmp;
+    }
+    if constexpr (momentum) {
+#pragma unroll
+      for (int k = 0; k < 2 * D + 1; k++) fc[(k * M + 1 + dir) * stride] = -fc[(k * M + 1 + dir) * stride];
+    }
+  }
+}
+
+// the inflow state in the path's type
+template <class R>
+__device__ __forceinline__ const R* inflow_state(const DevParams& P) {
+  if constexpr (sizeof(R) == 4)
+    return P.pf.u_in;
+  else
+    return P.u_in;
+}
+
+// 1 - sigma(x) of the sponge at extended column e (sigma = (1 + cos(pi r))/2,
+// r = (x - x0)/width; 1 left of x0, 0 past the width)
+template <class R>
+__device__ __forceinline__ R sponge_keep(const DevParams& P, int e) {
+  const R r = (R(e) + R(0.5)) * (sizeof(R) == 4 ? R(P.pf.sponge_dx_over_w) : R(P.sponge_dx_over_w));
+  if (!(r > R(0))) return R(0);
+  if (r >= R(1)) return R(1);
+  const R sigma = R(0.5) * (R(1) + cos(R(3.14159265358979323846) * r));
+  return R(1) - sigma;
+}
+
 // Coefficients of one step of one lattice, in the arithmetic type of the path
 // (Eq. 2.20, 2.21 and the weights a_k of Eq. 2.5).
 template <class R>
@@ -278,15 +348,21 @@ __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml
       const int x0 = strip * WOUT;
       int gx[CPT];
       bool outc[CPT];
-      R xr_ghost[CPT], xr_out[CPT];
+      R xr_ghost[CPT], xr_out[CPT], keep[CPT];
+      int colside[CPT];
+      const bool sponge = P.sponge_width > 0.0;
   #pragma unroll
       for (int j = 0; j < CPT; j++) {
         const int sc = sc0 + j;
         gx[j] = x0 - 4 + sc;
         outc[j] = sc >= 4 && sc < NC - 4 && gx[j] < P.nx;
-        const int mx = map_index(gx[j], P.nx, P.bc[0], P.bc[1]);
-        xr_ghost[j] = K.xb + R(mx) * K.dx;  // a ghost node sits where the node it copies sits
+        // a periodic/outflow ghost sits where the node it copies sits, a
+        // reflecting ghost at its own position
+        const int mx = pos_index(gx[j], P.nx, P.bc[0], P.bc[1]);
+        xr_ghost[j] = K.xb + R(mx) * K.dx;
         xr_out[j] = K.xb + R(gx[j]) * K.dx;
+        colside[j] = ghost_side(gx[j], P.nx, P.bc[0], P.bc[1]);
+        keep[j] = sponge ? sponge_keep<R>(P, gx[j]) : R(1);
       }
       // ghost columns whose source node lies in this strip's output range: the
       // CTA writes them after each row from the staged output
@@ -361,7 +437,19 @@ __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml
           issued_end = s + 1;
         }
         if (!mbar_wait_bounded(smem_u32(&bars[sidx % S]), (sidx / S) & 1u)) *s_abort = 1;
-        const R* frow = fring + (size_t)(sidx % S) * QM * NC;
+        R* frow_w = fring + (size_t)(sidx % S) * QM * NC;
+        if (P.has_special_bc) {  // ghost nodes across reflecting / inflow sides (own columns only)
+          const int rs = ghost_side(r, P.ny, P.bc[2], P.bc[3]);
+          bool fixed = false;
+  #pragma unroll
+          for (int j = 0; j < CPT; j++)
+            if (colside[j] >= BC_REFLECT || rs >= BC_REFLECT) {
+              ghost_fixup<SYS, 2, R>(frow_w + sc0 + j, NC, colside[j], rs, K, inflow_state<R>(P), a0, al0, al1, inv2l);
+              fixed = true;
+            }
+          if (fixed) fence_proxy_async();  // before the slot is refilled by TMA
+        }
+        const R* frow = frow_w;
         // B: moments of row r
         R Ur[CPT][M];
   #pragma unroll
@@ -425,11 +513,12 @@ __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml
           R cl = j > 0 ? colsum[j > 0 ? j - 1 : 0] : colsm[scl];
           R cr = j < CPT - 1 ? colsum[j < CPT - 1 ? j + 1 : 0] : colsm[scr];
           R om = fixed_omega ? om_fixed : R(1) + fdiv(R(1), R(1) + (cl + colsum[j] + cr));
+          if (sponge) om = R(1) + (om - R(1)) * keep[j];
           R Fx[M], Fy[M], Sr[M];
           flux<SYS, 2, R>(K, U2[j], w2[j], 0, Fx);
           flux<SYS, 2, R>(K, U2[j], w2[j], 1, Fy);
           if constexpr (SRC) {
-            const int my2 = map_index(r - 2, P.ny, P.bc[2], P.bc[3]);
+            const int my2 = pos_index(r - 2, P.ny, P.bc[2], P.bc[3]);
             source<SYS, 2, R>(K, U2[j], xr_ghost[j], K.yb + R(my2) * K.dx, Sr);
           }
   #pragma unroll
@@ -704,13 +793,18 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
     const int mx = map_index(gx, P.nx, P.bc[0], P.bc[1]);
     R f[Q][M], U[M];
 #pragma unroll
+    for (int c = 0; c < M; c++)
+#pragma unroll
+      for (int k = 0; k < Q; k++) f[k][c] = fin[(long long)(k * M + c) * P.plane + mx + XPAD];
+    if (P.has_special_bc) {
+      const int cs = ghost_side(gx, P.nx, P.bc[0], P.bc[1]);
+      if (cs >= BC_REFLECT) ghost_fixup<SYS, 1, R>(&f[0][0], 1, cs, -1, K, inflow_state<R>(P), a0, al0, al0, inv2l);
+    }
+#pragma unroll
     for (int c = 0; c < M; c++) {
       R sum = R(0);
 #pragma unroll
-      for (int k = 0; k < Q; k++) {
-        f[k][c] = fin[(long long)(k * M + c) * P.plane + mx + XPAD];
-        sum += f[k][c];
-      }
+      for (int k = 0; k < Q; k++) sum += f[k][c];
       U[c] = sum;
       Us[c][t] = sum;
     }
@@ -730,9 +824,10 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
     __syncthreads();
     R om = cf.om_fixed;
     if (!fixed_omega && t >= 1 && t < FT - 1) om = R(1) + fdiv(R(1), R(1) + (nus[t - 1] + nus[t] + nus[t + 1]));
+    if (P.sponge_width > 0.0) om = R(1) + (om - R(1)) * sponge_keep<R>(P, gx);
     R F[M], S[M], post0[M];
     flux<SYS, 1, R>(K, U, w, 0, F);
-    if constexpr (SRC) source<SYS, 1, R>(K, U, K.xb + R(mx) * K.dx, R(0), S);
+    if constexpr (SRC) source<SYS, 1, R>(K, U, K.xb + R(pos_index(gx, P.nx, P.bc[0], P.bc[1])) * K.dx, R(0), S);
 #pragma unroll
     for (int c = 0; c < M; c++) {
       R feq0 = a0 * U[c], feq1 = (al0 * U[c] + F[c]) * inv2l, feq2 = (al0 * U[c] - F[c]) * inv2l;

@@ -2,6 +2,8 @@
 // translation of an lbmh_problem into the kernels' DevParams.
 #pragma once
 #include <math.h>
+
+#include <cmath>
 #include <string.h>
 
 #include <string>
@@ -21,6 +23,13 @@ inline int nfields(int sys, int dim) {
   return -1;
 }
 
+// reflecting or inflow sides, or a sponge: implemented by the fused kernels only
+inline bool needs_fused(const lbmh_problem* p) {
+  bool special = p->sponge_width > 0.0;
+  for (int s = 0; s < 2 * p->dim; s++) special = special || p->bc[s] == LBMH_BC_REFLECT || p->bc[s] == LBMH_BC_INFLOW;
+  return special;
+}
+
 inline int validate(const lbmh_problem* p, std::string& why) {
   if (!p) { why = "problem is NULL"; return LBMH_ERR_INVALID_ARG; }
   if (p->system == LBMH_LINEAR) { why = "LBMH_LINEAR is provided by the oracle only"; return LBMH_ERR_UNSUPPORTED; }
@@ -29,8 +38,27 @@ inline int validate(const lbmh_problem* p, std::string& why) {
   if (p->nx < 1 || (p->dim == 2 && p->ny < 1)) { why = "grid must have at least one node"; return LBMH_ERR_INVALID_ARG; }
   if ((long long)p->nx * (p->dim == 2 ? p->ny : 1) > (1ll << 34)) { why = "grid too large"; return LBMH_ERR_INVALID_ARG; }
   if (!(p->x1 > p->x0)) { why = "x1 must exceed x0"; return LBMH_ERR_INVALID_ARG; }
-  for (int s = 0; s < 4; s++)
-    if (p->bc[s] != LBMH_BC_PERIODIC && p->bc[s] != LBMH_BC_OUTFLOW) { why = "bad boundary condition"; return LBMH_ERR_INVALID_ARG; }
+  for (int s = 0; s < 2 * p->dim; s++)
+    if (p->bc[s] < LBMH_BC_PERIODIC || p->bc[s] > LBMH_BC_INFLOW) { why = "bad boundary condition"; return LBMH_ERR_INVALID_ARG; }
+  for (int s = 0; s < 2 * p->dim; s++)
+    if (p->bc[s] == LBMH_BC_REFLECT && (s < 2 ? p->nx : p->ny) < 4) {
+      why = "a reflecting side needs at least 4 nodes across";
+      return LBMH_ERR_INVALID_ARG;
+    }
+  if (!(p->sponge_width >= 0.0) || p->sponge_width > p->x1 - p->x0) { why = "sponge width must lie in [0, x1 - x0]"; return LBMH_ERR_INVALID_ARG; }
+  for (int s = 0; s < 2 * p->dim; s++)
+    if (p->bc[s] == LBMH_BC_INFLOW) {
+      const double* u = p->u_in;
+      bool ok = true;
+      for (int c = 0; c < nfields(p->system, p->dim); c++) ok = ok && std::isfinite(u[c]);
+      if (p->system == LBMH_SWE || p->system == LBMH_EULER || p->system == LBMH_REACTIVE_EULER) ok = ok && u[0] > 0.0;
+      if (p->system == LBMH_EULER || p->system == LBMH_REACTIVE_EULER) {
+        double msq = u[1] * u[1] + (p->dim == 2 ? u[2] * u[2] : 0.0);
+        double chem = p->system == LBMH_REACTIVE_EULER ? p->q * u[p->dim + 2] : 0.0;
+        ok = ok && (u[p->dim + 1] - 0.5 * msq / u[0] - chem) > 0.0;
+      }
+      if (!ok) { why = "u_in must be a finite physical state for an inflow side"; return LBMH_ERR_INVALID_ARG; }
+    }
   if ((p->bc[0] == LBMH_BC_PERIODIC) != (p->bc[1] == LBMH_BC_PERIODIC)) { why = "periodic x boundaries must pair"; return LBMH_ERR_INVALID_ARG; }
   if (p->dim == 2) {
     if ((p->bc[2] == LBMH_BC_PERIODIC) != (p->bc[3] == LBMH_BC_PERIODIC)) { why = "periodic y boundaries must pair"; return LBMH_ERR_INVALID_ARG; }
@@ -79,6 +107,11 @@ inline DevParams make_devparams(const lbmh_problem* p, int pitch) {
   P.q = p->q;
   P.has_bed = p->bed_amp != 0.0;
   P.has_react = p->K != 0.0;
+  P.sponge_width = p->sponge_width;
+  P.sponge_dx_over_w = p->sponge_width > 0.0 ? P.dx / p->sponge_width : 0.0;
+  for (int c = 0; c < 8; c++) P.u_in[c] = p->u_in[c];
+  P.has_special_bc = 0;
+  for (int s = 0; s < 4; s++) P.has_special_bc |= (p->bc[s] == LBMH_BC_REFLECT || p->bc[s] == LBMH_BC_INFLOW);
   P.omega_mode = p->omega_mode;
   P.omega_fixed = p->omega_fixed;
   PhysConstF& f = P.pf;
@@ -100,6 +133,8 @@ inline DevParams make_devparams(const lbmh_problem* p, int pitch) {
   f.K = (float)P.K;
   f.Ti = (float)P.Ti;
   f.omega_fixed = (float)P.omega_fixed;
+  f.sponge_dx_over_w = (float)P.sponge_dx_over_w;
+  for (int c = 0; c < 8; c++) f.u_in[c] = (float)P.u_in[c];
   return P;
 }
 

@@ -384,6 +384,10 @@ int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
     return fail(nullptr, LBMH_ERR_UNSUPPORTED, "no fused kernel for this system/dimension/precision");
   }
   h->kernel = (want_fused && h->ops->has_fused) ? LBMH_KERNEL_FUSED : LBMH_KERNEL_UNFUSED;
+  if (h->kernel == LBMH_KERNEL_UNFUSED && needs_fused(p)) {
+    delete h;
+    return fail(nullptr, LBMH_ERR_UNSUPPORTED, "reflecting/inflow sides and the sponge need the fused kernel");
+  }
 
   h->G.ex = P.nx + 2 * GH;
   h->G.gy = p->dim == 2 ? GH : 0;
@@ -405,7 +409,7 @@ int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
     memset(&h->fp, 0, sizeof h->fp);
     if (h->ops->setup_fused(h) != 0) {
       cudaGetLastError();
-      if (p->kernel == LBMH_KERNEL_FUSED) {
+      if (p->kernel == LBMH_KERNEL_FUSED || needs_fused(p)) {
         free_handle(h);
         return fail(nullptr, LBMH_ERR_CUDA, "fused kernel setup failed");
       }
@@ -671,6 +675,7 @@ extern "C" int lbmh_step_static(const lbmh_problem* p, const double* f_in, doubl
   int rc = validate(p, why);
   if (rc) return fail(nullptr, rc, why);
   if (p->precision != LBMH_FP64) return fail(nullptr, LBMH_ERR_UNSUPPORTED, "lbmh_step_static runs in FP64 only");
+  if (needs_fused(p)) return fail(nullptr, LBMH_ERR_UNSUPPORTED, "lbmh_step_static has no reflecting/inflow sides or sponge");
   if (!f_in || !f_out || f_in == f_out) return fail(nullptr, LBMH_ERR_INVALID_ARG, "f_in and f_out must be distinct device arrays");
   const int m = nfields(p->system, p->dim), Q = 2 * p->dim + 1;
   const DevParams P = make_devparams(p, p->nx);  // the caller's arrays are unpadded [Q][m][ny][nx]

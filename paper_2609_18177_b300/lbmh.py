@@ -46,6 +46,8 @@ class _Problem(ctypes.Structure):
         ("h_dry", ctypes.c_double),
         ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p),
+        ("sponge_width", ctypes.c_double),
+        ("u_in", ctypes.c_double * 8),
     ]
 
 
@@ -140,6 +142,9 @@ def _c_problem(pb, precision, kernel, stream):
     s.h_dry = float(pb.h_dry)
     s.precision, s.kernel = int(precision), int(kernel)
     s.cuda_stream = stream
+    s.sponge_width = float(getattr(pb, "sponge_width", 0.0))
+    for i, v in enumerate(tuple(getattr(pb, "u_in", ()))[:8]):
+        s.u_in[i] = float(v)
     return s
 
 

@@ -1,0 +1,134 @@
+"""Reflecting walls, fixed inflow and the sponge layer (the boundaries of
+Example 5.13) on the fused CUDA path against the FP64 oracle: every system,
+1D and 2D, grids wider than one 120-column strip, corners where two kinds of
+side meet; the Example 5.13 lattice itself at reduced size, alone and in a
+batch.  FP64: relative max error <= 1e-12 per field; FP32: relative L1 <=
+2e-5 and relative max <= 5e-4 (the bars of the other parity tests)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_18177_b300 import lbmh
+from paper_2609_18177_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL, FP32_L1, FP32_MAX = 1e-12, 2e-5, 5e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    lbmh.load()
+
+
+def rel_max(g, o):
+    m = o.shape[0]
+    g2, o2 = g.reshape(m, -1), o.reshape(m, -1)
+    s = np.abs(o2).max(axis=1)
+    return np.abs(g2 - o2).max(axis=1) / np.where(s > 0, s, 1.0)
+
+
+def rel_l1(g, o):
+    m = o.shape[0]
+    g2, o2 = g.reshape(m, -1), o.reshape(m, -1)
+    s = np.abs(o2).sum(axis=1)
+    return np.abs(g2 - o2).sum(axis=1) / np.where(s > 0, s, 1.0)
+
+
+def check(Ug, Uo, precision, where):
+    if precision == lbmh.FP64:
+        assert np.all(rel_max(Ug, Uo) <= FP64_TOL), (where, rel_max(Ug, Uo))
+    else:
+        assert np.all(rel_l1(Ug, Uo) <= FP32_L1), (where, rel_l1(Ug, Uo))
+        assert np.all(rel_max(Ug, Uo) <= FP32_MAX), (where, rel_max(Ug, Uo))
+
+
+COMBOS = {
+    1: [((W.REFLECT, W.INFLOW, 0, 0), 0.35), ((W.INFLOW, W.REFLECT, 0, 0), 0.0), ((W.OUTFLOW, W.REFLECT, 0, 0), 0.5)],
+    2: [((W.OUTFLOW, W.INFLOW, W.REFLECT, W.REFLECT), 0.3), ((W.REFLECT, W.REFLECT, W.PERIODIC, W.PERIODIC), 0.0),
+        ((W.INFLOW, W.OUTFLOW, W.INFLOW, W.REFLECT), 0.45)],
+}
+
+
+def make(system, dim, bc, sponge, nx, ny, seed):
+    y1 = ny / nx if dim == 2 else 1.0
+    kw = dict(dim=dim, nx=nx, ny=ny if dim == 2 else 1, y1=y1, bc=bc, cfl=0.8, sponge_width=sponge)
+    if system == W.ADVECTION:
+        pb = W.Problem(system=system, adv=(0.8, -0.45), **kw)
+    elif system == W.EULER:
+        pb = W.Problem(system=system, **kw)
+    elif system == W.SWE:
+        pb = W.Problem(system=system, bed_amp=0.3, bed_w2=0.05, bed_xc=0.45, bed_yc=0.2, **kw)
+    else:
+        pb = W.Problem(system=system, gamma=1.2, q=5.0, K=40.0, Ti=2.0, **kw)
+    pb = pb.with_(u_in=tuple(W.random_state(pb, seed=seed + 100).reshape(pb.nfields, -1)[:, 0]))
+    return pb, W.random_state(pb, seed=seed)
+
+
+CASES = [(s, d, bc, sp) for s in (W.ADVECTION, W.EULER, W.SWE, W.REACTIVE) for d in (1, 2) for bc, sp in COMBOS[d]]
+IDS = [f"{W.SYSTEM_NAMES[s]}-{d}d-" + "".join("POR I"[b] for b in bc[:2 * d]) + (f"-s{sp}" if sp else "")
+       for s, d, bc, sp in CASES]
+
+
+@pytest.mark.parametrize("precision", [lbmh.FP64, lbmh.FP32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("system,dim,bc,sponge", CASES, ids=IDS)
+def test_boundaries_match_oracle(system, dim, bc, sponge, precision):
+    nx, ny = (300, 1) if dim == 1 else (257, 37)
+    pb, U0 = make(system, dim, bc, sponge, nx, ny, seed=3)
+    pb = pb.with_(precision=precision)
+    r = oracle.Run(pb, U0)
+    s = lbmh.Solver(pb, precision=precision, kernel=lbmh.KERNEL_FUSED).set_state(U0)
+    for n in range(4):
+        r.step(5)
+        s.step(5)
+        check(s.moments(), r.moments(), precision, 5 * (n + 1))
+    s.close()
+
+
+def test_unfused_path_rejects_the_new_boundaries():
+    pb, _U0 = make(W.EULER, 2, COMBOS[2][0][0], 0.0, 64, 16, seed=1)
+    with pytest.raises(lbmh.LbmhError) as ei:
+        lbmh.Solver(pb, precision=lbmh.FP64, kernel=lbmh.KERNEL_UNFUSED)
+    assert ei.value.code == lbmh.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", [lbmh.FP64, lbmh.FP32], ids=["fp64", "fp32"])
+def test_cellular_detonation_reduced(precision):
+    """Example 5.13 at 1/5 resolution (240 x 180, dx = 1/6), 30 steps."""
+    pb, U0 = W.cellular_detonation(nx=240, ny=180)
+    pb = pb.with_(precision=precision)
+    r = oracle.Run(pb, U0)
+    s = lbmh.Solver(pb, precision=precision, kernel=lbmh.KERNEL_FUSED).set_state(U0)
+    for n in range(3):
+        r.step(10)
+        s.step(10)
+        check(s.moments(), r.moments(), precision, 10 * (n + 1))
+        assert s.info()["status"] & 1 == 0
+    s.close()
+
+
+def test_cellular_detonation_in_a_batch_equals_alone():
+    """The detonation lattice in a batch with a second one gives the bits it
+    gives alone, and agrees with the single-lattice handle at FP32 rounding."""
+    pb, U0 = W.cellular_detonation(nx=120, ny=90)
+    pb2, U2 = W.cellular_detonation(nx=180, ny=135, k=4)
+    pb, pb2 = pb.with_(precision=lbmh.FP32), pb2.with_(precision=lbmh.FP32)
+    cap = 4 * (lbmh.Batch.footprint(pb, lbmh.FP32) + lbmh.Batch.footprint(pb2, lbmh.FP32))
+    alone = lbmh.Batch(W.REACTIVE, precision=lbmh.FP32, capacity_bytes=cap, max_instances=1)
+    sa = alone.add(pb, U0)
+    mix = lbmh.Batch(W.REACTIVE, precision=lbmh.FP32, capacity_bytes=cap, max_instances=2)
+    sm = mix.add(pb, U0)
+    mix.add(pb2, U2)
+    alone.step(25)
+    mix.step(25)
+    Ua, Um = alone.moments(sa), mix.moments(sm)
+    assert np.array_equal(Ua, Um)
+    s = lbmh.Solver(pb, precision=lbmh.FP32, kernel=lbmh.KERNEL_FUSED).set_state(U0).step(25)
+    Us = s.moments()
+    assert np.all(rel_l1(Ua, Us) <= FP32_L1) and np.all(rel_max(Ua, Us) <= FP32_MAX)
+    s.close()
+    alone.close()
+    mix.close()
