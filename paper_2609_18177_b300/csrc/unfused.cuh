@@ -34,13 +34,31 @@ __global__ void k_moments_ext(DevParams P, R* const* buf, const Ctl* ctl, int sl
   int i = map_index(ei - GH, P.nx, P.bc[0], P.bc[1]);
   int j = D == 2 ? map_index(ej - G.gy, P.ny, P.bc[2], P.bc[3]) : 0;
   long long off = cell(P, i, j);
+  R U[M];
 #pragma unroll
   for (int c = 0; c < M; c++) {
     R s = R(0);
 #pragma unroll
     for (int k = 0; k < Q; k++) s += f[(long long)(k * M + c) * P.plane + off];
-    Ue[(long long)c * n + e] = s;
+    U[c] = s;
   }
+  if (P.has_special_bc) {
+    // the moments of the ghost distributions of the fused kernels: a
+    // reflecting ghost has the mirror state with the normal momentum
+    // reversed, an inflow ghost the inflow state
+    const int xs = ghost_side(ei - GH, P.nx, P.bc[0], P.bc[1]);
+    const int ys = D == 2 ? ghost_side(ej - G.gy, P.ny, P.bc[2], P.bc[3]) : -1;
+    constexpr bool momentum = SYS == SYS_EULER || SYS == SYS_SWE || SYS == SYS_REACT;
+    if (xs == BC_INFLOW || ys == BC_INFLOW) {
+#pragma unroll
+      for (int c = 0; c < M; c++) U[c] = sizeof(R) == 4 ? R(P.pf.u_in[c]) : R(P.u_in[c]);
+    } else if constexpr (momentum) {
+      if (xs == BC_REFLECT) U[1] = -U[1];
+      if (D == 2 && ys == BC_REFLECT) U[2] = -U[2];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < M; c++) Ue[(long long)c * n + e] = U[c];
 }
 
 // K1: nu = sum_j sum_r theta^{(r,j)} (Eq. 2.10/2.14) one layer inside the extension
@@ -91,6 +109,12 @@ __global__ void k_omega(DevParams P, const Ctl* ctl, int slot, ExtGeom G, const 
     for (int bj = (D == 2 ? -1 : 0); bj <= (D == 2 ? 1 : 0); bj++)
       for (int bi = -1; bi <= 1; bi++) s += nu[e + (long long)bj * G.ex + bi];
     w = R(1) + fdiv(R(1), R(1) + s);
+  }
+  if (P.sponge_width > 0.0) {  // blended toward 1 over the sponge (x-lo)
+    const double r = (double)(ei - GH) + 0.5;
+    const double x = r * P.sponge_dx_over_w;
+    const double keep = x <= 0.0 ? 0.0 : (x >= 1.0 ? 1.0 : 1.0 - 0.5 * (1.0 + cos(3.14159265358979323846 * x)));
+    w = R(1) + (w - R(1)) * R(keep);
   }
   om[e] = w;
 }

@@ -132,3 +132,15 @@ def test_cellular_detonation_in_a_batch_equals_alone():
     s.close()
     alone.close()
     mix.close()
+
+
+@pytest.mark.parametrize("case", [0, 2])
+def test_omega_diagnostic_with_walls_inflow_and_sponge(case):
+    bc, sponge = COMBOS[2][case]
+    pb, U0 = make(W.EULER, 2, bc, sponge, 130, 21, seed=8)
+    r = oracle.Run(pb, U0).step(4)
+    s = lbmh.Solver(pb, precision=lbmh.FP64, kernel=lbmh.KERNEL_FUSED).set_state(U0).step(4)
+    om_g = s.omega()
+    r.step(1, want_omega=True)
+    assert np.abs(om_g - r.omega).max() <= 1e-12
+    s.close()
