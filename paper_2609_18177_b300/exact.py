@@ -1,4 +1,5 @@
-"""Exact solutions used to pin the oracle (test infrastructure).
+"""Exact solutions of textbook problems: they pin the oracle in the tests and
+are the reference curves of the example figures (`figures.py`).
 
 - Euler Riemann problem: exact solver built on the pressure function of the
   two-rarefaction/two-shock analysis (Toro, "Riemann Solvers and Numerical
@@ -7,8 +8,8 @@
 - Shallow-water dam break over a dry bed (Ritter's solution), used for
   Example 5.9.
 
-Written from the textbook definitions; nothing here is shared with the oracle
-or the CUDA path.
+Written from the textbook definitions; neither the oracle nor the CUDA path
+uses it.
 """
 import math
 

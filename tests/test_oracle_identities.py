@@ -19,7 +19,7 @@ import pytest
 from scipy.optimize import brentq
 
 import oracle
-from exact_solutions import riemann_profile, ritter
+from paper_2609_18177_b300.exact import riemann_profile, ritter
 from paper_2609_18177_b300 import workloads as W
 
 GAMMA = 1.4

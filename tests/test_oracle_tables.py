@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 from conftest import load_golden
-from exact_solutions import total_variation
+from paper_2609_18177_b300.exact import total_variation
 from paper_2609_18177_b300 import workloads as W
 
 
