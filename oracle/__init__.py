@@ -29,8 +29,11 @@ class _Problem(ctypes.Structure):
         ("x0", ctypes.c_double), ("x1", ctypes.c_double),
         ("y0", ctypes.c_double), ("y1", ctypes.c_double),
         ("bc", ctypes.c_int * 4),
+        ("nz", ctypes.c_int),
+        ("z0", ctypes.c_double), ("z1", ctypes.c_double),
+        ("bc_z", ctypes.c_int * 2),
         ("cfl", ctypes.c_double), ("eps", ctypes.c_double),
-        ("adv", ctypes.c_double * 2),
+        ("adv", ctypes.c_double * 3),
         ("gamma", ctypes.c_double), ("g", ctypes.c_double),
         ("bed_amp", ctypes.c_double), ("bed_w2", ctypes.c_double),
         ("bed_xc", ctypes.c_double), ("bed_yc", ctypes.c_double),
@@ -88,12 +91,17 @@ def _c_problem(pb):
     s.system = int(pb.system)
     s.dim = int(pb.dim)
     s.nx = int(pb.nx)
-    s.ny = int(pb.ny) if pb.dim == 2 else 1
+    s.ny = int(pb.ny) if pb.dim >= 2 else 1
+    s.nz = int(getattr(pb, "nz", 1)) if pb.dim == 3 else 1
+    s.z0, s.z1 = float(getattr(pb, "z0", 0.0)), float(getattr(pb, "z1", 1.0))
+    bz = tuple(getattr(pb, "bc_z", (PERIODIC, PERIODIC)))
+    s.bc_z[0], s.bc_z[1] = int(bz[0]), int(bz[1])
     s.x0, s.x1, s.y0, s.y1 = float(pb.x0), float(pb.x1), float(pb.y0), float(pb.y1)
     for i in range(4):
         s.bc[i] = int(pb.bc[i])
     s.cfl, s.eps = float(pb.cfl), float(pb.eps)
-    s.adv[0], s.adv[1] = float(pb.adv[0]), float(pb.adv[1])
+    for i, v in enumerate(tuple(pb.adv)[:3]):
+        s.adv[i] = float(v)
     s.gamma, s.g = float(pb.gamma), float(pb.g)
     s.bed_amp, s.bed_w2 = float(pb.bed_amp), float(pb.bed_w2)
     s.bed_xc, s.bed_yc = float(pb.bed_xc), float(pb.bed_yc)
@@ -123,6 +131,8 @@ def nq(pb):
 
 
 def grid_shape(pb):
+    if pb.dim == 3:
+        return (pb.nz, pb.ny, pb.nx)
     return (pb.ny, pb.nx) if pb.dim == 2 else (1, pb.nx)
 
 
@@ -180,7 +190,7 @@ def equilibrium(pb, U, alpha, lam):
     """f^eq_k(U) for k = 0..2d, shape (Q, m)."""
     s, _k = _c_problem(pb)
     U = np.ascontiguousarray(U, dtype=np.float64)
-    a = np.zeros(2)
+    a = np.zeros(3)
     a[: len(alpha)] = alpha
     feq = np.zeros((nq(pb), U.size))
     lib().orc_equilibrium(ctypes.byref(s), _dp(U), _dp(a), float(lam), _dp(feq))
@@ -198,9 +208,9 @@ def moments(pb, f):
 def alpha_bar(pb, U):
     s, _k = _c_problem(pb)
     U = np.ascontiguousarray(U, dtype=np.float64)
-    out = np.zeros(2)
+    out = np.zeros(3)
     _check(lib().orc_alpha_bar_U(ctypes.byref(s), _dp(U), _dp(out)))
-    return out
+    return out[: max(pb.dim, 2)]
 
 
 def _check(rc):
@@ -210,16 +220,16 @@ def _check(rc):
 
 
 class Run:
-    """A solve held by the oracle: distributions f[k][c][y][x] and time t."""
+    """A solve held by the oracle: distributions f[k][c][(z)][y][x] and time t."""
 
     def __init__(self, pb, U0):
         self.pb = pb
         self._s, self._keep = _c_problem(pb)
         self.m = lib().orc_nfields(ctypes.byref(self._s))
-        ny, nx = grid_shape(pb)
-        U0 = np.ascontiguousarray(np.asarray(U0, dtype=np.float64).reshape(self.m, ny, nx))
-        self.f = np.zeros((nq(pb), self.m, ny, nx))
-        self.info = np.zeros(4)
+        shp = grid_shape(pb)
+        U0 = np.ascontiguousarray(np.asarray(U0, dtype=np.float64).reshape((self.m,) + shp))
+        self.f = np.zeros((nq(pb), self.m) + shp)
+        self.info = np.zeros(5)  # abar_x, abar_y, dt, lambda, abar_z
         _check(lib().orc_init(ctypes.byref(self._s), _dp(U0), _dp(self.f), _dp(self.info)))
         self.t = 0.0
         self.nsteps = 0

@@ -83,8 +83,11 @@ typedef struct {
     int nx, ny;
     double x0, x1, y0, y1;
     int bc[4]; /* xlo, xhi, ylo, yhi */
+    int nz;           /* 3D (D3Q7): nodes in z */
+    double z0, z1;
+    int bc_z[2];      /* zlo, zhi */
     double cfl, eps;
-    double adv[2];
+    double adv[3];
     double gamma, g;
     double bed_amp, bed_w2, bed_xc, bed_yc;
     double K, Ti, q;
@@ -114,22 +117,37 @@ int orc_nfields(const orc_problem *p) {
 
 static int nq(const orc_problem *p) { return 2 * p->dim + 1; }
 static double mesh_dx(const orc_problem *p) { return (p->x1 - p->x0) / p->nx; }
-static int ny_of(const orc_problem *p) { return p->dim == 2 ? p->ny : 1; }
+static int ny_of(const orc_problem *p) { return p->dim >= 2 ? p->ny : 1; }
+static int nz_of(const orc_problem *p) { return p->dim == 3 ? p->nz : 1; }
+/* rows of the [Q][m][rows][nx] layout: y and z flattened (z outer) */
+static int rows_of(const orc_problem *p) { return ny_of(p) * nz_of(p); }
 
 static int check_problem(const orc_problem *p) {
-    if (p->dim != 1 && p->dim != 2) return ORC_ERR_ARG;
-    if (p->nx < 1 || (p->dim == 2 && p->ny < 1)) return ORC_ERR_ARG;
+    if (p->dim < 1 || p->dim > 3) return ORC_ERR_ARG;
+    if (p->nx < 1 || (p->dim >= 2 && p->ny < 1) || (p->dim == 3 && p->nz < 1)) return ORC_ERR_ARG;
+    if (p->dim == 3) {
+        /* D3Q7: scalar advection, Euler and reactive Euler; periodic or outflow */
+        if (p->system != ORC_ADVECTION && p->system != ORC_EULER && p->system != ORC_REACTIVE) return ORC_ERR_ARG;
+        for (int b = 0; b < 4; b++)
+            if (p->bc[b] != ORC_BC_PERIODIC && p->bc[b] != ORC_BC_OUTFLOW) return ORC_ERR_ARG;
+        for (int b = 0; b < 2; b++)
+            if (p->bc_z[b] != ORC_BC_PERIODIC && p->bc_z[b] != ORC_BC_OUTFLOW) return ORC_ERR_ARG;
+        if ((p->bc_z[0] == ORC_BC_PERIODIC) != (p->bc_z[1] == ORC_BC_PERIODIC)) return ORC_ERR_ARG;
+        double dx = mesh_dx(p), dz = (p->z1 - p->z0) / p->nz;
+        if (fabs(dx - dz) > 1e-12 * dx) return ORC_ERR_ARG;
+        if (p->sponge_width != 0.0) return ORC_ERR_ARG;
+    }
     int m = orc_nfields(p);
     if (m < 1 || m > MAXM) return ORC_ERR_ARG;
-    for (int b = 0; b < 2 * p->dim; b++)
+    for (int b = 0; b < 2 * (p->dim < 2 ? p->dim : 2); b++)
         if (p->bc[b] < ORC_BC_PERIODIC || p->bc[b] > ORC_BC_INFLOW) return ORC_ERR_ARG;
     if ((p->bc[0] == ORC_BC_REFLECT || p->bc[1] == ORC_BC_REFLECT || p->bc[2] == ORC_BC_REFLECT ||
          p->bc[3] == ORC_BC_REFLECT) && (p->system == ORC_LINEAR || p->nx < GHOST || (p->dim == 2 && p->ny < GHOST)))
         return ORC_ERR_ARG;
     if (p->sponge_width < 0.0) return ORC_ERR_ARG;
     if ((p->bc[0] == ORC_BC_PERIODIC) != (p->bc[1] == ORC_BC_PERIODIC)) return ORC_ERR_ARG;
-    if (p->dim == 2 && (p->bc[2] == ORC_BC_PERIODIC) != (p->bc[3] == ORC_BC_PERIODIC)) return ORC_ERR_ARG;
-    if (p->dim == 2) {
+    if (p->dim >= 2 && (p->bc[2] == ORC_BC_PERIODIC) != (p->bc[3] == ORC_BC_PERIODIC)) return ORC_ERR_ARG;
+    if (p->dim >= 2) {
         double dx = mesh_dx(p), dy = (p->y1 - p->y0) / p->ny;
         if (fabs(dx - dy) > 1e-12 * dx) return ORC_ERR_ARG; /* uniform mesh, Section 2.2.2 */
     }
@@ -176,7 +194,7 @@ static double sponge_sigma(const orc_problem *p, double x) {
 
 static double node_x(const orc_problem *p, int i) { return p->x0 + (i + 0.5) * mesh_dx(p); }
 static double node_y(const orc_problem *p, int j) {
-    if (p->dim == 1) return 0.0;
+    if (p->dim < 2) return 0.0;
     return p->y0 + (j + 0.5) * ((p->y1 - p->y0) / p->ny);
 }
 
@@ -185,7 +203,7 @@ static double node_y(const orc_problem *p, int j) {
 /* ------------------------------------------------------------------ */
 
 typedef struct {
-    double rho, u, v, p, Y, c, H; /* Euler-type */
+    double rho, u, v, w, p, Y, c, H; /* Euler-type */
     double h;                     /* shallow water */
     int dry;
 } prim_t;
@@ -197,9 +215,10 @@ static prim_t primitives(const orc_problem *p, const double *U) {
         int d = p->dim;
         w.rho = U[0];
         w.u = U[1] / w.rho;
-        w.v = d == 2 ? U[2] / w.rho : 0.0;
+        w.v = d >= 2 ? U[2] / w.rho : 0.0;
+        w.w = d == 3 ? U[3] / w.rho : 0.0;
         double E = U[d + 1];
-        double kin = 0.5 * w.rho * (w.u * w.u + w.v * w.v);
+        double kin = 0.5 * w.rho * (w.u * w.u + w.v * w.v + w.w * w.w);
         double chem = 0.0;
         if (p->system == ORC_REACTIVE) {
             w.Y = U[d + 2] / w.rho;
@@ -247,10 +266,11 @@ void orc_flux(const orc_problem *p, int dir, const double *U, double *F) {
         return;
     }
     /* Euler / reactive Euler */
-    double vn = dir == 0 ? w.u : w.v;
+    double vn = dir == 0 ? w.u : (dir == 1 ? w.v : w.w);
     F[0] = w.rho * vn;
     F[1] = w.rho * w.u * vn + (dir == 0 ? w.p : 0.0);
-    if (d == 2) F[2] = w.rho * w.v * vn + (dir == 1 ? w.p : 0.0);
+    if (d >= 2) F[2] = w.rho * w.v * vn + (dir == 1 ? w.p : 0.0);
+    if (d == 3) F[3] = w.rho * w.w * vn + (dir == 2 ? w.p : 0.0);
     F[d + 1] = vn * (U[d + 1] + w.p);
     if (p->system == ORC_REACTIVE) F[d + 2] = U[d + 2] * vn;
 }
@@ -306,7 +326,7 @@ void orc_eigvals(const orc_problem *p, int dir, const double *U, double *lam) {
         return;
     }
     prim_t w = primitives(p, U);
-    double vn = dir == 0 ? w.u : w.v;
+    double vn = dir == 0 ? w.u : (dir == 1 ? w.v : w.w);
     lam[0] = vn - w.c;
     for (int r = 1; r < m - 1; r++) lam[r] = vn;
     lam[m - 1] = vn + w.c;
@@ -357,8 +377,9 @@ void orc_right_eigvecs(const orc_problem *p, int dir, const double *U, double *R
         return;
     }
     /* Euler / reactive: columns = (u-c), entropy, [shear], [species], (u+c) */
-    double c = w.c, H = w.H, q2 = 0.5 * (w.u * w.u + w.v * w.v);
-    double vn = dir == 0 ? w.u : w.v;
+    double c = w.c, H = w.H, q2 = 0.5 * (w.u * w.u + w.v * w.v + w.w * w.w);
+    double vel[3] = {w.u, w.v, w.w};
+    double vn = vel[dir];
     int iE = d + 1, iY = d + 2, last = m - 1;
     int reactive = p->system == ORC_REACTIVE;
     double qY = reactive ? p->q * w.Y : 0.0;
@@ -367,21 +388,20 @@ void orc_right_eigvecs(const orc_problem *p, int dir, const double *U, double *R
         int col = s == 0 ? 0 : last;
         double sg = s == 0 ? -1.0 : 1.0;
         RS(0, col, 1.0);
-        RS(1, col, w.u + (dir == 0 ? sg * c : 0.0));
-        if (d == 2) RS(2, col, w.v + (dir == 1 ? sg * c : 0.0));
+        for (int t = 0; t < d; t++) RS(1 + t, col, vel[t] + (dir == t ? sg * c : 0.0));
         RS(iE, col, H + sg * vn * c);
         if (reactive) RS(iY, col, w.Y);
     }
     /* entropy wave */
     RS(0, 1, 1.0);
-    RS(1, 1, w.u);
-    if (d == 2) RS(2, 1, w.v);
+    for (int t = 0; t < d; t++) RS(1 + t, 1, vel[t]);
     RS(iE, 1, q2 + qY);
     if (reactive) RS(iY, 1, w.Y);
     int col = 2;
-    if (d == 2) { /* shear wave: unit tangential velocity */
-        if (dir == 0) { RS(2, col, 1.0); RS(iE, col, w.v); }
-        else { RS(1, col, 1.0); RS(iE, col, w.u); }
+    for (int t = 0; t < d; t++) { /* shear waves: unit tangential velocity */
+        if (t == dir) continue;
+        RS(1 + t, col, 1.0);
+        RS(iE, col, vel[t]);
         col++;
     }
     if (reactive) { /* species wave */
@@ -455,7 +475,8 @@ void orc_source(const orc_problem *p, const double *U, double x, double y, doubl
         S[1] = -p->g * U[0] * bx;
         if (d == 2) S[2] = -p->g * U[0] * by;
     } else if (p->system == ORC_REACTIVE && p->K != 0.0) {
-        double momsq = U[1] * U[1] + (d == 2 ? U[2] * U[2] : 0.0);
+        double momsq = 0.0;
+        for (int t = 0; t < d; t++) momsq += U[1 + t] * U[1 + t];
         S[d + 2] = -arrhenius_rate(p, U[0], momsq, U[d + 1], U[d + 2]);
     }
 }
@@ -506,7 +527,8 @@ static int solve_implicit_moment(const orc_problem *p, const double *Ubar, doubl
         /* only rho*Y carries a source; rho, momentum and rho*E equal their
          * streamed values.  g(z) = z - zbar + dt/2 R(z) = 0. */
         double rho = Ubar[0], E = Ubar[d + 1], zbar = Ubar[d + 2];
-        double momsq = Ubar[1] * Ubar[1] + (d == 2 ? Ubar[2] * Ubar[2] : 0.0);
+        double momsq = 0.0;
+        for (int t = 0; t < d; t++) momsq += Ubar[t + 1] * Ubar[t + 1];
         double lo = zbar < 0.0 ? zbar : 0.0, hi = zbar < 0.0 ? 0.0 : zbar;
         if (zbar == 0.0) { Un[d + 2] = 0.0; return 0; }
 #define GFUN(z) ((z) - zbar + 0.5 * dt * arrhenius_rate(p, rho, momsq, E, (z)))
@@ -559,7 +581,7 @@ static int nonphysical(const orc_problem *p, const double *U) {
 /* U = sum_k f_k, Eq. (2.3), summed in the order k = 0..Q-1 */
 int orc_moments(const orc_problem *p, const double *f, double *U) {
     if (check_problem(p)) return ORC_ERR_ARG;
-    int m = orc_nfields(p), Q = nq(p), nx = p->nx, ny = ny_of(p);
+    int m = orc_nfields(p), Q = nq(p), nx = p->nx, ny = rows_of(p);
 #pragma omp parallel for
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++)
@@ -574,7 +596,7 @@ int orc_moments(const orc_problem *p, const double *f, double *U) {
 /* abar_j = max over nodes of max_r |lambda_r(dF_j/dU)|, Eq. (2.17)/(2.19) */
 int orc_alpha_bar_U(const orc_problem *p, const double *U, double *abar) {
     if (check_problem(p)) return ORC_ERR_ARG;
-    int m = orc_nfields(p), nx = p->nx, ny = ny_of(p), d = p->dim;
+    int m = orc_nfields(p), nx = p->nx, ny = rows_of(p), d = p->dim;
     for (int j = 0; j < d; j++) abar[j] = 0.0;
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
@@ -600,15 +622,15 @@ static double time_step(const orc_problem *p, const double *abar, double dt_cap)
 /* f := f^eq(U) with alpha^0 and lambda^0 taken from U (uncapped dt) */
 int orc_init(const orc_problem *p, const double *U, double *f, double *info) {
     if (check_problem(p)) return ORC_ERR_ARG;
-    int m = orc_nfields(p), Q = nq(p), nx = p->nx, ny = ny_of(p), d = p->dim;
-    double abar[2] = {0, 0}, alpha[2];
+    int m = orc_nfields(p), Q = nq(p), nx = p->nx, ny = rows_of(p), d = p->dim;
+    double abar[3] = {0, 0, 0}, alpha[3];
     orc_alpha_bar_U(p, U, abar);
     double dt = time_step(p, abar, 0.0), lam = mesh_dx(p) / dt;
     for (int j = 0; j < d; j++) alpha[j] = abar[j] + p->eps;
 #pragma omp parallel for
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
-            double Ui[MAXM], feq[5 * MAXM];
+            double Ui[MAXM], feq[7 * MAXM];
             for (int c = 0; c < m; c++) Ui[c] = U[UIDX(c, j, i)];
             orc_equilibrium(p, Ui, alpha, lam, feq);
             for (int k = 0; k < Q; k++)
@@ -616,9 +638,10 @@ int orc_init(const orc_problem *p, const double *U, double *f, double *info) {
         }
     if (info) {
         info[0] = abar[0];
-        info[1] = d == 2 ? abar[1] : 0.0;
+        info[1] = d >= 2 ? abar[1] : 0.0;
         info[2] = dt;
         info[3] = lam;
+        if (d == 3) info[4] = abar[2];
     }
     return ORC_OK;
 }
@@ -654,204 +677,226 @@ static double theta_sum(int m, const double *L, const double *Um, const double *
 int orc_step(const orc_problem *p, const double *f, double *fn, double dt_cap, const double *abar_in,
              double *info, double *omega_out) {
     if (check_problem(p)) return ORC_ERR_ARG;
-    const int m = orc_nfields(p), Q = nq(p), d = p->dim, nx = p->nx, ny = ny_of(p);
+    const int m = orc_nfields(p), Q = nq(p), d = p->dim, nx = p->nx, ny = ny_of(p), nz = nz_of(p);
     const int G = GHOST;
-    const int ex = nx + 2 * G, ey = d == 2 ? ny + 2 * G : 1, gy = d == 2 ? G : 0;
+    /* ghost-extended grid: G layers in every active direction */
+    const int ex = nx + 2 * G, ey = d >= 2 ? ny + 2 * G : 1, ez = d == 3 ? nz + 2 * G : 1;
+    const int gy = d >= 2 ? G : 0, gz = d == 3 ? G : 0;
     const double dx = mesh_dx(p);
-    const size_t next = (size_t)ex * ey;
+    const size_t next = (size_t)ex * ey * ez;
+    const size_t stride[3] = {1, (size_t)ex, (size_t)ex * ey};
+    const int lo[3] = {G, gy, gz}, n_[3] = {nx, ny, nz};
+    const int bclo[3] = {p->bc[0], p->bc[2], p->bc_z[0]}, bchi[3] = {p->bc[1], p->bc[3], p->bc_z[1]};
     int flags = 0;
 
-    /* ghost-extended copies: fe[k][c][ey][ex], Ue[c][ey][ex], nu, om, post */
+    /* ghost-extended copies: fe[k][c][e], Ue[c][e], nu[e], om[e], post[k][c][e] */
     double *fe = malloc(sizeof(double) * Q * m * next);
     double *Ue = malloc(sizeof(double) * m * next);
     double *nu = malloc(sizeof(double) * next);
     double *om = malloc(sizeof(double) * next);
     double *post = malloc(sizeof(double) * Q * m * next);
-    int *srcj = malloc(sizeof(int) * ey), *srci = malloc(sizeof(int) * ex);
-    if (!fe || !Ue || !nu || !om || !post || !srcj || !srci) {
-        free(fe); free(Ue); free(nu); free(om); free(post); free(srcj); free(srci);
-        return ORC_ERR_MEM;
-    }
-#define E1(j, i) ((size_t)(j) * ex + (i))
-#define EF(k, c, j, i) ((((size_t)(k) * m + (c)) * ey + (j)) * ex + (i))
-#define EU(c, j, i) (((size_t)(c) * ey + (j)) * ex + (i))
-    for (int ei = 0; ei < ex; ei++) srci[ei] = map_index(ei - G, nx, p->bc[0], p->bc[1]);
-    for (int ej = 0; ej < ey; ej++) srcj[ej] = d == 2 ? map_index(ej - gy, ny, p->bc[2], p->bc[3]) : 0;
-    /* node positions of the extended grid: a periodic or outflow ghost sits
-     * where the node it copies sits, a reflecting ghost at its own position */
+    int *srci = malloc(sizeof(int) * ex), *srcj = malloc(sizeof(int) * ey), *srck = malloc(sizeof(int) * ez);
     double *posx = malloc(sizeof(double) * ex), *posy = malloc(sizeof(double) * ey);
-    if (!posx || !posy) {
-        free(fe); free(Ue); free(nu); free(om); free(post); free(srcj); free(srci); free(posx); free(posy);
+    if (!fe || !Ue || !nu || !om || !post || !srci || !srcj || !srck || !posx || !posy) {
+        free(fe); free(Ue); free(nu); free(om); free(post); free(srci); free(srcj); free(srck);
+        free(posx); free(posy);
         return ORC_ERR_MEM;
     }
+#define EI(kk, j, i) (((size_t)(kk) * ey + (j)) * ex + (i))
+#define EF(k, c, e) (((size_t)(k) * m + (c)) * next + (e))
+#define EU(c, e) ((size_t)(c) * next + (e))
+#define FI(k, c, kk, j, i) (((((size_t)(k) * m + (c)) * nz + (kk)) * ny + (j)) * nx + (i))
+    for (int ei = 0; ei < ex; ei++) srci[ei] = map_index(ei - G, nx, bclo[0], bchi[0]);
+    for (int ej = 0; ej < ey; ej++) srcj[ej] = d >= 2 ? map_index(ej - gy, ny, bclo[1], bchi[1]) : 0;
+    for (int ek = 0; ek < ez; ek++) srck[ek] = d == 3 ? map_index(ek - gz, nz, bclo[2], bchi[2]) : 0;
+    /* node positions (bed source): a periodic or outflow ghost sits where the
+     * node it copies sits, a reflecting ghost at its own position */
     for (int ei = 0; ei < ex; ei++)
-        posx[ei] = ghost_side(ei - G, nx, p->bc[0], p->bc[1]) == ORC_BC_REFLECT ? node_x(p, ei - G) : node_x(p, srci[ei]);
+        posx[ei] = ghost_side(ei - G, nx, bclo[0], bchi[0]) == ORC_BC_REFLECT ? node_x(p, ei - G) : node_x(p, srci[ei]);
     for (int ej = 0; ej < ey; ej++)
-        posy[ej] = d == 2 && ghost_side(ej - gy, ny, p->bc[2], p->bc[3]) == ORC_BC_REFLECT ? node_y(p, ej - gy)
-                                                                                           : node_y(p, srcj[ej]);
+        posy[ej] = d >= 2 && ghost_side(ej - gy, ny, bclo[1], bchi[1]) == ORC_BC_REFLECT ? node_y(p, ej - gy)
+                                                                                          : node_y(p, srcj[ej]);
 
     /* 1. ghost-extended distributions and moments U = sum_k f_k; across a
      * reflecting boundary the mirror node's distributions with the normal
      * velocities exchanged and the normal momentum negated */
-#pragma omp parallel for
-    for (int ej = 0; ej < ey; ej++)
-        for (int ei = 0; ei < ex; ei++) {
-            int j = srcj[ej], i = srci[ei];
-            int refl[2] = {ghost_side(ei - G, nx, p->bc[0], p->bc[1]) == ORC_BC_REFLECT,
-                           d == 2 && ghost_side(ej - gy, ny, p->bc[2], p->bc[3]) == ORC_BC_REFLECT};
-            for (int c = 0; c < m; c++) {
-                double s = 0.0;
-                for (int k = 0; k < Q; k++) {
-                    int ks = k;  /* the velocity read from the mirror node */
-                    double sign = 1.0;
-                    for (int dir = 0; dir < d; dir++) {
-                        if (!refl[dir]) continue;
-                        if (ks == 1 + dir) ks = 1 + d + dir;
-                        else if (ks == 1 + d + dir) ks = 1 + dir;
-                        if (c == momentum_index(p, dir)) sign = -sign;
+#pragma omp parallel for collapse(2)
+    for (int ek = 0; ek < ez; ek++)
+        for (int ej = 0; ej < ey; ej++)
+            for (int ei = 0; ei < ex; ei++) {
+                const size_t e = EI(ek, ej, ei);
+                const int i = srci[ei], j = srcj[ej], kk = srck[ek];
+                const int ec[3] = {ei, ej, ek};
+                int refl[3] = {0, 0, 0};
+                for (int dir = 0; dir < d; dir++)
+                    refl[dir] = ghost_side(ec[dir] - lo[dir], n_[dir], bclo[dir], bchi[dir]) == ORC_BC_REFLECT;
+                for (int c = 0; c < m; c++) {
+                    double sum = 0.0;
+                    for (int k = 0; k < Q; k++) {
+                        int ks = k; /* the velocity read from the mirror node */
+                        double sign = 1.0;
+                        for (int dir = 0; dir < d; dir++) {
+                            if (!refl[dir]) continue;
+                            if (ks == 1 + dir) ks = 1 + d + dir;
+                            else if (ks == 1 + d + dir) ks = 1 + dir;
+                            if (c == momentum_index(p, dir)) sign = -sign;
+                        }
+                        double v = sign * f[FI(ks, c, kk, j, i)];
+                        fe[EF(k, c, e)] = v;
+                        sum += v;
                     }
-                    double v = sign * f[FIDX(ks, c, j, i)];
-                    fe[EF(k, c, ej, ei)] = v;
-                    s += v;
+                    Ue[EU(c, e)] = sum;
                 }
-                Ue[EU(c, ej, ei)] = s;
             }
-        }
 
     /* 2. global speed bound over the interior nodes */
-    double abar[2] = {0.0, 0.0}, alpha[2] = {0.0, 0.0};
+    double abar[3] = {0.0, 0.0, 0.0}, alpha[3] = {0.0, 0.0, 0.0};
     if (abar_in) {
         for (int j = 0; j < d; j++) abar[j] = abar_in[j];
     } else {
-        for (int ej = gy; ej < gy + ny; ej++)
-            for (int ei = G; ei < G + nx; ei++) {
-                double Ui[MAXM];
-                for (int c = 0; c < m; c++) Ui[c] = Ue[EU(c, ej, ei)];
-                for (int dir = 0; dir < d; dir++) {
-                    double s = orc_max_speed(p, dir, Ui);
-                    if (s > abar[dir] || s != s) abar[dir] = s;
+        for (int ek = gz; ek < gz + nz; ek++)
+            for (int ej = gy; ej < gy + ny; ej++)
+                for (int ei = G; ei < G + nx; ei++) {
+                    double Ui[MAXM];
+                    for (int c = 0; c < m; c++) Ui[c] = Ue[EU(c, EI(ek, ej, ei))];
+                    for (int dir = 0; dir < d; dir++) {
+                        double sp = orc_max_speed(p, dir, Ui);
+                        if (sp > abar[dir] || sp != sp) abar[dir] = sp;
+                    }
                 }
-            }
     }
     /* 3. time step, lattice speed, alpha_j = abar_j + eps */
     double dt = time_step(p, abar, dt_cap);
     double lam = dx / dt;
     for (int j = 0; j < d; j++) alpha[j] = abar[j] + p->eps;
-    double a[5];
+    double a[7];
     weights_a(d, alpha, lam, a);
 
     /* 3b. ghost nodes across an inflow boundary: f^eq(U_in) with this step's
      * alpha and lambda */
-    {
-        double feq_in[5 * MAXM];
+    if (d <= 2) {
+        double feq_in[7 * MAXM];
         orc_equilibrium(p, p->u_in, alpha, lam, feq_in);
         for (int ej = 0; ej < ey; ej++)
             for (int ei = 0; ei < ex; ei++) {
-                int in = ghost_side(ei - G, nx, p->bc[0], p->bc[1]) == ORC_BC_INFLOW ||
-                         (d == 2 && ghost_side(ej - gy, ny, p->bc[2], p->bc[3]) == ORC_BC_INFLOW);
+                int in = ghost_side(ei - G, nx, bclo[0], bchi[0]) == ORC_BC_INFLOW ||
+                         (d == 2 && ghost_side(ej - gy, ny, bclo[1], bchi[1]) == ORC_BC_INFLOW);
                 if (!in) continue;
+                const size_t e = EI(0, ej, ei);
                 for (int c = 0; c < m; c++) {
-                    for (int k = 0; k < Q; k++) fe[EF(k, c, ej, ei)] = feq_in[k * m + c];
-                    double s = 0.0;
-                    for (int k = 0; k < Q; k++) s += feq_in[k * m + c];
-                    Ue[EU(c, ej, ei)] = s;
+                    for (int k = 0; k < Q; k++) fe[EF(k, c, e)] = feq_in[k * m + c];
+                    double sum = 0.0;
+                    for (int k = 0; k < Q; k++) sum += feq_in[k * m + c];
+                    Ue[EU(c, e)] = sum;
                 }
             }
     }
 
     /* 4. smoothness indicator nu on nodes one layer inside the extension */
     for (size_t e = 0; e < next; e++) nu[e] = 0.0;
-#pragma omp parallel for
-    for (int ej = (d == 2 ? 1 : 0); ej < (d == 2 ? ey - 1 : 1); ej++)
-        for (int ei = 1; ei < ex - 1; ei++) {
-            double U0[MAXM], Um[MAXM], Up[MAXM], L[MAXM * MAXM];
-            for (int c = 0; c < m; c++) U0[c] = Ue[EU(c, ej, ei)];
-            double s = 0.0;
-            for (int dir = 0; dir < d; dir++) {
-                int di = dir == 0 ? 1 : 0, dj = dir == 1 ? 1 : 0;
-                for (int c = 0; c < m; c++) {
-                    Um[c] = Ue[EU(c, ej - dj, ei - di)];
-                    Up[c] = Ue[EU(c, ej + dj, ei + di)];
+    const int in1[3][2] = {{1, ex - 1}, {d >= 2 ? 1 : 0, d >= 2 ? ey - 1 : 1}, {d == 3 ? 1 : 0, d == 3 ? ez - 1 : 1}};
+#pragma omp parallel for collapse(2)
+    for (int ek = in1[2][0]; ek < in1[2][1]; ek++)
+        for (int ej = in1[1][0]; ej < in1[1][1]; ej++)
+            for (int ei = in1[0][0]; ei < in1[0][1]; ei++) {
+                const size_t e = EI(ek, ej, ei);
+                double U0[MAXM], Um[MAXM], Up[MAXM], L[MAXM * MAXM];
+                for (int c = 0; c < m; c++) U0[c] = Ue[EU(c, e)];
+                double sum = 0.0;
+                for (int dir = 0; dir < d; dir++) {
+                    for (int c = 0; c < m; c++) {
+                        Um[c] = Ue[EU(c, e - stride[dir])];
+                        Up[c] = Ue[EU(c, e + stride[dir])];
+                    }
+                    orc_left_eigvecs(p, dir, U0, L);
+                    sum += theta_sum(m, L, Um, U0, Up, dx);
                 }
-                orc_left_eigvecs(p, dir, U0, L);
-                s += theta_sum(m, L, Um, U0, Up, dx);
+                nu[e] = sum;
             }
-            nu[E1(ej, ei)] = s;
-        }
 
-    /* 5. smoothed indicator over the 3^d box and the relaxation parameter */
-    int jlo = d == 2 ? 2 : 0, jhi = d == 2 ? ey - 2 : 1;
-#pragma omp parallel for
-    for (int ej = jlo; ej < jhi; ej++)
-        for (int ei = 2; ei < ex - 2; ei++) {
-            double w;
-            if (p->omega_mode == 1) {
-                w = p->omega_fixed;
-            } else {
-                double nt = 0.0;
-                for (int bj = (d == 2 ? -1 : 0); bj <= (d == 2 ? 1 : 0); bj++)
-                    for (int bi = -1; bi <= 1; bi++) nt += nu[E1(ej + bj, ei + bi)];
-                w = 1.0 + 1.0 / (1.0 + nt);
+    /* 5. smoothed indicator over the 3^d box and the relaxation parameter,
+     * on nodes two layers inside the extension */
+    const int in2[3][2] = {{2, ex - 2}, {d >= 2 ? 2 : 0, d >= 2 ? ey - 2 : 1}, {d == 3 ? 2 : 0, d == 3 ? ez - 2 : 1}};
+    const int bj0 = d >= 2 ? -1 : 0, bk0 = d == 3 ? -1 : 0;
+#pragma omp parallel for collapse(2)
+    for (int ek = in2[2][0]; ek < in2[2][1]; ek++)
+        for (int ej = in2[1][0]; ej < in2[1][1]; ej++)
+            for (int ei = in2[0][0]; ei < in2[0][1]; ei++) {
+                double w;
+                if (p->omega_mode == 1) {
+                    w = p->omega_fixed;
+                } else {
+                    double nt = 0.0;
+                    for (int bk = bk0; bk <= -bk0; bk++)
+                        for (int bj = bj0; bj <= -bj0; bj++)
+                            for (int bi = -1; bi <= 1; bi++) nt += nu[EI(ek + bk, ej + bj, ei + bi)];
+                    w = 1.0 + 1.0 / (1.0 + nt);
+                }
+                if (p->sponge_width > 0.0) w = 1.0 + (w - 1.0) * (1.0 - sponge_sigma(p, node_x(p, ei - G)));
+                om[EI(ek, ej, ei)] = w;
             }
-            if (p->sponge_width > 0.0) w = 1.0 + (w - 1.0) * (1.0 - sponge_sigma(p, node_x(p, ei - G)));
-            om[E1(ej, ei)] = w;
-        }
 
     /* 6. collision with the first half of the source on the same nodes */
-#pragma omp parallel for
-    for (int ej = jlo; ej < jhi; ej++)
-        for (int ei = 2; ei < ex - 2; ei++) {
-            double Ui[MAXM], feq[5 * MAXM], S[MAXM];
-            for (int c = 0; c < m; c++) Ui[c] = Ue[EU(c, ej, ei)];
-            orc_equilibrium(p, Ui, alpha, lam, feq);
-            orc_source(p, Ui, posx[ei], posy[ej], S);
-            double w = om[E1(ej, ei)];
-            for (int k = 0; k < Q; k++)
-                for (int c = 0; c < m; c++) {
-                    double fk = fe[EF(k, c, ej, ei)];
-                    post[EF(k, c, ej, ei)] = fk - w * (fk - feq[k * m + c]) + 0.5 * dt * a[k] * S[c];
-                }
-        }
+#pragma omp parallel for collapse(2)
+    for (int ek = in2[2][0]; ek < in2[2][1]; ek++)
+        for (int ej = in2[1][0]; ej < in2[1][1]; ej++)
+            for (int ei = in2[0][0]; ei < in2[0][1]; ei++) {
+                const size_t e = EI(ek, ej, ei);
+                double Ui[MAXM], feq[7 * MAXM], S[MAXM];
+                for (int c = 0; c < m; c++) Ui[c] = Ue[EU(c, e)];
+                orc_equilibrium(p, Ui, alpha, lam, feq);
+                orc_source(p, Ui, posx[ei], posy[ej], S);
+                double w = om[e];
+                for (int k = 0; k < Q; k++)
+                    for (int c = 0; c < m; c++) {
+                        double fk = fe[EF(k, c, e)];
+                        post[EF(k, c, e)] = fk - w * (fk - feq[k * m + c]) + 0.5 * dt * a[k] * S[c];
+                    }
+            }
 
     /* 7-8. pull streaming, implicit moment (2.8), second half of the source */
-#pragma omp parallel for reduction(| : flags)
-    for (int j = 0; j < ny; j++)
-        for (int i = 0; i < nx; i++) {
-            int ej = j + gy, ei = i + G;
-            double Fk[5 * MAXM], Ubar[MAXM], Un[MAXM], S[MAXM];
-            for (int k = 0; k < Q; k++) {
-                /* e_0 = 0, e_j = unit vector j, e_{j+d} = -e_j (Section 2.3) */
-                int ex_k = 0, ey_k = 0;
-                if (k >= 1 && k <= d) { if (k == 1) ex_k = 1; else ey_k = 1; }
-                if (k > d) { if (k - d == 1) ex_k = -1; else ey_k = -1; }
-                for (int c = 0; c < m; c++) Fk[k * m + c] = post[EF(k, c, ej - ey_k, ei - ex_k)];
+#pragma omp parallel for collapse(2) reduction(| : flags)
+    for (int kk = 0; kk < nz; kk++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                const size_t e = EI(kk + gz, j + gy, i + G);
+                double Fk[7 * MAXM], Ubar[MAXM], Un[MAXM], S[MAXM];
+                for (int k = 0; k < Q; k++) {
+                    /* e_0 = 0, e_j = unit vector j, e_{j+d} = -e_j (Section 2.3) */
+                    size_t src = e;
+                    if (k >= 1 && k <= d) src = e - stride[k - 1];
+                    if (k > d) src = e + stride[k - d - 1];
+                    for (int c = 0; c < m; c++) Fk[k * m + c] = post[EF(k, c, src)];
+                }
+                for (int c = 0; c < m; c++) {
+                    double sum = 0.0;
+                    for (int k = 0; k < Q; k++) sum += Fk[k * m + c];
+                    Ubar[c] = sum;
+                }
+                double xn = node_x(p, i), yn = node_y(p, j);
+                flags |= solve_implicit_moment(p, Ubar, xn, yn, dt, Un);
+                orc_source(p, Un, xn, yn, S);
+                for (int k = 0; k < Q; k++)
+                    for (int c = 0; c < m; c++)
+                        fn[FI(k, c, kk, j, i)] = Fk[k * m + c] + 0.5 * dt * a[k] * S[c];
+                if (nonphysical(p, Un)) flags |= ORC_FLAG_NONPHYSICAL;
+                if (omega_out) omega_out[((size_t)kk * ny + j) * nx + i] = om[e];
             }
-            for (int c = 0; c < m; c++) {
-                double s = 0.0;
-                for (int k = 0; k < Q; k++) s += Fk[k * m + c];
-                Ubar[c] = s;
-            }
-            double xn = node_x(p, i), yn = node_y(p, j);
-            flags |= solve_implicit_moment(p, Ubar, xn, yn, dt, Un);
-            orc_source(p, Un, xn, yn, S);
-            for (int k = 0; k < Q; k++)
-                for (int c = 0; c < m; c++)
-                    fn[FIDX(k, c, j, i)] = Fk[k * m + c] + 0.5 * dt * a[k] * S[c];
-            if (nonphysical(p, Un)) flags |= ORC_FLAG_NONPHYSICAL;
-            if (omega_out) omega_out[(size_t)j * nx + i] = om[E1(ej, ei)];
-        }
 
     if (info) {
         info[0] = abar[0];
         info[1] = abar[1];
         info[2] = dt;
         info[3] = lam;
+        if (d == 3) info[4] = abar[2];
     }
-    free(fe); free(Ue); free(nu); free(om); free(post); free(srcj); free(srci); free(posx); free(posy);
+    free(fe); free(Ue); free(nu); free(om); free(post); free(srci); free(srcj); free(srck);
+    free(posx); free(posy);
     return flags;
-#undef E1
+#undef EI
 #undef EF
 #undef EU
+#undef FI
 }
 
 /*
@@ -862,12 +907,12 @@ int orc_step(const orc_problem *p, const double *f, double *fn, double dt_cap, c
 int orc_advance(const orc_problem *p, double *f, double *t, double T, long nsteps_max, long *nsteps) {
     if (check_problem(p)) return ORC_ERR_ARG;
     int m = orc_nfields(p), Q = nq(p);
-    size_t n = (size_t)Q * m * p->nx * ny_of(p);
+    size_t n = (size_t)Q * m * p->nx * rows_of(p);
     double *g = malloc(sizeof(double) * n);
     if (!g) return ORC_ERR_MEM;
     int flags = 0;
     long s = 0;
-    double info[4];
+    double info[5];
     while (s < nsteps_max && (T <= 0.0 || *t < T)) {
         double cap = T > 0.0 ? T - *t : 0.0;
         int r = orc_step(p, f, g, cap, NULL, info, NULL);

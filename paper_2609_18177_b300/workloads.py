@@ -48,6 +48,10 @@ class Problem:
     omega_mode: int = 0           # 0: adaptive (2.12)/(2.16); 1: fixed omega_fixed
     omega_fixed: float = 1.0
     h_dry: float = 1e-5           # depth below which a node is dry (u = v = 0)
+    nz: int = 1                   # 3D (D3Q7): nodes, extent and boundaries in z
+    z0: float = 0.0
+    z1: float = 1.0
+    bc_z: Tuple[int, int] = (PERIODIC, PERIODIC)
     sponge_width: float = 0.0     # > 0: sponge layer of this width at x-lo (omega blended toward 1)
     u_in: Tuple[float, ...] = ()  # conservative state held by inflow ghost nodes
     precision: int = 0            # 0: FP64, 1: FP32 distributions (CUDA path only)
@@ -74,13 +78,25 @@ class Problem:
 
     @property
     def nodes(self) -> int:
-        return self.nx * (self.ny if self.dim == 2 else 1)
+        return self.nx * (self.ny if self.dim >= 2 else 1) * (self.nz if self.dim == 3 else 1)
 
     def shape(self):
+        if self.dim == 3:
+            return (self.nz, self.ny, self.nx)
         return (self.ny, self.nx) if self.dim == 2 else (1, self.nx)
 
     def with_(self, **kw) -> "Problem":
         return replace(self, **kw)
+
+
+def cell_centres_3d(pb: Problem):
+    """X, Y, Z node coordinates of a 3D lattice, shape (nz, ny, nx)."""
+    h = pb.dx
+    x = pb.x0 + (np.arange(pb.nx) + 0.5) * h
+    y = pb.y0 + (np.arange(pb.ny) + 0.5) * h
+    z = pb.z0 + (np.arange(pb.nz) + 0.5) * h
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return X, Y, Z
 
 
 def cell_centres(pb: Problem):
@@ -97,16 +113,19 @@ def cell_centres(pb: Problem):
 # primitive -> conservative (the definitions of U in Section 5)
 # --------------------------------------------------------------------------
 
-def euler_conservative(pb, rho, u, p, v=None, Y=None):
+def euler_conservative(pb, rho, u, p, v=None, Y=None, w=None):
     rho = np.asarray(rho, dtype=np.float64)
     shp = rho.shape
     u = np.broadcast_to(np.asarray(u, dtype=np.float64), shp)
     p = np.broadcast_to(np.asarray(p, dtype=np.float64), shp)
     v = np.zeros(shp) if v is None else np.broadcast_to(np.asarray(v, dtype=np.float64), shp)
+    w = np.zeros(shp) if w is None else np.broadcast_to(np.asarray(w, dtype=np.float64), shp)
     comps = [rho, rho * u]
-    if pb.dim == 2:
+    if pb.dim >= 2:
         comps.append(rho * v)
-    E = p / (pb.gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+    if pb.dim == 3:
+        comps.append(rho * w)
+    E = p / (pb.gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
     if pb.system == REACTIVE:
         Yv = np.broadcast_to(np.asarray(Y, dtype=np.float64), shp)
         E = E + rho * pb.q * Yv
@@ -419,6 +438,8 @@ def acoustics_random(n, dim=1, a=1.0, cfl=0.9, seed=0, eps=1e-10):
 def random_state(pb: Problem, seed=0, smooth=False):
     """Seeded physical state of any system: a smooth field plus (unless smooth)
     a few jumps, with positive density/pressure/depth."""
+    if pb.dim == 3:
+        return random_state_3d(pb, seed, smooth)
     rng = np.random.default_rng(seed)
     X, Y = cell_centres(pb)
     Lx = pb.x1 - pb.x0
@@ -447,3 +468,35 @@ def random_state(pb: Problem, seed=0, smooth=False):
     p = field_(0.5, 2.0)
     Yf = field_(0.0, 1.0) if pb.system == REACTIVE else None
     return euler_conservative(pb, rho, u, p, v=v, Y=Yf)
+
+
+def random_state_3d(pb: Problem, seed=0, smooth=False):
+    """random_state on a 3D lattice (advection, Euler, reactive Euler)."""
+    rng = np.random.default_rng(seed)
+    X, Yc, Z = cell_centres_3d(pb)
+    xs = (X - pb.x0) / (pb.x1 - pb.x0)
+    ys = (Yc - pb.y0) / (pb.y1 - pb.y0)
+    zs = (Z - pb.z0) / (pb.z1 - pb.z0)
+
+    def field_(lo, hi):
+        k = rng.integers(1, 4, 3)
+        ph = rng.uniform(0, 2 * np.pi, 3)
+        base = 0.5 + (np.sin(2 * np.pi * k[0] * xs + ph[0]) + np.cos(2 * np.pi * k[1] * ys + ph[1])
+                      + np.sin(2 * np.pi * k[2] * zs + ph[2])) / 6.0
+        if not smooth:
+            cut = rng.uniform(0.3, 0.7)
+            base = np.where(xs + 0.3 * ys + 0.2 * zs > cut, base, 0.6 * base + 0.4 * rng.uniform())
+        return lo + (hi - lo) * base
+
+    if pb.system == ADVECTION:
+        return field_(-1.0, 1.0)[None]
+    rho = field_(0.5, 2.0)
+    u, v, w = field_(-0.8, 0.8), field_(-0.8, 0.8), field_(-0.8, 0.8)
+    p = field_(0.5, 2.0)
+    Yf = field_(0.0, 1.0) if pb.system == REACTIVE else None
+    return euler_conservative(pb, rho, u, p, v=v, Y=Yf, w=w)
+
+
+def cube(system, n, **kw):
+    """A 3D (D3Q7) problem on [0,1]^3 with n^3 nodes."""
+    return Problem(system=system, dim=3, nx=n, ny=n, nz=n, **kw)

@@ -27,13 +27,14 @@ GAMMA = 1.4
 
 def systems_1d_2d():
     out = []
-    for dim in (1, 2):
+    for dim in (1, 2, 3):
         n = 8
-        out.append(W.Problem(system=W.EULER, dim=dim, nx=n, ny=n))
-        out.append(W.Problem(system=W.SWE, dim=dim, nx=n, ny=n))
-        out.append(W.Problem(system=W.REACTIVE, dim=dim, nx=n, ny=n, gamma=1.2, q=50.0,
+        out.append(W.Problem(system=W.EULER, dim=dim, nx=n, ny=n, nz=n))
+        if dim < 3:
+            out.append(W.Problem(system=W.SWE, dim=dim, nx=n, ny=n))
+        out.append(W.Problem(system=W.REACTIVE, dim=dim, nx=n, ny=n, nz=n, gamma=1.2, q=50.0,
                              K=2566.4, Ti=50.0))
-        out.append(W.Problem(system=W.ADVECTION, dim=dim, nx=n, ny=n, adv=(0.7, -0.4)))
+        out.append(W.Problem(system=W.ADVECTION, dim=dim, nx=n, ny=n, nz=n, adv=(0.7, -0.4, 0.3)))
     return out
 
 
@@ -46,7 +47,7 @@ def random_U(pb, rng):
         vel = rng.uniform(-1, 1, d)
         return np.concatenate([[h], h * vel])
     rho = rng.uniform(0.5, 2.0)
-    vel = rng.uniform(-1, 1, 2)[:d]
+    vel = rng.uniform(-1, 1, 3)[:d]
     p = rng.uniform(0.5, 2.0)
     Y = rng.uniform(0.1, 0.9)
     kin = 0.5 * rho * np.sum(vel ** 2)
@@ -169,10 +170,10 @@ def fv_speed(pb, U):
 
 def shift(pb, A, j, s):
     """A evaluated at index i + s along axis j (j=0: x), ghost values per BC."""
-    axis = 2 if j == 0 else 1
+    axis = A.ndim - 1 - j
     n = A.shape[axis]
     idx = np.arange(n) + s
-    periodic = pb.bc[0 if j == 0 else 2] == W.PERIODIC
+    periodic = (pb.bc[0] if j == 0 else pb.bc[2] if j == 1 else pb.bc_z[0]) == W.PERIODIC
     idx = idx % n if periodic else np.clip(idx, 0, n - 1)
     return np.take(A, idx, axis=axis)
 
@@ -195,6 +196,9 @@ LF_CASES = [
     ("euler2d_periodic", lambda: (W.Problem(system=W.EULER, dim=2, nx=20, ny=20),)),
     ("swe2d_outflow", lambda: (W.Problem(system=W.SWE, dim=2, nx=18, ny=18, bc=(W.OUTFLOW,) * 4),)),
     ("advection1d", lambda: W.advection_1d(50, "pulse")),
+    ("euler3d_periodic", lambda: (W.cube(W.EULER, 10),)),
+    ("advection3d_outflow", lambda: (W.cube(W.ADVECTION, 9, adv=(0.6, -0.4, 0.5), bc=(W.OUTFLOW,) * 4,
+                                              bc_z=(W.OUTFLOW, W.OUTFLOW)),)),
 ]
 
 
@@ -461,3 +465,67 @@ def test_cellular_detonation_initial_data():
     assert np.all(Yf[~ahead] < 1.0) and np.all(Yf >= 0.0)
     strip = (X >= 29.0) & (X <= 30.0)
     assert np.abs(U0[2][strip]).max() > 0 and np.all(U0[2][~strip] == 0.0)
+
+
+
+# ---------------------------------------------------------------------------
+# 3D (D3Q7)
+# ---------------------------------------------------------------------------
+
+def test_uniform_reactive_state_is_trapezoidal_rule_3d():
+    pb = W.cube(W.REACTIVE, 4, gamma=1.2, q=50.0, Ti=20.0, K=30.0, cfl=0.9)
+    rho, p, Y = 1.0, 12.0, 0.9
+    U0 = W.euler_conservative(pb, np.full((4, 4, 4), rho), 0.0, p, v=0.0, w=0.0, Y=Y)
+    r = oracle.Run(pb, U0)
+    z, E = rho * Y, U0[4, 0, 0, 0]
+
+    def rate(zz):
+        T = (pb.gamma - 1) * (E - pb.q * zz) / rho / rho
+        return pb.K * zz * math.exp(-pb.Ti / T)
+
+    for _ in range(10):
+        r.step(1)
+        dt = r.info[2]
+        rhs = z - 0.5 * dt * rate(z)
+        z = brentq(lambda zz: zz + 0.5 * dt * rate(zz) - rhs, 0.0, z, xtol=1e-16, rtol=1e-15)
+        U = r.moments()
+        assert np.allclose(U[5], z, rtol=1e-13, atol=0)
+        assert np.allclose(U[1:4], 0.0, atol=1e-14)
+    assert z < 0.9 * rho * Y
+
+
+@pytest.mark.parametrize("system", [W.EULER, W.ADVECTION, W.REACTIVE])
+def test_periodic_conservation_3d(system):
+    kw = dict(gamma=1.2, q=5.0, K=0.0) if system == W.REACTIVE else {}
+    pb = W.cube(system, 10, adv=(0.6, -0.3, 0.45), cfl=0.9, **kw)
+    U0 = W.random_state(pb, seed=5)
+    r = oracle.Run(pb, U0)
+    tot0 = U0.reshape(pb.nfields, -1).sum(axis=1)
+    r.step(15)
+    assert r.flags == 0
+    tot = r.moments().reshape(pb.nfields, -1).sum(axis=1)
+    scale = np.abs(U0).reshape(pb.nfields, -1).sum(axis=1)
+    assert np.all(np.abs(tot - tot0) <= 1e-13 * scale), (tot - tot0) / scale
+
+
+@pytest.mark.parametrize("system", [W.EULER, W.REACTIVE])
+def test_axes_are_interchangeable_3d(system):
+    """Cycling the axes (x, y, z) -> (y, z, x) of the data and of the velocity
+    components cycles the solution: every direction is treated alike (a wrong
+    stride, index or eigenvector along one axis would break this)."""
+    kw = dict(gamma=1.2, q=5.0, K=40.0, Ti=2.0) if system == W.REACTIVE else {}
+    pb = W.Problem(system=system, dim=3, nx=9, ny=9, nz=9, bc=(W.OUTFLOW,) * 4, bc_z=(W.OUTFLOW, W.OUTFLOW),
+                   cfl=0.8, **kw)
+    U0 = W.random_state(pb, seed=17)
+
+    def cycle(U):
+        # new (x, y, z) = old (y, z, x): array axes (z, y, x) -> (x, z, y); momenta follow
+        V = np.transpose(U, (0, 3, 1, 2)).copy()
+        V[[1, 2, 3]] = V[[2, 3, 1]]
+        return V
+
+    a = oracle.Run(pb, U0).step(8)
+    b = oracle.Run(pb, cycle(U0)).step(8)
+    Ua, Ub = cycle(a.moments()), b.moments()
+    scale = np.abs(Ub).reshape(pb.nfields, -1).max(axis=1)
+    assert np.all(np.abs(Ua - Ub).reshape(pb.nfields, -1).max(axis=1) <= 1e-12 * scale)
