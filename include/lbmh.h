@@ -95,7 +95,7 @@ typedef enum { LBMH_KERNEL_AUTO = 0, LBMH_KERNEL_FUSED = 1, LBMH_KERNEL_UNFUSED 
  * uses 1e-10), omega from (2.16) unless omega_mode is FIXED. */
 typedef struct lbmh_problem {
   int system;          /* lbmh_system */
-  int dim;             /* 1 or 2; the lattice is DdQ(2d+1) */
+  int dim;             /* 1, 2 or 3; the lattice is DdQ(2d+1) */
   int nx, ny;          /* nodes per direction (ny ignored in 1D) */
   double x0, x1, y0, y1; /* domain; 2D requires (x1-x0)/nx == (y1-y0)/ny */
   int bc[4];           /* lbmh_bc at x-lo, x-hi, y-lo, y-hi; periodic must pair */
@@ -116,6 +116,14 @@ typedef struct lbmh_problem {
                           blended toward 1, omega' = 1 + (omega - 1)(1 - sigma(x)),
                           sigma = (1 + cos(pi (x - x0) / sponge_width)) / 2; 0: none */
   double u_in[8];      /* conservative state (first m entries) held by INFLOW sides */
+  /* 3D (dim = 3, the D3Q7 lattice; the paper names 3D as future work):
+   * advection, Euler and reactive Euler, periodic or outflow sides, the
+   * four-kernel path (KERNEL_AUTO); dx == dy == dz required.  U and f are
+   * laid out [..][nz][ny][nx]. */
+  int nz;
+  double z0, z1;
+  int bc_z[2];         /* lbmh_bc at z-lo, z-hi */
+  double adv_z;        /* advection velocity along z */
 } lbmh_problem;
 
 typedef struct lbmh_handle lbmh_handle;

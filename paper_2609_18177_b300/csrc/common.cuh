@@ -34,6 +34,7 @@ struct PhysConstF {
   float gamma, gm1, g, half_g, h_dry, cmin, q, adv0, adv1, dx;
   float bed_amp, bed_inv_w2, bed_m2_inv_w2, xb, yb, K, Ti;
   float omega_fixed;
+  float adv2;  // advection speed along z (3D)
   float sponge_dx_over_w;
   float u_in[8];
 };
@@ -59,6 +60,11 @@ struct DevParams {
   double sponge_dx_over_w;  // dx / sponge_width
   double u_in[8];           // conservative state of INFLOW ghost nodes
   int has_special_bc;       // some side is REFLECT or INFLOW
+  // 3D (D3Q7): ny above counts rows = ny3 * nz3 (z outer), so the row-wise
+  // kernels (moments, checkpoints) serve 3D lattices unchanged
+  int ny3, nz3;
+  int bc_z[2];
+  double z0, adv_z;
   PhysConstF pf;
 };
 
@@ -76,6 +82,8 @@ struct Ctl {
   double ainit[2];                // speed bound of the initial state U0
   unsigned int status;            // LBMH status bits, sticky
   unsigned int pad2;
+  unsigned long long amax_z[3];  // 3D: speed bound along z per slot (bit pattern)
+  double ainit_z;
 };
 
 // status bits: NONPHYSICAL (NaN/inf, rho <= 0 or p <= 0) fails lbmh_moments;

@@ -34,9 +34,21 @@ inline int validate(const lbmh_problem* p, std::string& why) {
   if (!p) { why = "problem is NULL"; return LBMH_ERR_INVALID_ARG; }
   if (p->system == LBMH_LINEAR) { why = "LBMH_LINEAR is provided by the oracle only"; return LBMH_ERR_UNSUPPORTED; }
   if (p->system < 0 || p->system > 3) { why = "unknown system"; return LBMH_ERR_INVALID_ARG; }
-  if (p->dim != 1 && p->dim != 2) { why = "dim must be 1 or 2"; return LBMH_ERR_INVALID_ARG; }
-  if (p->nx < 1 || (p->dim == 2 && p->ny < 1)) { why = "grid must have at least one node"; return LBMH_ERR_INVALID_ARG; }
-  if ((long long)p->nx * (p->dim == 2 ? p->ny : 1) > (1ll << 34)) { why = "grid too large"; return LBMH_ERR_INVALID_ARG; }
+  if (p->dim < 1 || p->dim > 3) { why = "dim must be 1, 2 or 3"; return LBMH_ERR_INVALID_ARG; }
+  if (p->nx < 1 || (p->dim >= 2 && p->ny < 1) || (p->dim == 3 && p->nz < 1)) { why = "grid must have at least one node"; return LBMH_ERR_INVALID_ARG; }
+  if ((long long)p->nx * (p->dim >= 2 ? p->ny : 1) * (p->dim == 3 ? p->nz : 1) > (1ll << 34)) { why = "grid too large"; return LBMH_ERR_INVALID_ARG; }
+  if (p->dim == 3) {
+    if (p->system == LBMH_SWE) { why = "3D lattices: advection, Euler and reactive Euler"; return LBMH_ERR_UNSUPPORTED; }
+    for (int s = 0; s < 4; s++)
+      if (p->bc[s] != LBMH_BC_PERIODIC && p->bc[s] != LBMH_BC_OUTFLOW) { why = "3D lattices: periodic or outflow sides"; return LBMH_ERR_UNSUPPORTED; }
+    for (int s = 0; s < 2; s++)
+      if (p->bc_z[s] != LBMH_BC_PERIODIC && p->bc_z[s] != LBMH_BC_OUTFLOW) { why = "3D lattices: periodic or outflow sides"; return LBMH_ERR_UNSUPPORTED; }
+    if ((p->bc_z[0] == LBMH_BC_PERIODIC) != (p->bc_z[1] == LBMH_BC_PERIODIC)) { why = "periodic z boundaries must pair"; return LBMH_ERR_INVALID_ARG; }
+    double dx = (p->x1 - p->x0) / p->nx, dz = (p->z1 - p->z0) / p->nz;
+    if (!(fabs(dx - dz) <= 1e-12 * dx)) { why = "3D mesh must satisfy dx == dy == dz"; return LBMH_ERR_INVALID_ARG; }
+    if (p->sponge_width != 0.0) { why = "no sponge on 3D lattices"; return LBMH_ERR_UNSUPPORTED; }
+    if (p->kernel == LBMH_KERNEL_FUSED) { why = "3D lattices run on the four-kernel path"; return LBMH_ERR_UNSUPPORTED; }
+  }
   if (!(p->x1 > p->x0)) { why = "x1 must exceed x0"; return LBMH_ERR_INVALID_ARG; }
   for (int s = 0; s < 2 * p->dim; s++)
     if (p->bc[s] < LBMH_BC_PERIODIC || p->bc[s] > LBMH_BC_INFLOW) { why = "bad boundary condition"; return LBMH_ERR_INVALID_ARG; }
@@ -60,7 +72,7 @@ inline int validate(const lbmh_problem* p, std::string& why) {
       if (!ok) { why = "u_in must be a finite physical state for an inflow side"; return LBMH_ERR_INVALID_ARG; }
     }
   if ((p->bc[0] == LBMH_BC_PERIODIC) != (p->bc[1] == LBMH_BC_PERIODIC)) { why = "periodic x boundaries must pair"; return LBMH_ERR_INVALID_ARG; }
-  if (p->dim == 2) {
+  if (p->dim >= 2) {
     if ((p->bc[2] == LBMH_BC_PERIODIC) != (p->bc[3] == LBMH_BC_PERIODIC)) { why = "periodic y boundaries must pair"; return LBMH_ERR_INVALID_ARG; }
     double dx = (p->x1 - p->x0) / p->nx, dy = (p->y1 - p->y0) / p->ny;
     if (!(fabs(dx - dy) <= 1e-12 * dx)) { why = "2D mesh must satisfy dx == dy (Section 2.2.2)"; return LBMH_ERR_INVALID_ARG; }
@@ -81,13 +93,19 @@ inline DevParams make_devparams(const lbmh_problem* p, int pitch) {
   DevParams P;
   memset(&P, 0, sizeof P);
   P.nx = p->nx;
-  P.ny = p->dim == 2 ? p->ny : 1;
+  P.ny3 = p->dim >= 2 ? p->ny : 1;
+  P.nz3 = p->dim == 3 ? p->nz : 1;
+  P.ny = P.ny3 * P.nz3;  // rows (z outer) in 3D
   P.pitch = pitch;
   P.plane = (long long)P.ny * P.pitch;
   for (int s = 0; s < 4; s++) P.bc[s] = p->bc[s];
   if (p->dim == 1) P.bc[2] = P.bc[3] = LBMH_BC_PERIODIC;
+  P.bc_z[0] = p->dim == 3 ? p->bc_z[0] : LBMH_BC_PERIODIC;
+  P.bc_z[1] = p->dim == 3 ? p->bc_z[1] : LBMH_BC_PERIODIC;
   P.x0 = p->x0;
-  P.y0 = p->dim == 2 ? p->y0 : 0.0;
+  P.y0 = p->dim >= 2 ? p->y0 : 0.0;
+  P.z0 = p->dim == 3 ? p->z0 : 0.0;
+  P.adv_z = p->dim == 3 ? p->adv_z : 0.0;
   P.dx = (p->x1 - p->x0) / p->nx;
   P.cfl = p->cfl;
   P.eps = p->eps;
@@ -133,6 +151,7 @@ inline DevParams make_devparams(const lbmh_problem* p, int pitch) {
   f.K = (float)P.K;
   f.Ti = (float)P.Ti;
   f.omega_fixed = (float)P.omega_fixed;
+  f.adv2 = (float)P.adv_z;
   f.sponge_dx_over_w = (float)P.sponge_dx_over_w;
   for (int c = 0; c < 8; c++) f.u_in[c] = (float)P.u_in[c];
   return P;

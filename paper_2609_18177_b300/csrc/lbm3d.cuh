@@ -1,0 +1,542 @@
+// 3D lattice (D3Q7): scalar advection, Euler and reactive Euler.
+//
+// The method of Section 2 in three dimensions (the DdQ(2d+1) lattice of
+// Section 2.3 with d = 3; the paper names 3D detonations as future work):
+// velocities e_0 = 0, e_j = unit vector j, e_{j+3} = -e_j; speed bounds,
+// alpha_j and the step control of Eqs. 2.19/2.21 over three directions; the
+// indicator (2.13)/(2.14) summed over three directions and smoothed over the
+// 3^3 box (2.15); collision, pull streaming and the implicit moment as in 2D.
+//
+// Implementation: four kernels over a ghost-extended copy of U (3 ghost
+// layers per side, periodic or outflow), the 3D counterpart of the unfused
+// 2D path: K0 moments, K1 indicator, K2 omega, K3 collision + streaming +
+// implicit moment + side outputs.  Distributions use the row layout of the
+// 2D path with rows = z * ny + y, so the row-wise kernels (moments,
+// checkpoints) serve 3D lattices unchanged.
+#pragma once
+#include "common.cuh"
+#include "physics.cuh"
+#include "unfused.cuh"
+
+namespace lbmh {
+
+// primitive variables of a 3D Euler-type state
+template <class R>
+struct Prim3 {
+  R rho, u, v, w, p, c, Y;
+};
+
+template <int SYS>
+struct Fields3 {
+  static constexpr int M = SYS == SYS_ADV ? 1 : (SYS == SYS_EULER ? 5 : 6);
+  static constexpr int Q = 7;
+};
+
+template <int SYS, class R>
+__device__ __forceinline__ Prim3<R> prim3(const Phys<R>& K, const R* U) {
+  Prim3<R> w;
+  w.rho = w.u = w.v = w.w = w.p = w.c = w.Y = R(0);
+  if constexpr (SYS != SYS_ADV) {
+    w.rho = U[0];
+    const R inv = frcp(w.rho);
+    w.u = U[1] * inv;
+    w.v = U[2] * inv;
+    w.w = U[3] * inv;
+    const R kin = R(0.5) * w.rho * (w.u * w.u + w.v * w.v + w.w * w.w);
+    R chem = R(0);
+    if constexpr (SYS == SYS_REACT) {
+      w.Y = U[5] * inv;
+      chem = K.q * U[5];
+    }
+    w.p = K.gm1 * (U[4] - kin - chem);
+    w.c = fsqrt(K.gamma * w.p * inv);
+  }
+  return w;
+}
+
+template <class R>
+__device__ __forceinline__ R adv3(const Phys<R>& K, const DevParams& P, int dir) {
+  if (dir == 0) return K.adv0;
+  if (dir == 1) return K.adv1;
+  if constexpr (sizeof(R) == 4)
+    return P.pf.adv2;
+  else
+    return P.adv_z;
+}
+
+template <int SYS, class R>
+__device__ __forceinline__ void flux3(const Phys<R>& K, const DevParams& P, const R* U, const Prim3<R>& w, int dir,
+                                      R* F) {
+  if constexpr (SYS == SYS_ADV) {
+    F[0] = adv3<R>(K, P, dir) * U[0];
+  } else {
+    const R vel[3] = {w.u, w.v, w.w};
+    const R vn = vel[dir];
+    F[0] = w.rho * vn;
+#pragma unroll
+    for (int t = 0; t < 3; t++) F[1 + t] = U[1 + t] * vn + (dir == t ? w.p : R(0));
+    F[4] = vn * (U[4] + w.p);
+    if constexpr (SYS == SYS_REACT) F[5] = U[5] * vn;
+  }
+}
+
+template <int SYS, class R>
+__device__ __forceinline__ R speed3(const Phys<R>& K, const DevParams& P, const Prim3<R>& w, int dir) {
+  if constexpr (SYS == SYS_ADV) {
+    return rabs(adv3<R>(K, P, dir));
+  } else {
+    const R vel[3] = {w.u, w.v, w.w};
+    return rabs(vel[dir]) + w.c;
+  }
+}
+
+// Sum over the characteristic fields of theta^{(r,j)} (Eq. 2.13) along dir:
+// closed-form L_j for the Toro-normalised right eigenvectors (acoustic
+// (1, u -+ c e_j, H -+ u_j c[, Y]), entropy (1, u, |u|^2/2 [+ qY][, Y]), two
+// shear waves (unit tangential velocity), species (0, 0, q, 1)).
+template <int SYS, class R>
+__device__ __forceinline__ R theta3(const Phys<R>& K, const Prim3<R>& w, int dir, const R* dm, const R* dp) {
+  constexpr int M = Fields3<SYS>::M;
+  R wm[M], wp[M];
+  if constexpr (SYS == SYS_ADV) {
+    wm[0] = dm[0];
+    wp[0] = dp[0];
+  } else {
+    const R c = w.c;
+    const R inv_c2 = frcp(c * c);
+    const R vel[3] = {w.u, w.v, w.w};
+    const R q2 = R(0.5) * (w.u * w.u + w.v * w.v + w.w * w.w);
+    const R un = vel[dir];
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      const R* dU = s == 0 ? dm : dp;
+      R* out = s == 0 ? wm : wp;
+      R chem = R(0);
+      if constexpr (SYS == SYS_REACT) chem = K.q * dU[5];
+      const R dpres = K.gm1 * (dU[4] - w.u * dU[1] - w.v * dU[2] - w.w * dU[3] + q2 * dU[0] - chem);
+      const R rdun = dU[1 + dir] - un * dU[0];  // rho d(u_n)
+      out[0] = R(0.5) * (dpres - c * rdun) * inv_c2;
+      out[1] = dU[0] - dpres * inv_c2;
+      int r = 2;
+#pragma unroll
+      for (int t = 0; t < 3; t++)
+        if (t != dir) out[r++] = dU[1 + t] - vel[t] * dU[0];  // rho d(u_t)
+      if constexpr (SYS == SYS_REACT) out[r++] = dU[5] - w.Y * dU[0];  // rho dY
+      out[M - 1] = R(0.5) * (dpres + c * rdun) * inv_c2;
+    }
+  }
+  R nu = R(0);
+#pragma unroll
+  for (int r = 0; r < M; r++) {
+    const R am = rabs(wm[r]), ap = rabs(wp[r]);
+    nu += fdiv(rabs(wp[r] - wm[r]), am + ap + K.dx) + am + ap;
+  }
+  return nu;
+}
+
+struct StepCoef3 {
+  double dt, lam, alpha[3], a0, aj[3];
+  int active;
+};
+
+__device__ __forceinline__ StepCoef3 step_coef3(const DevParams& P, const Ctl* ctl, int slot) {
+  StepCoef3 c;
+  const double ab[3] = {bits_to_double(ctl->amax[slot][0]), bits_to_double(ctl->amax[slot][1]),
+                        bits_to_double(ctl->amax_z[slot])};
+  const double t = ctl->t[slot];
+  c.active = !(P.T > 0.0 && t >= P.T) && !(P.max_steps > 0 && ctl->nsteps[slot] >= P.max_steps);
+  c.dt = P.cfl * P.dx / (ab[0] + ab[1] + ab[2]);
+  c.lam = P.dx / c.dt;
+  double alsum = 0.0;
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    c.alpha[j] = ab[j] + P.eps;
+    alsum += c.alpha[j];
+  }
+  c.a0 = 1.0 - alsum / c.lam;
+#pragma unroll
+  for (int j = 0; j < 3; j++) c.aj[j] = c.alpha[j] / (2.0 * c.lam);
+  return c;
+}
+
+__device__ __forceinline__ void advance_ctl3(Ctl* ctl, int slot, const StepCoef3& c) {
+  const int s1 = (slot + 1) % 3, s2 = (slot + 2) % 3;
+  if (c.active) {
+    ctl->t[s1] = ctl->t[slot] + c.dt;
+    ctl->nsteps[s1] = ctl->nsteps[slot] + 1;
+    ctl->parity[s1] = ctl->parity[slot] ^ 1;
+    ctl->last_dt = c.dt;
+    ctl->last_lambda = c.lam;
+  } else {
+    ctl->t[s1] = ctl->t[slot];
+    ctl->nsteps[s1] = ctl->nsteps[slot];
+    ctl->parity[s1] = ctl->parity[slot];
+    ctl->amax[s1][0] = ctl->amax[slot][0];
+    ctl->amax[s1][1] = ctl->amax[slot][1];
+    ctl->amax_z[s1] = ctl->amax_z[slot];
+  }
+  ctl->amax[s2][0] = ctl->amax[s2][1] = 0ull;
+  ctl->amax_z[s2] = 0ull;
+}
+
+// ghost-extended 3D geometry: ex x ey x ez nodes, 3 ghost layers per side
+struct ExtGeom3 {
+  int ex, ey, ez;
+  __device__ __forceinline__ long long idx(int ek, int ej, int ei) const {
+    return ((long long)ek * ey + ej) * ex + ei;
+  }
+};
+
+// offset of node (i, j, k) in a distribution plane (row = k * ny + j)
+__device__ __forceinline__ long long cell3(const DevParams& P, int i, int j, int k) {
+  return ((long long)k * P.ny3 + j) * P.pitch + i + XPAD;
+}
+
+__device__ __forceinline__ double nanmax3(double a, double b) { return (a > b || a != a) ? a : b; }
+
+// block maxima of three speeds into d0..d2 (one atomic per block and value)
+__device__ __forceinline__ void block_max3_to(double s0, double s1, double s2, unsigned long long* d0,
+                                              unsigned long long* d1, unsigned long long* d2) {
+  __shared__ double red[3][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 = nanmax3(s0, __shfl_xor_sync(0xffffffffu, s0, o));
+    s1 = nanmax3(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+    s2 = nanmax3(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+  }
+  __syncthreads();
+  if (lane == 0) {
+    red[0][w] = s0;
+    red[1][w] = s1;
+    red[2][w] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+    for (int i = 0; i < nw; i++) {
+      m0 = nanmax3(m0, red[0][i]);
+      m1 = nanmax3(m1, red[1][i]);
+      m2 = nanmax3(m2, red[2][i]);
+    }
+    atomic_max_nonneg(d0, m0);
+    atomic_max_nonneg(d1, m1);
+    atomic_max_nonneg(d2, m2);
+  }
+}
+
+// speed bound of the FP64 initial state -> ainit (Eq. 2.19)
+template <int SYS>
+__global__ void __launch_bounds__(kBlock) k3_init_speed(DevParams P, const double* U0, Ctl* ctl) {
+  constexpr int M = Fields3<SYS>::M;
+  const long long nn = (long long)P.nx * P.ny;
+  const Phys<double> K = make_phys<double>(P);
+  double s[3] = {0.0, 0.0, 0.0};
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < nn;
+       node += (long long)gridDim.x * blockDim.x) {
+    double U[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) U[c] = U0[c * nn + node];
+    const Prim3<double> w = prim3<SYS, double>(K, U);
+#pragma unroll
+    for (int d = 0; d < 3; d++) s[d] = nanmax3(s[d], speed3<SYS, double>(K, P, w, d));
+  }
+  block_max3_to(s[0], s[1], s[2], (unsigned long long*)&ctl->ainit[0], (unsigned long long*)&ctl->ainit[1],
+                (unsigned long long*)&ctl->ainit_z);
+}
+
+// f := f^eq(U0) with alpha^0, lambda^0 (Eq. 2.20); speed bound of the stored
+// state into slot 0
+template <int SYS, class R>
+__global__ void __launch_bounds__(kBlock) k3_init_eq(DevParams P, const double* U0, R* f, Ctl* ctl) {
+  constexpr int M = Fields3<SYS>::M;
+  const long long nn = (long long)P.nx * P.ny;
+  const double ab[3] = {ctl->ainit[0], ctl->ainit[1], ctl->ainit_z};
+  const double dt = P.cfl * P.dx / (ab[0] + ab[1] + ab[2]);
+  const double lam = P.dx / dt;
+  const double al[3] = {ab[0] + P.eps, ab[1] + P.eps, ab[2] + P.eps};
+  const R a0 = R(1.0 - (al[0] + al[1] + al[2]) / lam), inv2l = R(1.0 / (2.0 * lam));
+  const Phys<R> K = make_phys<R>(P);
+  double s[3] = {0.0, 0.0, 0.0};
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < nn;
+       node += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)(node / P.nx), i = (int)(node % P.nx);
+    const long long off = (long long)row * P.pitch + i + XPAD;
+    R U[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) U[c] = R(U0[c * nn + node]);
+    const Prim3<R> w = prim3<SYS, R>(K, U);
+#pragma unroll
+    for (int c = 0; c < M; c++) f[(long long)c * P.plane + off] = a0 * U[c];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      R F[M];
+      flux3<SYS, R>(K, P, U, w, d, F);
+#pragma unroll
+      for (int c = 0; c < M; c++) {
+        f[(long long)((1 + d) * M + c) * P.plane + off] = (R(al[d]) * U[c] + F[c]) * inv2l;
+        f[(long long)((4 + d) * M + c) * P.plane + off] = (R(al[d]) * U[c] - F[c]) * inv2l;
+      }
+    }
+    // moments of the stored distributions, summed k = 0..6 as a step does
+    R Us[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) {
+      R sum = R(0);
+#pragma unroll
+      for (int k = 0; k < 7; k++) sum += f[(long long)(k * M + c) * P.plane + off];
+      Us[c] = sum;
+    }
+    const Prim3<R> ws = prim3<SYS, R>(K, Us);
+#pragma unroll
+    for (int d = 0; d < 3; d++) s[d] = nanmax3(s[d], (double)speed3<SYS, R>(K, P, ws, d));
+  }
+  block_max3_to(s[0], s[1], s[2], &ctl->amax[0][0], &ctl->amax[0][1], &ctl->amax_z[0]);
+}
+
+// speed bound of the stored distributions -> slot 0 (after a checkpoint load)
+template <int SYS, class R>
+__global__ void __launch_bounds__(kBlock) k3_speed_of_f(DevParams P, R* const* buf, Ctl* ctl) {
+  constexpr int M = Fields3<SYS>::M;
+  const long long nn = (long long)P.nx * P.ny;
+  const Phys<R> K = make_phys<R>(P);
+  const R* f = buf[ctl->parity[0]];
+  double s[3] = {0.0, 0.0, 0.0};
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < nn;
+       node += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)(node / P.nx), i = (int)(node % P.nx);
+    const long long off = (long long)row * P.pitch + i + XPAD;
+    R U[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) {
+      R sum = R(0);
+#pragma unroll
+      for (int k = 0; k < 7; k++) sum += f[(long long)(k * M + c) * P.plane + off];
+      U[c] = sum;
+    }
+    const Prim3<R> w = prim3<SYS, R>(K, U);
+#pragma unroll
+    for (int d = 0; d < 3; d++) s[d] = nanmax3(s[d], (double)speed3<SYS, R>(K, P, w, d));
+  }
+  block_max3_to(s[0], s[1], s[2], &ctl->amax[0][0], &ctl->amax[0][1], &ctl->amax_z[0]);
+}
+
+__device__ __forceinline__ void ext_coords(const ExtGeom3& G, long long e, int& ei, int& ej, int& ek) {
+  ei = (int)(e % G.ex);
+  ej = (int)((e / G.ex) % G.ey);
+  ek = (int)(e / ((long long)G.ex * G.ey));
+}
+
+// K0: U = sum_k f_k on the ghost-extended grid (wrapped / clamped reads)
+template <int SYS, class R>
+__global__ void k3_moments_ext(DevParams P, R* const* buf, const Ctl* ctl, int slot, ExtGeom3 G, R* Ue) {
+  constexpr int M = Fields3<SYS>::M;
+  const long long n = (long long)G.ex * G.ey * G.ez;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  if (P.T > 0.0 && ctl->t[slot] >= P.T) return;
+  const R* f = buf[ctl->parity[slot]];
+  int ei, ej, ek;
+  ext_coords(G, e, ei, ej, ek);
+  const long long off = cell3(P, map_index(ei - GH, P.nx, P.bc[0], P.bc[1]), map_index(ej - GH, P.ny3, P.bc[2], P.bc[3]),
+                              map_index(ek - GH, P.nz3, P.bc_z[0], P.bc_z[1]));
+#pragma unroll
+  for (int c = 0; c < M; c++) {
+    R sum = R(0);
+#pragma unroll
+    for (int q = 0; q < 7; q++) sum += f[(long long)(q * M + c) * P.plane + off];
+    Ue[(long long)c * n + e] = sum;
+  }
+}
+
+// K1: nu = sum_j sum_r theta^{(r,j)} one layer inside the extension
+template <int SYS, class R>
+__global__ void k3_indicator(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, const R* Ue, R* nu) {
+  constexpr int M = Fields3<SYS>::M;
+  const long long n = (long long)G.ex * G.ey * G.ez;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  if (P.T > 0.0 && ctl->t[slot] >= P.T) return;
+  int ei, ej, ek;
+  ext_coords(G, e, ei, ej, ek);
+  if (ei < 1 || ei >= G.ex - 1 || ej < 1 || ej >= G.ey - 1 || ek < 1 || ek >= G.ez - 1) return;
+  const Phys<R> K = make_phys<R>(P);
+  const long long stride[3] = {1, G.ex, (long long)G.ex * G.ey};
+  R U0[M], dm[M], dp[M];
+#pragma unroll
+  for (int c = 0; c < M; c++) U0[c] = Ue[(long long)c * n + e];
+  const Prim3<R> w = prim3<SYS, R>(K, U0);
+  R sum = R(0);
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+#pragma unroll
+    for (int c = 0; c < M; c++) {
+      dm[c] = U0[c] - Ue[(long long)c * n + e - stride[d]];
+      dp[c] = Ue[(long long)c * n + e + stride[d]] - U0[c];
+    }
+    sum += theta3<SYS, R>(K, w, d, dm, dp);
+  }
+  nu[e] = sum;
+}
+
+// K2: omega = 1 + 1/(1 + nu~), nu~ the sum over the 3^3 box (Eq. 2.15, 2.16)
+template <class R>
+__global__ void k3_omega(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, const R* nu, R* om) {
+  const long long n = (long long)G.ex * G.ey * G.ez;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  if (P.T > 0.0 && ctl->t[slot] >= P.T) return;
+  int ei, ej, ek;
+  ext_coords(G, e, ei, ej, ek);
+  if (ei < 2 || ei >= G.ex - 2 || ej < 2 || ej >= G.ey - 2 || ek < 2 || ek >= G.ez - 2) return;
+  R w;
+  if (P.omega_mode == 1) {
+    if constexpr (sizeof(R) == 4)
+      w = P.pf.omega_fixed;
+    else
+      w = P.omega_fixed;
+  } else {
+    R s = R(0);
+    for (int bk = -1; bk <= 1; bk++)
+      for (int bj = -1; bj <= 1; bj++)
+        for (int bi = -1; bi <= 1; bi++) s += nu[e + ((long long)bk * G.ey + bj) * G.ex + bi];
+    w = R(1) + fdiv(R(1), R(1) + s);
+  }
+  om[e] = w;
+}
+
+// source of the 3D systems: Arrhenius on rho*Y (reactive, FP64), none otherwise
+template <int SYS, class R>
+__device__ __forceinline__ void source3(const Phys<R>& K, const R* U, R* S) {
+  constexpr int M = Fields3<SYS>::M;
+#pragma unroll
+  for (int c = 0; c < M; c++) S[c] = R(0);
+  if constexpr (SYS == SYS_REACT) {
+    if (K.react) {
+      const double momsq = (double)U[1] * U[1] + (double)U[2] * U[2] + (double)U[3] * U[3];
+      S[5] = R(-arrhenius(K, (double)U[0], momsq, (double)U[4], (double)U[5]));
+    }
+  }
+}
+
+// K3: collision with the first half-source at x - e_k (Eq. 2.2), pull
+// streaming, the implicit moment (2.8) in FP64 and the second half-source at
+// x; writes f^{n+1}; side outputs (three speed bounds, FP64 sums, status).
+template <int SYS, class R>
+__global__ void __launch_bounds__(kBlock) k3_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
+                                                            ExtGeom3 G, const R* Ue, const R* om, double* partials) {
+  constexpr int M = Fields3<SYS>::M, Q = 7;
+  constexpr bool SRC = SYS == SYS_REACT;
+  const StepCoef3 cf = step_coef3(P, ctl, slot);
+  if (!cf.active) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) advance_ctl3(ctl, slot, cf);
+    return;
+  }
+  const R* f = buf[ctl->parity[slot]];
+  R* fo = buf[ctl->parity[slot] ^ 1];
+  const long long nn = (long long)P.nx * P.ny;
+  const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n = (long long)G.ex * G.ey * G.ez;
+  double sp[3] = {0.0, 0.0, 0.0}, usum[M];
+#pragma unroll
+  for (int c = 0; c < M; c++) usum[c] = 0.0;
+  unsigned st = 0u;
+  if (node < nn) {
+    const Phys<R> K = make_phys<R>(P);
+    const R a0 = R(cf.a0), inv2l = R(1.0 / (2.0 * cf.lam)), hdt = R(0.5 * cf.dt);
+    const R al[3] = {R(cf.alpha[0]), R(cf.alpha[1]), R(cf.alpha[2])};
+    const R ak[7] = {a0, R(cf.aj[0]), R(cf.aj[1]), R(cf.aj[2]), R(cf.aj[0]), R(cf.aj[1]), R(cf.aj[2])};
+    const int i = (int)(node % P.nx), row = (int)(node / P.nx);
+    const int j = row % P.ny3, k = row / P.ny3;
+    const long long stride[3] = {1, G.ex, (long long)G.ex * G.ey};
+    const long long e0 = G.idx(k + GH, j + GH, i + GH);
+    R Fk[Q][M];
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      // post_q at x - e_q (q = 1..3: +unit vector q-1; q = 4..6: -unit vector q-4)
+      const long long es = q == 0 ? e0 : (q <= 3 ? e0 - stride[q - 1] : e0 + stride[q - 4]);
+      int si, sj, sk;
+      ext_coords(G, es, si, sj, sk);
+      const long long soff = cell3(P, map_index(si - GH, P.nx, P.bc[0], P.bc[1]),
+                                   map_index(sj - GH, P.ny3, P.bc[2], P.bc[3]),
+                                   map_index(sk - GH, P.nz3, P.bc_z[0], P.bc_z[1]));
+      R U[M];
+#pragma unroll
+      for (int c = 0; c < M; c++) U[c] = Ue[(long long)c * n + es];
+      R F[M], S[M];
+#pragma unroll
+      for (int c = 0; c < M; c++) F[c] = R(0);
+      if (q != 0) {
+        const Prim3<R> w = prim3<SYS, R>(K, U);
+        flux3<SYS, R>(K, P, U, w, (q - 1) % 3, F);
+      }
+      if constexpr (SRC) source3<SYS, R>(K, U, S);
+      const R w_om = om[es];
+#pragma unroll
+      for (int c = 0; c < M; c++) {
+        R feq;
+        if (q == 0)
+          feq = a0 * U[c];
+        else if (q <= 3)
+          feq = (al[q - 1] * U[c] + F[c]) * inv2l;
+        else
+          feq = (al[q - 4] * U[c] - F[c]) * inv2l;
+        const R fq = f[(long long)(q * M + c) * P.plane + soff];
+        R v = fq - w_om * (fq - feq);
+        if constexpr (SRC) v += hdt * ak[q] * S[c];
+        Fk[q][c] = v;
+      }
+    }
+    R Ubar[M], Un[M], Sn[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) {
+      R sum = R(0);
+#pragma unroll
+      for (int q = 0; q < Q; q++) sum += Fk[q][c];
+      Ubar[c] = sum;
+      Un[c] = sum;
+      Sn[c] = R(0);
+    }
+    if constexpr (SRC) {
+      if (K.react && Ubar[5] != R(0)) {
+        const double mx = (double)Ubar[1], my = (double)Ubar[2], mz = (double)Ubar[3];
+        const RootF64 rt = react_root_f64((double)Ubar[0], mx * mx + my * my + mz * mz, (double)Ubar[4],
+                                          (double)Ubar[5], 0.5 * cf.dt * K.K, K.gamma_d - 1.0, K.q_d, K.Ti);
+        Un[5] = R(rt.z);
+        st |= rt.st;
+      }
+      source3<SYS, R>(K, Un, Sn);
+    }
+    const long long off = cell3(P, i, j, k);
+    R Uo[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) Uo[c] = R(0);
+#pragma unroll
+    for (int q = 0; q < Q; q++)
+#pragma unroll
+      for (int c = 0; c < M; c++) {
+        R v = Fk[q][c];
+        if constexpr (SRC) v += hdt * ak[q] * Sn[c];
+        fo[(long long)(q * M + c) * P.plane + off] = v;
+        Uo[c] += v;
+      }
+    const Prim3<R> wn = prim3<SYS, R>(K, Uo);
+#pragma unroll
+    for (int d = 0; d < 3; d++) sp[d] = (double)speed3<SYS, R>(K, P, wn, d);
+#pragma unroll
+    for (int c = 0; c < M; c++) usum[c] = (double)Uo[c];
+    bool bad = false;
+#pragma unroll
+    for (int c = 0; c < M; c++) bad |= !(Uo[c] == Uo[c]);
+    if constexpr (SYS != SYS_ADV) bad |= !(wn.rho > R(0)) || !(wn.p > R(0));
+    if (bad) st |= ST_NONPHYSICAL;
+  }
+  // side outputs: x, y bounds, sums and status through the 2D reduction; the
+  // z bound through its own block maximum
+  block_side_outputs_to<M>(sp[0], sp[1], usum, ctl, (slot + 1) % 3, partials + (long long)blockIdx.x * M, st);
+  unsigned long long* zs = &ctl->amax_z[(slot + 1) % 3];
+  block_max3_to(0.0, 0.0, sp[2], zs, zs, zs);
+  if (blockIdx.x == 0 && threadIdx.x == 0) advance_ctl3(ctl, slot, cf);
+}
+
+}  // namespace lbmh

@@ -15,6 +15,7 @@
 #include "host_util.h"
 #include "physics.cuh"
 #include "state.cuh"
+#include "lbm3d.cuh"
 #include "unfused.cuh"
 
 using namespace lbmh;
@@ -105,7 +106,7 @@ struct Impl {
   }
 
   static int unfused_front(lbmh_handle* h, int slot, const DevParams& P) {
-    long long next = (long long)h->G.ex * h->G.ey;
+    long long next = (long long)h->G.ex * h->G.ey * h->G.ez;
     unsigned nb = blocks_for(next);
     R* const* buf = (R* const*)h->dbuf;
     k_moments_ext<SYS, D, R><<<nb, kBlock, 0, h->stream>>>(P, buf, h->ctl, slot, h->G, (R*)h->Ue);
@@ -196,8 +197,97 @@ struct Impl {
   }
 };
 
+// 3D (D3Q7) operations: the four-kernel path of lbm3d.cuh; the row-wise
+// kernels (moments, checkpoints) are shared with 1D/2D (rows = z * ny + y)
+template <int SYS, class R>
+struct Impl3 {
+  static constexpr int M = Fields3<SYS>::M, Q = 7;
+
+  static ExtGeom3 geom(const lbmh_handle* h) { return ExtGeom3{h->G.ex, h->G.ey, h->G.ez}; }
+
+  static int launch_step(lbmh_handle* h, int slot, double T) {
+    DevParams P = h->P;
+    P.T = T;
+    const ExtGeom3 G = geom(h);
+    const long long next = (long long)G.ex * G.ey * G.ez;
+    const unsigned nb = blocks_for(next);
+    R* const* buf = (R* const*)h->dbuf;
+    k3_moments_ext<SYS, R><<<nb, kBlock, 0, h->stream>>>(P, buf, h->ctl, slot, G, (R*)h->Ue);
+    k3_indicator<SYS, R><<<nb, kBlock, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->Ue, (R*)h->nue);
+    k3_omega<R><<<nb, kBlock, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->nue, (R*)h->ome);
+    const long long nn = (long long)P.nx * P.ny;
+    const unsigned nbn = blocks_for(nn);
+    k3_collide_stream<SYS, R><<<nbn, kBlock, 0, h->stream>>>(P, buf, h->ctl, slot, G, (const R*)h->Ue,
+                                                             (const R*)h->ome, h->partials);
+    h->nblocks = (int)nbn;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "3D step launch");
+    return LBMH_OK;
+  }
+
+  static int launch_unfused_diag(lbmh_handle* h, int) {
+    return fail(h, LBMH_ERR_UNSUPPORTED, "the omega diagnostic is not provided for 3D lattices");
+  }
+
+  static int init(lbmh_handle* h, const double* U0dev) {
+    const long long nn = (long long)h->P.nx * h->P.ny;
+    const unsigned nb = reduce_blocks_for(nn);
+    k3_init_speed<SYS><<<nb, kBlock, 0, h->stream>>>(h->P, U0dev, h->ctl);
+    k3_init_eq<SYS, R><<<nb, kBlock, 0, h->stream>>>(h->P, U0dev, (R*)h->fbuf[0], h->ctl);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "3D init launch");
+    return LBMH_OK;
+  }
+
+  static int moments(lbmh_handle* h, int slot, double* Udev) {
+    const long long nn = (long long)h->P.nx * h->P.ny;
+    k_moments<M, Q, R><<<blocks_for(nn), kBlock, 0, h->stream>>>(h->P, (R* const*)h->dbuf, h->ctl, slot, Udev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments launch");
+    return LBMH_OK;
+  }
+
+  static int get_f(lbmh_handle* h, int slot, double* dev) {
+    const long long n = (long long)h->P.nx * h->P.ny * Q * M;
+    k_get_f<R><<<blocks_for(n), kBlock, 0, h->stream>>>(h->P, Q * M, (R* const*)h->dbuf, h->ctl, slot, dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_f launch");
+    return LBMH_OK;
+  }
+
+  static int set_f(lbmh_handle* h, const double* dev) {
+    const long long n = (long long)h->P.nx * h->P.ny * Q * M;
+    k_set_f<R><<<blocks_for(n), kBlock, 0, h->stream>>>(h->P, Q * M, (R*)h->fbuf[0], dev);
+    k3_speed_of_f<SYS, R><<<reduce_blocks_for((long long)h->P.nx * h->P.ny), kBlock, 0, h->stream>>>(
+        h->P, (R* const*)h->dbuf, h->ctl);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_f launch");
+    return LBMH_OK;
+  }
+
+  static int omega_extract(lbmh_handle* h, double*) {
+    return fail(h, LBMH_ERR_UNSUPPORTED, "the omega diagnostic is not provided for 3D lattices");
+  }
+
+  static int setup_fused(lbmh_handle*) { return -1; }
+
+  static const Ops* ops() {
+    static const Ops o = {launch_step, launch_unfused_diag, init, moments, get_f, set_f, omega_extract, setup_fused,
+                          false};
+    return &o;
+  }
+};
+
 template <class R>
 const Ops* pick_dim(int sys, int dim) {
+  if (dim == 3) {
+    switch (sys) {
+      case SYS_ADV: return Impl3<SYS_ADV, R>::ops();
+      case SYS_EULER: return Impl3<SYS_EULER, R>::ops();
+      case SYS_REACT: return Impl3<SYS_REACT, R>::ops();
+    }
+    return nullptr;
+  }
 #define PICK(S)                                        \
   case S:                                              \
     return dim == 1 ? Impl<S, 1, R>::ops() : Impl<S, 2, R>::ops();
@@ -251,7 +341,7 @@ int ensure_utmp(lbmh_handle* h, size_t bytes) {
 // ghost-extended scratch of the unfused path (also used by lbmh_omega)
 int ensure_scratch(lbmh_handle* h) {
   if (h->Ue) return LBMH_OK;
-  long long next = (long long)h->G.ex * h->G.ey;
+  long long next = (long long)h->G.ex * h->G.ey * h->G.ez;
   size_t b1 = (size_t)next * h->m * h->elem, b2 = (size_t)next * h->elem;
   if (cudaMalloc(&h->Ue, b1) != cudaSuccess || cudaMalloc(&h->nue, b2) != cudaSuccess ||
       cudaMalloc(&h->ome, b2) != cudaSuccess) {
@@ -390,8 +480,9 @@ int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
   }
 
   h->G.ex = P.nx + 2 * GH;
-  h->G.gy = p->dim == 2 ? GH : 0;
-  h->G.ey = p->dim == 2 ? P.ny + 2 * GH : 1;
+  h->G.gy = p->dim >= 2 ? GH : 0;
+  h->G.ey = p->dim == 2 ? P.ny + 2 * GH : (p->dim == 3 ? P.ny3 + 2 * GH : 1);
+  h->G.ez = p->dim == 3 ? P.nz3 + 2 * GH : 1;
   long long nn = (long long)P.nx * P.ny;
   size_t fbytes = (size_t)h->Q * h->m * P.plane * h->elem;
   h->max_blocks = (int)blocks_for(nn);
@@ -490,7 +581,8 @@ int lbmh_advance_to(lbmh_handle* h, double T, int64_t max_steps) {
     int slot = current_slot(h);
     double t = c.t[slot];
     if (t >= T) break;
-    double ab = bits_to_host(c.amax[slot][0]) + (h->dim == 2 ? bits_to_host(c.amax[slot][1]) : 0.0);
+    double ab = bits_to_host(c.amax[slot][0]) + (h->dim >= 2 ? bits_to_host(c.amax[slot][1]) : 0.0) +
+                (h->dim == 3 ? bits_to_host(c.amax_z[slot]) : 0.0);
     double dt_est = h->P.cfl * h->P.dx / ab;
     int64_t est = (int64_t)((T - t) / dt_est) + 1;
     int64_t chunk = est < 8 ? 8 : (est > 256 ? 256 : est);
@@ -676,6 +768,7 @@ extern "C" int lbmh_step_static(const lbmh_problem* p, const double* f_in, doubl
   if (rc) return fail(nullptr, rc, why);
   if (p->precision != LBMH_FP64) return fail(nullptr, LBMH_ERR_UNSUPPORTED, "lbmh_step_static runs in FP64 only");
   if (needs_fused(p)) return fail(nullptr, LBMH_ERR_UNSUPPORTED, "lbmh_step_static has no reflecting/inflow sides or sponge");
+  if (p->dim == 3) return fail(nullptr, LBMH_ERR_UNSUPPORTED, "lbmh_step_static serves 1D and 2D lattices");
   if (!f_in || !f_out || f_in == f_out) return fail(nullptr, LBMH_ERR_INVALID_ARG, "f_in and f_out must be distinct device arrays");
   const int m = nfields(p->system, p->dim), Q = 2 * p->dim + 1;
   const DevParams P = make_devparams(p, p->nx);  // the caller's arrays are unpadded [Q][m][ny][nx]

@@ -12,6 +12,7 @@ constexpr int GH = 3;  // ghost layers: the update of one node reads f^n up to 3
 
 struct ExtGeom {
   int ex, ey, gy;  // extended sizes; gy = ghost rows (0 in 1D)
+  int ez = 1;      // 3D only: extended size in z
   __device__ __forceinline__ long long idx(int ej, int ei) const { return (long long)ej * ex + ei; }
 };
 

@@ -48,6 +48,10 @@ class _Problem(ctypes.Structure):
         ("cuda_stream", ctypes.c_void_p),
         ("sponge_width", ctypes.c_double),
         ("u_in", ctypes.c_double * 8),
+        ("nz", ctypes.c_int),
+        ("z0", ctypes.c_double), ("z1", ctypes.c_double),
+        ("bc_z", ctypes.c_int * 2),
+        ("adv_z", ctypes.c_double),
     ]
 
 
@@ -127,7 +131,7 @@ def load(path=LIB_PATH):
 def _c_problem(pb, precision, kernel, stream):
     s = _Problem()
     s.system, s.dim, s.nx = int(pb.system), int(pb.dim), int(pb.nx)
-    s.ny = int(pb.ny) if pb.dim == 2 else 1
+    s.ny = int(pb.ny) if pb.dim >= 2 else 1
     s.x0, s.x1, s.y0, s.y1 = float(pb.x0), float(pb.x1), float(pb.y0), float(pb.y1)
     for i in range(4):
         s.bc[i] = int(pb.bc[i])
@@ -145,6 +149,13 @@ def _c_problem(pb, precision, kernel, stream):
     s.sponge_width = float(getattr(pb, "sponge_width", 0.0))
     for i, v in enumerate(tuple(getattr(pb, "u_in", ()))[:8]):
         s.u_in[i] = float(v)
+    if pb.dim == 3:
+        s.nz = int(pb.nz)
+        s.z0, s.z1 = float(pb.z0), float(pb.z1)
+        s.bc_z[0], s.bc_z[1] = int(pb.bc_z[0]), int(pb.bc_z[1])
+        s.adv_z = float(pb.adv[2]) if len(pb.adv) > 2 else 0.0
+    else:
+        s.nz = 1
     return s
 
 
