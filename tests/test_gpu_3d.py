@@ -1,0 +1,101 @@
+"""The 3D (D3Q7) path against the FP64 oracle: advection, Euler and reactive
+Euler, periodic and outflow sides, ragged grids, FP64 (relative max error <=
+1e-12 per field) and FP32 (relative L1 <= 2e-5, relative max <= 5e-4);
+checkpoints, time targets and the unsupported combinations."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_18177_b300 import lbmh
+from paper_2609_18177_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    lbmh.load()
+
+
+def rel_max(g, o):
+    m = o.shape[0]
+    g2, o2 = g.reshape(m, -1), o.reshape(m, -1)
+    s = np.abs(o2).max(axis=1)
+    return np.abs(g2 - o2).max(axis=1) / np.where(s > 0, s, 1.0)
+
+
+def rel_l1(g, o):
+    m = o.shape[0]
+    g2, o2 = g.reshape(m, -1), o.reshape(m, -1)
+    s = np.abs(o2).sum(axis=1)
+    return np.abs(g2 - o2).sum(axis=1) / np.where(s > 0, s, 1.0)
+
+
+def case(system, bc, nx=23, ny=19, nz=17, seed=2):
+    h = 1.0 / nx
+    kw = dict(system=system, dim=3, nx=nx, ny=ny, nz=nz, y1=ny * h, z1=nz * h, cfl=0.8, bc=(bc,) * 4,
+              bc_z=(bc, bc), adv=(0.7, -0.45, 0.35))
+    if system == W.REACTIVE:
+        kw.update(gamma=1.2, q=5.0, K=40.0, Ti=2.0)
+    pb = W.Problem(**kw)
+    return pb, W.random_state(pb, seed=seed)
+
+
+CASES = [(s, bc) for s in (W.ADVECTION, W.EULER, W.REACTIVE) for bc in (W.PERIODIC, W.OUTFLOW)]
+IDS = [f"{W.SYSTEM_NAMES[s]}-{'per' if bc == 0 else 'out'}" for s, bc in CASES]
+
+
+@pytest.mark.parametrize("precision", [lbmh.FP64, lbmh.FP32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("system,bc", CASES, ids=IDS)
+def test_3d_matches_oracle(system, bc, precision):
+    pb, U0 = case(system, bc)
+    pb = pb.with_(precision=precision)
+    r = oracle.Run(pb, U0)
+    s = lbmh.Solver(pb, precision=precision).set_state(U0)
+    for n in range(4):
+        r.step(5)
+        s.step(5)
+        Ug, Uo = s.moments(), r.moments()
+        assert s.nsteps == r.nsteps
+        if precision == lbmh.FP64:
+            assert np.all(rel_max(Ug, Uo) <= 1e-12), (5 * (n + 1), rel_max(Ug, Uo))
+            assert abs(s.t - r.t) <= 1e-13 * r.t
+        else:
+            assert np.all(rel_l1(Ug, Uo) <= 2e-5), (5 * (n + 1), rel_l1(Ug, Uo))
+            assert np.all(rel_max(Ug, Uo) <= 5e-4), (5 * (n + 1), rel_max(Ug, Uo))
+    s.close()
+
+
+def test_3d_checkpoint_resume_is_bitwise_and_time_target():
+    pb, U0 = case(W.EULER, W.PERIODIC, nx=16, ny=16, nz=16)
+    for prec in (lbmh.FP64, lbmh.FP32):
+        a = lbmh.Solver(pb, precision=prec).set_state(U0).step(6)
+        f = a.get_f()
+        t, n = a.t, a.nsteps
+        a.step(4)
+        b = lbmh.Solver(pb, precision=prec).set_f(f, t, n).step(4)
+        assert np.array_equal(a.get_f(), b.get_f())
+        a.close()
+        b.close()
+    r = oracle.Run(pb, U0)
+    s = lbmh.Solver(pb, precision=lbmh.FP64).set_state(U0)
+    s.advance_to(0.02)
+    while r.t < 0.02:
+        r.step(1)
+    assert s.info()["steps"] == r.nsteps
+    assert np.all(rel_max(s.moments(), r.moments()) <= 1e-12)
+    s.close()
+
+
+def test_3d_unsupported_combinations():
+    pb, _U0 = case(W.EULER, W.PERIODIC, nx=8, ny=8, nz=8)
+    with pytest.raises(lbmh.LbmhError) as ei:
+        lbmh.Solver(pb.with_(system=W.SWE), precision=lbmh.FP64)
+    assert ei.value.code == lbmh.ERR_UNSUPPORTED
+    s = lbmh.Solver(pb, precision=lbmh.FP64).set_state(W.random_state(pb, seed=1))
+    with pytest.raises(lbmh.LbmhError):
+        s.omega()
+    s.close()
