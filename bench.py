@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-n", type=int, default=384)
-    ap.add_argument("--workload", default="riemann2d", choices=["riemann2d", "batched", "served", "lines1d"])
+    ap.add_argument("--workload", default="riemann2d",
+                    choices=["riemann2d", "batched", "served", "lines1d", "cube3d"])
     ap.add_argument("--lattice", default="riemann2d", choices=["riemann2d", "reactive", "dambreak"],
                     help="single-lattice line: the lattice stepped (default: the 2D Riemann roofline run)")
     ap.add_argument("--case", default=None,
@@ -454,12 +455,54 @@ def run_lines1d(args):
     }
 
 
+def run_cube3d(args):
+    """The 3D (D3Q7) path: Euler on a periodic n^3 cube with a seeded random
+    state (smooth fields plus a jump), FP32 and FP64, four kernels per step.
+    value = FP32 MLUPS; algorithmic bytes per node update 2 Q m sizeof(real)
+    (Q = 7, m = 5: 280 B in FP32)."""
+    import torch
+    from paper_2609_18177_b300 import lbmh
+    from paper_2609_18177_b300 import workloads as W
+    n = args.n if args.n != 8192 else 256
+    out = []
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = measured_peaks()
+    for prec in (lbmh.FP32, lbmh.FP64):
+        pb = W.cube(W.EULER, n, cfl=0.8)
+        U0 = W.random_state(pb, seed=args.seed)
+        s = lbmh.Solver(pb.with_(precision=prec), precision=prec).set_state(U0)
+        s.step(max(3, args.warmup))
+        steps = min(args.steps, 200) if prec == lbmh.FP32 else min(args.steps, 20)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = s.info()["status"]
+        s.close()
+        elem = 4 if prec == lbmh.FP32 else 8
+        gbs = 2 * 7 * 5 * elem * pb.nodes * steps / (ms / 1e3) / 1e9
+        out.append({"dtype": "f32" if prec == lbmh.FP32 else "f64", "n": n, "steps": steps,
+                    "ms_per_step": ms / steps, "mlups": pb.nodes * steps / (ms / 1e3) / 1e6,
+                    "hbm_gbs_algorithmic": gbs, "frac_of_peak": gbs / peak, "status": st})
+    return {
+        "metric": METRIC, "workload": "cube3d", "value": out[0]["mlups"], "unit": "MLUPS",
+        "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"3D Euler (D3Q7) periodic {n}^3, seeded random state, CFL 0.8, four-kernel path",
+                   "peak_gbs": peak, "peak_kind": peak_kind, "l2": "inputs larger than L2"},
+        "cases": out,
+    }
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in ("batched", "served", "lines1d"):
-        line = {"batched": run_batched, "served": run_served, "lines1d": run_lines1d}[args.workload](args)
+    if args.workload in ("batched", "served", "lines1d", "cube3d"):
+        line = {"batched": run_batched, "served": run_served, "lines1d": run_lines1d,
+                "cube3d": run_cube3d}[args.workload](args)
         print(json.dumps(line), flush=True)
         return 0
     import torch
