@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--sample", type=int, default=16)
     ap.add_argument("--requests", type=int, default=60)
     ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--autotune", action="store_true",
+                    help="served: let each system's batch time its kernel variants once it holds two lattices")
     ap.add_argument("--sweep-rates", default="16,8,4",
                     help="served: lower offered rates (req/s) of the load sweep, comma-separated")
     return ap.parse_args()
@@ -373,7 +375,8 @@ def run_served(args):
     for idx, (label, rate, nreq) in enumerate(plan):
         trace = S.poisson_trace(nreq, rate, seed=args.seed + idx)
         inputs = {r.rid: S.make_problem(r) for r in trace}
-        srv = S.Server(capacity_bytes=24 << 30, max_instances=256, chunk=32, keep_results=(label == "offered"))
+        srv = S.Server(capacity_bytes=24 << 30, max_instances=256, chunk=32, keep_results=(label == "offered"),
+                       autotune=args.autotune)
         results, stats = srv.run(trace, inputs=inputs)
         srv.close()
         stats["rate_req_per_s"] = rate
