@@ -321,10 +321,14 @@ __global__ void __launch_bounds__(kBlock) k3_speed_of_f(DevParams P, R* const* b
   block_max3_to(s[0], s[1], s[2], &ctl->amax[0][0], &ctl->amax[0][1], &ctl->amax_z[0]);
 }
 
-__device__ __forceinline__ void ext_coords(const ExtGeom3& G, long long e, int& ei, int& ej, int& ek) {
-  ei = (int)(e % G.ex);
-  ej = (int)((e / G.ex) % G.ey);
-  ek = (int)(e / ((long long)G.ex * G.ey));
+// the extended-grid kernels run on a grid (ceil(ex / blockDim.x), ey, ez):
+// coordinates come from the block indices, without 64-bit divisions
+__device__ __forceinline__ bool ext_coords(const ExtGeom3& G, int& ei, int& ej, int& ek, long long& e) {
+  ei = blockIdx.x * blockDim.x + threadIdx.x;
+  ej = blockIdx.y;
+  ek = blockIdx.z;
+  e = G.idx(ek, ej, ei);
+  return ei < G.ex;
 }
 
 // K0: U = sum_k f_k on the ghost-extended grid (wrapped / clamped reads)
@@ -332,12 +336,11 @@ template <int SYS, class R>
 __global__ void k3_moments_ext(DevParams P, R* const* buf, const Ctl* ctl, int slot, ExtGeom3 G, R* Ue) {
   constexpr int M = Fields3<SYS>::M;
   const long long n = (long long)G.ex * G.ey * G.ez;
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= n) return;
+  int ei, ej, ek;
+  long long e;
+  if (!ext_coords(G, ei, ej, ek, e)) return;
   if (P.T > 0.0 && ctl->t[slot] >= P.T) return;
   const R* f = buf[ctl->parity[slot]];
-  int ei, ej, ek;
-  ext_coords(G, e, ei, ej, ek);
   const long long off = cell3(P, map_index(ei - GH, P.nx, P.bc[0], P.bc[1]), map_index(ej - GH, P.ny3, P.bc[2], P.bc[3]),
                               map_index(ek - GH, P.nz3, P.bc_z[0], P.bc_z[1]));
 #pragma unroll
@@ -354,11 +357,10 @@ template <int SYS, class R>
 __global__ void k3_indicator(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, const R* Ue, R* nu) {
   constexpr int M = Fields3<SYS>::M;
   const long long n = (long long)G.ex * G.ey * G.ez;
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  if (P.T > 0.0 && ctl->t[slot] >= P.T) return;
   int ei, ej, ek;
-  ext_coords(G, e, ei, ej, ek);
+  long long e;
+  if (!ext_coords(G, ei, ej, ek, e)) return;
+  if (P.T > 0.0 && ctl->t[slot] >= P.T) return;
   if (ei < 1 || ei >= G.ex - 1 || ej < 1 || ej >= G.ey - 1 || ek < 1 || ek >= G.ez - 1) return;
   const Phys<R> K = make_phys<R>(P);
   const long long stride[3] = {1, G.ex, (long long)G.ex * G.ey};
@@ -382,12 +384,10 @@ __global__ void k3_indicator(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, 
 // K2: omega = 1 + 1/(1 + nu~), nu~ the sum over the 3^3 box (Eq. 2.15, 2.16)
 template <class R>
 __global__ void k3_omega(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, const R* nu, R* om) {
-  const long long n = (long long)G.ex * G.ey * G.ez;
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  if (P.T > 0.0 && ctl->t[slot] >= P.T) return;
   int ei, ej, ek;
-  ext_coords(G, e, ei, ej, ek);
+  long long e;
+  if (!ext_coords(G, ei, ej, ek, e)) return;
+  if (P.T > 0.0 && ctl->t[slot] >= P.T) return;
   if (ei < 2 || ei >= G.ex - 2 || ej < 2 || ej >= G.ey - 2 || ek < 2 || ek >= G.ez - 2) return;
   R w;
   if (P.omega_mode == 1) {
@@ -429,37 +429,33 @@ __global__ void __launch_bounds__(kBlock) k3_collide_stream(DevParams P, R* cons
   constexpr bool SRC = SYS == SYS_REACT;
   const StepCoef3 cf = step_coef3(P, ctl, slot);
   if (!cf.active) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) advance_ctl3(ctl, slot, cf);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) advance_ctl3(ctl, slot, cf);
     return;
   }
   const R* f = buf[ctl->parity[slot]];
   R* fo = buf[ctl->parity[slot] ^ 1];
-  const long long nn = (long long)P.nx * P.ny;
-  const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  // grid (ceil(nx / blockDim.x), ny, nz): node (i, j, k) from the block indices
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
   const long long n = (long long)G.ex * G.ey * G.ez;
+  const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   double sp[3] = {0.0, 0.0, 0.0}, usum[M];
 #pragma unroll
   for (int c = 0; c < M; c++) usum[c] = 0.0;
   unsigned st = 0u;
-  if (node < nn) {
+  if (i < P.nx) {
     const Phys<R> K = make_phys<R>(P);
     const R a0 = R(cf.a0), inv2l = R(1.0 / (2.0 * cf.lam)), hdt = R(0.5 * cf.dt);
     const R al[3] = {R(cf.alpha[0]), R(cf.alpha[1]), R(cf.alpha[2])};
     const R ak[7] = {a0, R(cf.aj[0]), R(cf.aj[1]), R(cf.aj[2]), R(cf.aj[0]), R(cf.aj[1]), R(cf.aj[2])};
-    const int i = (int)(node % P.nx), row = (int)(node / P.nx);
-    const int j = row % P.ny3, k = row / P.ny3;
-    const long long stride[3] = {1, G.ex, (long long)G.ex * G.ey};
-    const long long e0 = G.idx(k + GH, j + GH, i + GH);
     R Fk[Q][M];
 #pragma unroll
     for (int q = 0; q < Q; q++) {
       // post_q at x - e_q (q = 1..3: +unit vector q-1; q = 4..6: -unit vector q-4)
-      const long long es = q == 0 ? e0 : (q <= 3 ? e0 - stride[q - 1] : e0 + stride[q - 4]);
-      int si, sj, sk;
-      ext_coords(G, es, si, sj, sk);
-      const long long soff = cell3(P, map_index(si - GH, P.nx, P.bc[0], P.bc[1]),
-                                   map_index(sj - GH, P.ny3, P.bc[2], P.bc[3]),
-                                   map_index(sk - GH, P.nz3, P.bc_z[0], P.bc_z[1]));
+      const int dir = q == 0 ? -1 : (q - 1) % 3, sg = q <= 3 ? -1 : 1;
+      const int si = i + (dir == 0 ? sg : 0), sj = j + (dir == 1 ? sg : 0), sk = k + (dir == 2 ? sg : 0);
+      const long long es = G.idx(sk + GH, sj + GH, si + GH);
+      const long long soff = cell3(P, map_index(si, P.nx, P.bc[0], P.bc[1]), map_index(sj, P.ny3, P.bc[2], P.bc[3]),
+                                   map_index(sk, P.nz3, P.bc_z[0], P.bc_z[1]));
       R U[M];
 #pragma unroll
       for (int c = 0; c < M; c++) U[c] = Ue[(long long)c * n + es];
@@ -533,10 +529,15 @@ __global__ void __launch_bounds__(kBlock) k3_collide_stream(DevParams P, R* cons
   }
   // side outputs: x, y bounds, sums and status through the 2D reduction; the
   // z bound through its own block maximum
-  block_side_outputs_to<M>(sp[0], sp[1], usum, ctl, (slot + 1) % 3, partials + (long long)blockIdx.x * M, st);
+  block_side_outputs_to<M>(sp[0], sp[1], usum, ctl, (slot + 1) % 3, partials + bid * M, st);
   unsigned long long* zs = &ctl->amax_z[(slot + 1) % 3];
   block_max3_to(0.0, 0.0, sp[2], zs, zs, zs);
-  if (blockIdx.x == 0 && threadIdx.x == 0) advance_ctl3(ctl, slot, cf);
+  if (bid == 0 && threadIdx.x == 0) advance_ctl3(ctl, slot, cf);
 }
+
+// launch shapes of the 3D kernels
+constexpr int kBlock3 = 128;
+inline dim3 grid3_ext(int ex, int ey, int ez) { return dim3((unsigned)((ex + kBlock3 - 1) / kBlock3), ey, ez); }
+inline dim3 grid3_nodes(int nx, int ny, int nz) { return dim3((unsigned)((nx + kBlock3 - 1) / kBlock3), ny, nz); }
 
 }  // namespace lbmh

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -209,17 +210,14 @@ struct Impl3 {
     DevParams P = h->P;
     P.T = T;
     const ExtGeom3 G = geom(h);
-    const long long next = (long long)G.ex * G.ey * G.ez;
-    const unsigned nb = blocks_for(next);
+    const dim3 ge = grid3_ext(G.ex, G.ey, G.ez), gn = grid3_nodes(P.nx, P.ny3, P.nz3);
     R* const* buf = (R* const*)h->dbuf;
-    k3_moments_ext<SYS, R><<<nb, kBlock, 0, h->stream>>>(P, buf, h->ctl, slot, G, (R*)h->Ue);
-    k3_indicator<SYS, R><<<nb, kBlock, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->Ue, (R*)h->nue);
-    k3_omega<R><<<nb, kBlock, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->nue, (R*)h->ome);
-    const long long nn = (long long)P.nx * P.ny;
-    const unsigned nbn = blocks_for(nn);
-    k3_collide_stream<SYS, R><<<nbn, kBlock, 0, h->stream>>>(P, buf, h->ctl, slot, G, (const R*)h->Ue,
+    k3_moments_ext<SYS, R><<<ge, kBlock3, 0, h->stream>>>(P, buf, h->ctl, slot, G, (R*)h->Ue);
+    k3_indicator<SYS, R><<<ge, kBlock3, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->Ue, (R*)h->nue);
+    k3_omega<R><<<ge, kBlock3, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->nue, (R*)h->ome);
+    k3_collide_stream<SYS, R><<<gn, kBlock3, 0, h->stream>>>(P, buf, h->ctl, slot, G, (const R*)h->Ue,
                                                              (const R*)h->ome, h->partials);
-    h->nblocks = (int)nbn;
+    h->nblocks = (int)(gn.x * gn.y * gn.z);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "3D step launch");
     return LBMH_OK;
@@ -486,6 +484,10 @@ int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
   long long nn = (long long)P.nx * P.ny;
   size_t fbytes = (size_t)h->Q * h->m * P.plane * h->elem;
   h->max_blocks = (int)blocks_for(nn);
+  if (p->dim == 3) {  // one block per (x segment, y, z) row of the 3D step
+    const dim3 g3 = grid3_nodes(P.nx, P.ny3, P.nz3);
+    h->max_blocks = std::max(h->max_blocks, (int)(g3.x * g3.y * g3.z));
+  }
   h->utmp_bytes = 0;
   auto alloc = [&](void** ptr, size_t bytes) -> bool {
     if (cudaMalloc(ptr, bytes) != cudaSuccess) {
