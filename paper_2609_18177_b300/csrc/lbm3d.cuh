@@ -16,6 +16,7 @@
 #pragma once
 #include "common.cuh"
 #include "physics.cuh"
+#include "fused.cuh"
 #include "unfused.cuh"
 
 namespace lbmh {
@@ -419,39 +420,70 @@ __device__ __forceinline__ void source3(const Phys<R>& K, const R* U, R* S) {
   }
 }
 
+// block maximum of one speed in the path's type into d (NaN propagates)
+template <class R>
+__device__ __forceinline__ void block_max1_to(R v, unsigned long long* d) {
+  __shared__ R red1[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const R u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = (u > v || u != u) ? u : v;
+  }
+  __syncthreads();
+  if (lane == 0) red1[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < nw; i++) m = nanmax3(m, (double)red1[i]);
+    atomic_max_nonneg(d, m);
+  }
+}
+
+// rows (y) per block of the 3D collision kernel
+constexpr int kRows3 = 8;
+
 // K3: collision with the first half-source at x - e_k (Eq. 2.2), pull
 // streaming, the implicit moment (2.8) in FP64 and the second half-source at
-// x; writes f^{n+1}; side outputs (three speed bounds, FP64 sums, status).
+// x; writes f^{n+1}; side outputs (three speed bounds, FP64-quality sums,
+// status).  Grid (ceil(nx / blockDim.x), ceil(ny / kRows3), nz): a block
+// handles kRows3 rows, so the side-output reduction is paid once per block.
 template <int SYS, class R>
-__global__ void __launch_bounds__(kBlock) k3_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
-                                                            ExtGeom3 G, const R* Ue, const R* om, double* partials) {
+__global__ void __launch_bounds__(128) k3_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot, ExtGeom3 G,
+                                                         const R* Ue, const R* om, double* partials) {
   constexpr int M = Fields3<SYS>::M, Q = 7;
   constexpr bool SRC = SYS == SYS_REACT;
   const StepCoef3 cf = step_coef3(P, ctl, slot);
+  const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   if (!cf.active) {
-    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) advance_ctl3(ctl, slot, cf);
+    if (bid == 0 && threadIdx.x == 0) advance_ctl3(ctl, slot, cf);
     return;
   }
   const R* f = buf[ctl->parity[slot]];
   R* fo = buf[ctl->parity[slot] ^ 1];
-  // grid (ceil(nx / blockDim.x), ny, nz): node (i, j, k) from the block indices
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
   const long long n = (long long)G.ex * G.ey * G.ez;
-  const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  double sp[3] = {0.0, 0.0, 0.0}, usum[M];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.z;
+  const Phys<R> K = make_phys<R>(P);
+  const R a0 = R(cf.a0), inv2l = R(1.0 / (2.0 * cf.lam)), hdt = R(0.5 * cf.dt);
+  const R al0 = R(cf.alpha[0]), al1 = R(cf.alpha[1]), al2 = R(cf.alpha[2]);
+  const R aj0 = R(cf.aj[0]), aj1 = R(cf.aj[1]), aj2 = R(cf.aj[2]);
+  R sp0 = R(0), sp1 = R(0), sp2 = R(0);
+  Acc<R> acc[M];
 #pragma unroll
-  for (int c = 0; c < M; c++) usum[c] = 0.0;
+  for (int c = 0; c < M; c++) acc[c].init();
   unsigned st = 0u;
-  if (i < P.nx) {
-    const Phys<R> K = make_phys<R>(P);
-    const R a0 = R(cf.a0), inv2l = R(1.0 / (2.0 * cf.lam)), hdt = R(0.5 * cf.dt);
-    const R al[3] = {R(cf.alpha[0]), R(cf.alpha[1]), R(cf.alpha[2])};
-    const R ak[7] = {a0, R(cf.aj[0]), R(cf.aj[1]), R(cf.aj[2]), R(cf.aj[0]), R(cf.aj[1]), R(cf.aj[2])};
-    R Fk[Q][M];
+  const int j0 = blockIdx.y * kRows3, j1 = min(j0 + kRows3, P.ny3);
+  for (int j = j0; j < j1 && i < P.nx; j++) {
+    R Fk[SRC ? Q : 1][M];
+    R Ubar[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) Ubar[c] = R(0);
+    const long long off = cell3(P, i, j, k);
 #pragma unroll
     for (int q = 0; q < Q; q++) {
       // post_q at x - e_q (q = 1..3: +unit vector q-1; q = 4..6: -unit vector q-4)
-      const int dir = q == 0 ? -1 : (q - 1) % 3, sg = q <= 3 ? -1 : 1;
+      const int dir = q == 0 ? -1 : (q - 1) % 3;
+      const int sg = q <= 3 ? -1 : 1;
       const int si = i + (dir == 0 ? sg : 0), sj = j + (dir == 1 ? sg : 0), sk = k + (dir == 2 ? sg : 0);
       const long long es = G.idx(sk + GH, sj + GH, si + GH);
       const long long soff = cell3(P, map_index(si, P.nx, P.bc[0], P.bc[1]), map_index(sj, P.ny3, P.bc[2], P.bc[3]),
@@ -459,85 +491,88 @@ __global__ void __launch_bounds__(kBlock) k3_collide_stream(DevParams P, R* cons
       R U[M];
 #pragma unroll
       for (int c = 0; c < M; c++) U[c] = Ue[(long long)c * n + es];
-      R F[M], S[M];
+      R F[M];
 #pragma unroll
       for (int c = 0; c < M; c++) F[c] = R(0);
       if (q != 0) {
         const Prim3<R> w = prim3<SYS, R>(K, U);
-        flux3<SYS, R>(K, P, U, w, (q - 1) % 3, F);
+        flux3<SYS, R>(K, P, U, w, dir, F);
       }
+      R S[M];
       if constexpr (SRC) source3<SYS, R>(K, U, S);
       const R w_om = om[es];
+      const R alq = dir == 0 ? al0 : (dir == 1 ? al1 : al2);
+      const R akq = q == 0 ? a0 : (dir == 0 ? aj0 : (dir == 1 ? aj1 : aj2));
 #pragma unroll
       for (int c = 0; c < M; c++) {
-        R feq;
-        if (q == 0)
-          feq = a0 * U[c];
-        else if (q <= 3)
-          feq = (al[q - 1] * U[c] + F[c]) * inv2l;
-        else
-          feq = (al[q - 4] * U[c] - F[c]) * inv2l;
+        const R feq = q == 0 ? a0 * U[c] : (q <= 3 ? (alq * U[c] + F[c]) * inv2l : (alq * U[c] - F[c]) * inv2l);
         const R fq = f[(long long)(q * M + c) * P.plane + soff];
         R v = fq - w_om * (fq - feq);
-        if constexpr (SRC) v += hdt * ak[q] * S[c];
-        Fk[q][c] = v;
+        if constexpr (SRC) {
+          v += hdt * akq * S[c];
+          Fk[q][c] = v;
+        } else {
+          fo[(long long)(q * M + c) * P.plane + off] = v;  // no source: F_q is final
+        }
+        Ubar[c] += v;
       }
     }
-    R Ubar[M], Un[M], Sn[M];
+    R Uo[M];
 #pragma unroll
-    for (int c = 0; c < M; c++) {
-      R sum = R(0);
-#pragma unroll
-      for (int q = 0; q < Q; q++) sum += Fk[q][c];
-      Ubar[c] = sum;
-      Un[c] = sum;
-      Sn[c] = R(0);
-    }
+    for (int c = 0; c < M; c++) Uo[c] = Ubar[c];
     if constexpr (SRC) {
+      R Sn[M];
+#pragma unroll
+      for (int c = 0; c < M; c++) Sn[c] = R(0);
       if (K.react && Ubar[5] != R(0)) {
         const double mx = (double)Ubar[1], my = (double)Ubar[2], mz = (double)Ubar[3];
         const RootF64 rt = react_root_f64((double)Ubar[0], mx * mx + my * my + mz * mz, (double)Ubar[4],
                                           (double)Ubar[5], 0.5 * cf.dt * K.K, K.gamma_d - 1.0, K.q_d, K.Ti);
+        R Un[M];
+#pragma unroll
+        for (int c = 0; c < M; c++) Un[c] = Ubar[c];
         Un[5] = R(rt.z);
         st |= rt.st;
+        source3<SYS, R>(K, Un, Sn);
       }
-      source3<SYS, R>(K, Un, Sn);
+#pragma unroll
+      for (int c = 0; c < M; c++) Uo[c] = R(0);
+#pragma unroll
+      for (int q = 0; q < Q; q++) {
+        const int dir = q == 0 ? -1 : (q - 1) % 3;
+        const R akq = q == 0 ? a0 : (dir == 0 ? aj0 : (dir == 1 ? aj1 : aj2));
+#pragma unroll
+        for (int c = 0; c < M; c++) {
+          const R v = Fk[q][c] + hdt * akq * Sn[c];
+          fo[(long long)(q * M + c) * P.plane + off] = v;
+          Uo[c] += v;
+        }
+      }
     }
-    const long long off = cell3(P, i, j, k);
-    R Uo[M];
-#pragma unroll
-    for (int c = 0; c < M; c++) Uo[c] = R(0);
-#pragma unroll
-    for (int q = 0; q < Q; q++)
-#pragma unroll
-      for (int c = 0; c < M; c++) {
-        R v = Fk[q][c];
-        if constexpr (SRC) v += hdt * ak[q] * Sn[c];
-        fo[(long long)(q * M + c) * P.plane + off] = v;
-        Uo[c] += v;
-      }
     const Prim3<R> wn = prim3<SYS, R>(K, Uo);
+    sp0 = rmax(sp0, speed3<SYS, R>(K, P, wn, 0));
+    sp1 = rmax(sp1, speed3<SYS, R>(K, P, wn, 1));
+    sp2 = rmax(sp2, speed3<SYS, R>(K, P, wn, 2));
 #pragma unroll
-    for (int d = 0; d < 3; d++) sp[d] = (double)speed3<SYS, R>(K, P, wn, d);
-#pragma unroll
-    for (int c = 0; c < M; c++) usum[c] = (double)Uo[c];
+    for (int c = 0; c < M; c++) acc[c].add(Uo[c]);
     bool bad = false;
 #pragma unroll
     for (int c = 0; c < M; c++) bad |= !(Uo[c] == Uo[c]);
     if constexpr (SYS != SYS_ADV) bad |= !(wn.rho > R(0)) || !(wn.p > R(0));
     if (bad) st |= ST_NONPHYSICAL;
   }
-  // side outputs: x, y bounds, sums and status through the 2D reduction; the
-  // z bound through its own block maximum
-  block_side_outputs_to<M>(sp[0], sp[1], usum, ctl, (slot + 1) % 3, partials + bid * M, st);
-  unsigned long long* zs = &ctl->amax_z[(slot + 1) % 3];
-  block_max3_to(0.0, 0.0, sp[2], zs, zs, zs);
+  // side outputs: x, y bounds, sums and status through the fused kernels'
+  // reduction; the z bound through its own block maximum
+  fused_side_outputs_to<M, R>(sp0, sp1, acc, ctl, (slot + 1) % 3, partials + bid * M, st);
+  block_max1_to<R>(sp2, &ctl->amax_z[(slot + 1) % 3]);
   if (bid == 0 && threadIdx.x == 0) advance_ctl3(ctl, slot, cf);
 }
 
 // launch shapes of the 3D kernels
 constexpr int kBlock3 = 128;
 inline dim3 grid3_ext(int ex, int ey, int ez) { return dim3((unsigned)((ex + kBlock3 - 1) / kBlock3), ey, ez); }
-inline dim3 grid3_nodes(int nx, int ny, int nz) { return dim3((unsigned)((nx + kBlock3 - 1) / kBlock3), ny, nz); }
+inline dim3 grid3_nodes(int nx, int ny, int nz) {
+  return dim3((unsigned)((nx + kBlock3 - 1) / kBlock3), (unsigned)((ny + kRows3 - 1) / kRows3), nz);
+}
 
 }  // namespace lbmh
