@@ -24,10 +24,11 @@
  *     except where stated; lbmh_moments, lbmh_get_f, lbmh_omega and lbmh_info
  *     synchronise the stream.
  *   - A handle is not thread-safe.  Handles are independent.
- *   - Layouts: conservative state U is SoA FP64 [m][ny][nx] (x fastest);
- *     distributions f are FP64 [Q][m][ny][nx] with k = 0..2d in the order
- *     e_0 = 0, e_j = unit vector j, e_{j+d} = -e_j (Section 2.3).  In 1D,
- *     ny = 1.  Nodes sit at cell centres x_i = x0 + (i + 1/2) dx.
+ *   - Layouts: conservative state U is SoA FP64 [m][ny][nx] (x fastest;
+ *     [m][nz][ny][nx] in 3D); distributions f are FP64 [Q][m][ny][nx]
+ *     ([Q][m][nz][ny][nx] in 3D) with k = 0..2d in the order e_0 = 0,
+ *     e_j = unit vector j, e_{j+d} = -e_j (Section 2.3).  In 1D, ny = 1.
+ *     Nodes sit at cell centres x_i = x0 + (i + 1/2) dx.
  */
 #ifndef LBMH_H
 #define LBMH_H
