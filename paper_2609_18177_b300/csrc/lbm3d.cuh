@@ -449,7 +449,7 @@ constexpr int kRows3 = 8;
 // status).  Grid (ceil(nx / blockDim.x), ceil(ny / kRows3), nz): a block
 // handles kRows3 rows, so the side-output reduction is paid once per block.
 template <int SYS, class R>
-__global__ void __launch_bounds__(128) k3_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot, ExtGeom3 G,
+__global__ void __launch_bounds__(128, 6) k3_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot, ExtGeom3 G,
                                                          const R* Ue, const R* om, double* partials) {
   constexpr int M = Fields3<SYS>::M, Q = 7;
   constexpr bool SRC = SYS == SYS_REACT;

@@ -83,11 +83,25 @@ def _create(lib, pb, **kw):
     (dict(system=W.LINEAR, m_linear=2), lbmh.ERR_UNSUPPORTED),
     (dict(dim=2, nx=10, ny=10, y1=2.0), lbmh.ERR_INVALID_ARG),  # dx != dy
     (dict(gamma=1.0), lbmh.ERR_INVALID_ARG),
+    (dict(dim=4), lbmh.ERR_INVALID_ARG),
+    (dict(system=W.SWE, dim=3, nx=8, ny=8, nz=8), lbmh.ERR_UNSUPPORTED),         # 3D: no shallow water
+    (dict(dim=3, nx=8, ny=8, nz=8, bc=(W.REFLECT, W.REFLECT, 0, 0)), lbmh.ERR_UNSUPPORTED),
+    (dict(dim=3, nx=8, ny=8, nz=8, z1=2.0), lbmh.ERR_INVALID_ARG),               # dz != dx
+    (dict(nx=3, bc=(W.REFLECT, W.OUTFLOW, 0, 0)), lbmh.ERR_INVALID_ARG),         # < 4 nodes across
+    (dict(bc=(W.OUTFLOW, W.INFLOW, 0, 0), u_in=(0.0, 0.0, 0.0)), lbmh.ERR_INVALID_ARG),  # not physical
+    (dict(sponge_width=2.0), lbmh.ERR_INVALID_ARG),                                # wider than the domain
+    (dict(bc=(4, 4, 0, 0)), lbmh.ERR_INVALID_ARG),
 ])
 def test_create_rejects_invalid_problems_before_touching_the_device(lib, bad, code):
     pb = W.Problem(system=W.EULER, dim=1, nx=16).with_(**bad)
     rc, h, msg = _create(lib, pb)
     assert rc == code and not h.value and msg
+
+
+def test_3d_lattices_have_no_fused_kernel(lib):
+    pb = W.Problem(system=W.EULER, dim=3, nx=8, ny=8, nz=8)
+    rc, h, msg = _create(lib, pb, kernel=lbmh.KERNEL_FUSED)
+    assert rc == lbmh.ERR_UNSUPPORTED and not h.value and msg
 
 
 def test_null_arguments(lib):
