@@ -440,19 +440,52 @@ __device__ __forceinline__ void block_max1_to(R v, unsigned long long* d) {
   }
 }
 
-// rows (y) per block of the 3D collision kernel
-constexpr int kRows3 = 8;
+// rows (y) per block of the 3D collision kernel; lanes per block along x and
+// the output lanes among them (lane 0 and lane 127 are halo)
+constexpr int kRows3 = 16;
+constexpr int kLanes3 = 128, kOut3 = kLanes3 - 2;
 
-// K3: collision with the first half-source at x - e_k (Eq. 2.2), pull
-// streaming, the implicit moment (2.8) in FP64 and the second half-source at
-// x; writes f^{n+1}; side outputs (three speed bounds, FP64-quality sums,
-// status).  Grid (ceil(nx / blockDim.x), ceil(ny / kRows3), nz): a block
-// handles kRows3 rows, so the side-output reduction is paid once per block.
+// post-collision value of direction q at a node with state U, relaxation w
+// and distributions fq[M] of that direction (Eq. 2.2 with half the source)
 template <int SYS, class R>
-__global__ void __launch_bounds__(128, 6) k3_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot, ExtGeom3 G,
-                                                         const R* Ue, const R* om, double* partials) {
+__device__ __forceinline__ void post_dir(const Phys<R>& K, const DevParams& P, const R* U, R w, const R* fq, int q,
+                                         R a0, R alq, R akq, R inv2l, R hdt, R* out) {
+  constexpr int M = Fields3<SYS>::M;
+  R F[M];
+#pragma unroll
+  for (int c = 0; c < M; c++) F[c] = R(0);
+  if (q != 0) {
+    const Prim3<R> pw = prim3<SYS, R>(K, U);
+    flux3<SYS, R>(K, P, U, pw, (q - 1) % 3, F);
+  }
+  R S[M];
+  if constexpr (SYS == SYS_REACT) source3<SYS, R>(K, U, S);
+#pragma unroll
+  for (int c = 0; c < M; c++) {
+    const R feq = q == 0 ? a0 * U[c] : (q <= 3 ? (alq * U[c] + F[c]) * inv2l : (alq * U[c] - F[c]) * inv2l);
+    R v = fq[c] - w * (fq[c] - feq);
+    if constexpr (SYS == SYS_REACT) v += hdt * akq * S[c];
+    out[c] = v;
+  }
+}
+
+// K3: collision with the first half-source (Eq. 2.2), pull streaming, the
+// implicit moment (2.8) in FP64 and the second half-source; writes f^{n+1};
+// side outputs (three speed bounds, FP64-quality sums, status).
+//
+// Grid (ceil(nx / 126), ceil(ny / kRows3), nz), 128 lanes along x (lane t at
+// x = 126 bx - 1 + t).  A block marches its rows in y: at row r every lane
+// computes its own post-collision values for e_0, +-x, +-y once; the +-x
+// values pass to the neighbouring lanes through shared memory, the +-y values
+// stay in the lane's registers for rows r +- 1, and row r - 1 is streamed.
+// The +-z values come from the planes k -+ 1 and are computed on the fly
+// (one direction each).
+template <int SYS, class R>
+__global__ void __launch_bounds__(kLanes3) k3_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
+                                                             ExtGeom3 G, const R* Ue, const R* om, double* partials) {
   constexpr int M = Fields3<SYS>::M, Q = 7;
   constexpr bool SRC = SYS == SYS_REACT;
+  __shared__ R sx[3][2][M][kLanes3];  // post_{+x}, post_{-x} of three rows (ring)
   const StepCoef3 cf = step_coef3(P, ctl, slot);
   const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   if (!cf.active) {
@@ -462,104 +495,134 @@ __global__ void __launch_bounds__(128, 6) k3_collide_stream(DevParams P, R* cons
   const R* f = buf[ctl->parity[slot]];
   R* fo = buf[ctl->parity[slot] ^ 1];
   const long long n = (long long)G.ex * G.ey * G.ez;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.z;
+  const int t = threadIdx.x;
+  const int i = blockIdx.x * kOut3 - 1 + t, k = blockIdx.z;
+  const bool out_lane = t >= 1 && t <= kOut3 && i < P.nx;
+  const bool halo_or_out = i <= P.nx;  // lanes past x = nx are never read (and lie outside the extension)
+  const int mi = map_index(i, P.nx, P.bc[0], P.bc[1]);
+  const int mkm = map_index(k - 1, P.nz3, P.bc_z[0], P.bc_z[1]), mkp = map_index(k + 1, P.nz3, P.bc_z[0], P.bc_z[1]);
   const Phys<R> K = make_phys<R>(P);
   const R a0 = R(cf.a0), inv2l = R(1.0 / (2.0 * cf.lam)), hdt = R(0.5 * cf.dt);
-  const R al0 = R(cf.alpha[0]), al1 = R(cf.alpha[1]), al2 = R(cf.alpha[2]);
-  const R aj0 = R(cf.aj[0]), aj1 = R(cf.aj[1]), aj2 = R(cf.aj[2]);
+  const R al[3] = {R(cf.alpha[0]), R(cf.alpha[1]), R(cf.alpha[2])};
+  const R aj[3] = {R(cf.aj[0]), R(cf.aj[1]), R(cf.aj[2])};
   R sp0 = R(0), sp1 = R(0), sp2 = R(0);
   Acc<R> acc[M];
 #pragma unroll
   for (int c = 0; c < M; c++) acc[c].init();
   unsigned st = 0u;
   const int j0 = blockIdx.y * kRows3, j1 = min(j0 + kRows3, P.ny3);
-  for (int j = j0; j < j1 && i < P.nx; j++) {
-    R Fk[SRC ? Q : 1][M];
-    R Ubar[M];
+  // lane registers: post_0 and post_{+y} of row r-1, post_{+y} of row r-2
+  R p0_prev[M], py_prev[M], py_prev2[M];
 #pragma unroll
-    for (int c = 0; c < M; c++) Ubar[c] = R(0);
-    const long long off = cell3(P, i, j, k);
+  for (int c = 0; c < M; c++) p0_prev[c] = py_prev[c] = py_prev2[c] = R(0);
+  for (int r = j0 - 1; r <= j1; r++) {
+    // own post-collision values of row r (ghost rows: the mapped node, A6)
+    const long long e = G.idx(k + GH, r + GH, i + GH);
+    const long long off = cell3(P, mi, map_index(r, P.ny3, P.bc[2], P.bc[3]), k);
+    R U[M], fq[M], p0[M], ppx[M], pmx[M], ppy[M], pmy[M];
 #pragma unroll
-    for (int q = 0; q < Q; q++) {
-      // post_q at x - e_q (q = 1..3: +unit vector q-1; q = 4..6: -unit vector q-4)
-      const int dir = q == 0 ? -1 : (q - 1) % 3;
-      const int sg = q <= 3 ? -1 : 1;
-      const int si = i + (dir == 0 ? sg : 0), sj = j + (dir == 1 ? sg : 0), sk = k + (dir == 2 ? sg : 0);
-      const long long es = G.idx(sk + GH, sj + GH, si + GH);
-      const long long soff = cell3(P, map_index(si, P.nx, P.bc[0], P.bc[1]), map_index(sj, P.ny3, P.bc[2], P.bc[3]),
-                                   map_index(sk, P.nz3, P.bc_z[0], P.bc_z[1]));
-      R U[M];
+    for (int c = 0; c < M; c++) U[c] = halo_or_out ? Ue[(long long)c * n + e] : R(1);
+    const R w = halo_or_out ? om[e] : R(1);
 #pragma unroll
-      for (int c = 0; c < M; c++) U[c] = Ue[(long long)c * n + es];
-      R F[M];
+    for (int q = 0; q < 5; q++) {
+      const int qq = q == 0 ? 0 : (q == 1 ? 1 : (q == 2 ? 4 : (q == 3 ? 2 : 5)));  // 0, +x, -x, +y, -y
+      const int dir = qq == 0 ? 0 : (qq - 1) % 3;
 #pragma unroll
-      for (int c = 0; c < M; c++) F[c] = R(0);
-      if (q != 0) {
-        const Prim3<R> w = prim3<SYS, R>(K, U);
-        flux3<SYS, R>(K, P, U, w, dir, F);
-      }
-      R S[M];
-      if constexpr (SRC) source3<SYS, R>(K, U, S);
-      const R w_om = om[es];
-      const R alq = dir == 0 ? al0 : (dir == 1 ? al1 : al2);
-      const R akq = q == 0 ? a0 : (dir == 0 ? aj0 : (dir == 1 ? aj1 : aj2));
+      for (int c = 0; c < M; c++) fq[c] = halo_or_out ? f[(long long)(qq * M + c) * P.plane + off] : R(0);
+      R* o = q == 0 ? p0 : (q == 1 ? ppx : (q == 2 ? pmx : (q == 3 ? ppy : pmy)));
+      post_dir<SYS, R>(K, P, U, w, fq, qq, a0, al[dir], qq == 0 ? a0 : aj[dir], inv2l, hdt, o);
+    }
+    const int slot3 = (r - j0 + 3) % 3;
+#pragma unroll
+    for (int c = 0; c < M; c++) {
+      sx[slot3][0][c][t] = ppx[c];
+      sx[slot3][1][c][t] = pmx[c];
+    }
+    __syncthreads();
+    const int y = r - 1;
+    if (y >= j0 && y < j1 && out_lane) {
+      const int ps = (r - 1 - j0 + 3) % 3;
+      R Fk[Q][M];
 #pragma unroll
       for (int c = 0; c < M; c++) {
-        const R feq = q == 0 ? a0 * U[c] : (q <= 3 ? (alq * U[c] + F[c]) * inv2l : (alq * U[c] - F[c]) * inv2l);
-        const R fq = f[(long long)(q * M + c) * P.plane + soff];
-        R v = fq - w_om * (fq - feq);
-        if constexpr (SRC) {
-          v += hdt * akq * S[c];
-          Fk[q][c] = v;
-        } else {
-          fo[(long long)(q * M + c) * P.plane + off] = v;  // no source: F_q is final
-        }
-        Ubar[c] += v;
+        Fk[0][c] = p0_prev[c];
+        Fk[1][c] = sx[ps][0][c][t - 1];  // F_{+x}(x) = post_{+x}(x - e_x)
+        Fk[4][c] = sx[ps][1][c][t + 1];  // F_{-x}(x) = post_{-x}(x + e_x)
+        Fk[2][c] = py_prev2[c];          // post_{+y} of row y - 1
+        Fk[5][c] = pmy[c];               // post_{-y} of row y + 1
       }
-    }
-    R Uo[M];
+      // +-z: post_{+z} at plane k - 1, post_{-z} at plane k + 1
+      const int my = map_index(y, P.ny3, P.bc[2], P.bc[3]);
 #pragma unroll
-    for (int c = 0; c < M; c++) Uo[c] = Ubar[c];
-    if constexpr (SRC) {
+      for (int s2 = 0; s2 < 2; s2++) {
+        const int kk = s2 == 0 ? k - 1 : k + 1, qq = s2 == 0 ? 3 : 6;
+        const long long ez = G.idx(kk + GH, y + GH, i + GH);
+        const long long offz = cell3(P, mi, my, s2 == 0 ? mkm : mkp);
+        R Uz[M], fz[M];
+#pragma unroll
+        for (int c = 0; c < M; c++) {
+          Uz[c] = Ue[(long long)c * n + ez];
+          fz[c] = f[(long long)(qq * M + c) * P.plane + offz];
+        }
+        post_dir<SYS, R>(K, P, Uz, om[ez], fz, qq, a0, al[2], aj[2], inv2l, hdt, Fk[qq]);
+      }
+      R Ubar[M];
+#pragma unroll
+      for (int c = 0; c < M; c++) {
+        R sum = R(0);
+#pragma unroll
+        for (int q = 0; q < Q; q++) sum += Fk[q][c];
+        Ubar[c] = sum;
+      }
       R Sn[M];
 #pragma unroll
       for (int c = 0; c < M; c++) Sn[c] = R(0);
-      if (K.react && Ubar[5] != R(0)) {
-        const double mx = (double)Ubar[1], my = (double)Ubar[2], mz = (double)Ubar[3];
-        const RootF64 rt = react_root_f64((double)Ubar[0], mx * mx + my * my + mz * mz, (double)Ubar[4],
-                                          (double)Ubar[5], 0.5 * cf.dt * K.K, K.gamma_d - 1.0, K.q_d, K.Ti);
-        R Un[M];
+      if constexpr (SRC) {
+        if (K.react && Ubar[5] != R(0)) {
+          const double mx = (double)Ubar[1], my2 = (double)Ubar[2], mz = (double)Ubar[3];
+          const RootF64 rt = react_root_f64((double)Ubar[0], mx * mx + my2 * my2 + mz * mz, (double)Ubar[4],
+                                            (double)Ubar[5], 0.5 * cf.dt * K.K, K.gamma_d - 1.0, K.q_d, K.Ti);
+          R Un[M];
 #pragma unroll
-        for (int c = 0; c < M; c++) Un[c] = Ubar[c];
-        Un[5] = R(rt.z);
-        st |= rt.st;
-        source3<SYS, R>(K, Un, Sn);
+          for (int c = 0; c < M; c++) Un[c] = Ubar[c];
+          Un[5] = R(rt.z);
+          st |= rt.st;
+          source3<SYS, R>(K, Un, Sn);
+        }
       }
+      const long long oo = cell3(P, i, y, k);
+      R Uo[M];
 #pragma unroll
       for (int c = 0; c < M; c++) Uo[c] = R(0);
 #pragma unroll
       for (int q = 0; q < Q; q++) {
-        const int dir = q == 0 ? -1 : (q - 1) % 3;
-        const R akq = q == 0 ? a0 : (dir == 0 ? aj0 : (dir == 1 ? aj1 : aj2));
+        const R akq = q == 0 ? a0 : aj[(q - 1) % 3];
 #pragma unroll
         for (int c = 0; c < M; c++) {
-          const R v = Fk[q][c] + hdt * akq * Sn[c];
-          fo[(long long)(q * M + c) * P.plane + off] = v;
+          R v = Fk[q][c];
+          if constexpr (SRC) v += hdt * akq * Sn[c];
+          fo[(long long)(q * M + c) * P.plane + oo] = v;
           Uo[c] += v;
         }
       }
+      const Prim3<R> wn = prim3<SYS, R>(K, Uo);
+      sp0 = rmax(sp0, speed3<SYS, R>(K, P, wn, 0));
+      sp1 = rmax(sp1, speed3<SYS, R>(K, P, wn, 1));
+      sp2 = rmax(sp2, speed3<SYS, R>(K, P, wn, 2));
+#pragma unroll
+      for (int c = 0; c < M; c++) acc[c].add(Uo[c]);
+      bool bad = false;
+#pragma unroll
+      for (int c = 0; c < M; c++) bad |= !(Uo[c] == Uo[c]);
+      if constexpr (SYS != SYS_ADV) bad |= !(wn.rho > R(0)) || !(wn.p > R(0));
+      if (bad) st |= ST_NONPHYSICAL;
     }
-    const Prim3<R> wn = prim3<SYS, R>(K, Uo);
-    sp0 = rmax(sp0, speed3<SYS, R>(K, P, wn, 0));
-    sp1 = rmax(sp1, speed3<SYS, R>(K, P, wn, 1));
-    sp2 = rmax(sp2, speed3<SYS, R>(K, P, wn, 2));
 #pragma unroll
-    for (int c = 0; c < M; c++) acc[c].add(Uo[c]);
-    bool bad = false;
-#pragma unroll
-    for (int c = 0; c < M; c++) bad |= !(Uo[c] == Uo[c]);
-    if constexpr (SYS != SYS_ADV) bad |= !(wn.rho > R(0)) || !(wn.p > R(0));
-    if (bad) st |= ST_NONPHYSICAL;
+    for (int c = 0; c < M; c++) {
+      py_prev2[c] = py_prev[c];
+      py_prev[c] = ppy[c];
+      p0_prev[c] = p0[c];
+    }
   }
   // side outputs: x, y bounds, sums and status through the fused kernels'
   // reduction; the z bound through its own block maximum
@@ -572,7 +635,7 @@ __global__ void __launch_bounds__(128, 6) k3_collide_stream(DevParams P, R* cons
 constexpr int kBlock3 = 128;
 inline dim3 grid3_ext(int ex, int ey, int ez) { return dim3((unsigned)((ex + kBlock3 - 1) / kBlock3), ey, ez); }
 inline dim3 grid3_nodes(int nx, int ny, int nz) {
-  return dim3((unsigned)((nx + kBlock3 - 1) / kBlock3), (unsigned)((ny + kRows3 - 1) / kRows3), nz);
+  return dim3((unsigned)((nx + kOut3 - 1) / kOut3), (unsigned)((ny + kRows3 - 1) / kRows3), nz);
 }
 
 }  // namespace lbmh
