@@ -289,8 +289,8 @@ __device__ __forceinline__ void source(const Phys<R>& K, const R* U, R xr, R yr,
 
 // FP32 root of g(z) = z - zbar + dt/2 K z exp(-Ti/T(z)) (see implicit_moment):
 // the same safeguarded Newton iteration in FP32, stopped when the Newton step
-// falls below 2^-22 |zbar| (about two FP32 ulps of zbar; the iterate is then
-// rounded to FP32 storage anyway).  Returns 0 (converged), 1 (no convergence
+// falls below max(2^-22 |zbar|, 2^-126) (about two FP32 ulps of zbar, or the
+// smallest normal float; the iterate is then rounded to FP32 storage anyway).  Returns 0 (converged), 1 (no convergence
 // in 30 iterations: the caller solves in FP64) or 2 (non-finite state: no
 // root is sought).
 template <int D>
@@ -305,7 +305,11 @@ __device__ __forceinline__ int react_root_f32(const Phys<float>& K, const float*
   float lo = zbar < 0.0f ? zbar : 0.0f, hi = zbar < 0.0f ? 0.0f : zbar;
   float z = fdiv(zbar, 1.0f + hk * expf(-fdiv(K.Tir, e0 + dTdz * zbar)));
   if (!(fabsf(z) <= 3.0e38f)) return 2;
-  const float tol = 0x1p-22f * fabsf(zbar);
+  // two FP32 ulps of zbar, but no less than the smallest normal float: once
+  // zbar is subnormal (a burnt region decays geometrically towards 0) the
+  // relative step underflows, the iteration alternates between neighbouring
+  // subnormals, and only the absolute floor ends it (an error < 2^-126 in z)
+  const float tol = fmaxf(0x1p-22f * fabsf(zbar), 0x1p-126f);
   for (int it = 0; it < 30; it++) {
     const float T = e0 + dTdz * z;
     const float a = fdiv(K.Tir, T);
@@ -336,7 +340,7 @@ struct RootF64 {
 // FP64 root of g(z) = z - zbar + hk z exp(-Ti/T(z)), T(z) = e0 + dTdz z,
 // hk = dt/2 K (see implicit_moment): Newton from the frozen-temperature guess,
 // safeguarded by bisection on the bracket between 0 and zbar, until the step
-// is below 1e-15 |zbar|.  A non-finite state returns z = zbar with ST_NOROOT.
+// is below max(1e-15 |zbar|, 2^-1022).  A non-finite state returns z = zbar with ST_NOROOT.
 __device__ __forceinline__ RootF64 react_root_f64(double rho, double momsq, double E, double zbar, double hk,
                                                   double gm1, double q, double Ti) {
   const double dTdz = -gm1 * q / rho;
@@ -355,7 +359,9 @@ __device__ __forceinline__ RootF64 react_root_f64(double rho, double momsq, doub
     // converged when the Newton step is below the tolerance; tested before
     // the bracket guard, since z itself has just become a bracket end and a
     // sub-resolution step lands on it
-    if (fabs(zn - z) <= 1e-15 * fabs(zbar)) return RootF64{zn, 0u};
+    // (the absolute floor, the smallest normal double, ends the iteration
+    // for a subnormal zbar as in the FP32 root)
+    if (fabs(zn - z) <= fmax(1e-15 * fabs(zbar), 0x1p-1022)) return RootF64{zn, 0u};
     if (!(zn > lo && zn < hi)) zn = 0.5 * (lo + hi);
     z = zn;
   }

@@ -98,10 +98,19 @@ class Server:
 
     def run(self, trace: List[Request], inputs: Optional[Dict[int, tuple]] = None, max_seconds=1e9):
         """Serve `trace` in real time; `inputs` may hold pre-built (problem, U0)
-        per request id.  Returns the list of results and summary statistics."""
+        per request id.  Returns the list of results and summary statistics.
+
+        Each system's batch runs its own cycle: when its previous chunk of
+        steps has finished on its stream (a CUDA event, polled without
+        blocking), finished lattices are harvested and removed, waiting
+        requests admitted, and the next chunk launched.  The batches do not
+        wait for one another, so a system with heavier steps does not hold the
+        others idle."""
+        torch = self.torch
         pending = sorted(trace, key=lambda r: r.arrival)
         queue: Dict[str, List[Request]] = {k: [] for k in KINDS}
         live: Dict[str, Dict[int, tuple]] = {k: {} for k in KINDS}  # slot -> (request, admitted time)
+        inflight: Dict[str, Optional[object]] = {k: None for k in KINDS}  # event of the launched chunk
         results: List[Result] = []
         node_steps = 0
         deferred = set()  # requests refused admission at least once (arena full)
@@ -112,8 +121,26 @@ class Server:
             while nxt < len(pending) and pending[nxt].arrival <= now:
                 queue[pending[nxt].kind].append(pending[nxt])
                 nxt += 1
-            # admission: first fit by footprint, in arrival order
+            progressed = False
             for k in KINDS:
+                ev = inflight[k]
+                if ev is not None:
+                    if not ev.query():
+                        continue  # this batch is still stepping
+                    inflight[k] = None
+                    progressed = True
+                    # harvest finished lattices
+                    done, t, steps, status = self.batches[k].poll()
+                    for slot in list(live[k].keys()):
+                        if done[slot] == 1:
+                            req, adm = live[k].pop(slot)
+                            U = self.batches[k].moments(slot)
+                            fin = time.perf_counter() - t0
+                            self.batches[k].remove(slot)
+                            node_steps += req.n * req.n * int(steps[slot])
+                            results.append(Result(req.rid, k, req.n, int(steps[slot]), req.arrival, adm, fin,
+                                                  U if self.keep_results else None))
+                # the batch is idle: admit (first fit by footprint, in arrival order)
                 kept = []
                 for req in queue[k]:
                     pb, U0 = inputs[req.rid] if inputs and req.rid in inputs else make_problem(req)
@@ -123,34 +150,31 @@ class Server:
                         deferred.add(req.rid)
                     else:
                         live[k][slot] = (req, time.perf_counter() - t0)
+                        progressed = True
                 queue[k] = kept
-            active = [k for k in KINDS if live[k]]
-            if not active:
+                if live[k]:
+                    if self.autotune and k not in self.tuned and len(live[k]) >= 2:
+                        self.batches[k].autotune(steps_per_candidate=2)
+                        self.tuned.add(k)
+                    self.batches[k].step(self.chunk)
+                    ev = torch.cuda.Event()
+                    ev.record(self.streams[k])
+                    inflight[k] = ev
+                    progressed = True
+            if not any(live.values()) and all(e is None for e in inflight.values()):
                 if nxt >= len(pending) and not any(queue.values()):
                     break
-                if nxt < len(pending):
-                    time.sleep(max(0.0, min(0.01, pending[nxt].arrival - (time.perf_counter() - t0))))
-                continue
-            # one chunk of steps on every live batch, the three streams overlapping
-            for k in active:
-                if self.autotune and k not in self.tuned and len(live[k]) >= 2:
-                    self.batches[k].autotune(steps_per_candidate=2)
-                    self.tuned.add(k)
-                self.batches[k].step(self.chunk)
-            # harvest finished lattices
-            for k in active:
-                done, t, steps, status = self.batches[k].poll()
-                for slot in list(live[k].keys()):
-                    if done[slot] == 1:
-                        req, adm = live[k].pop(slot)
-                        U = self.batches[k].moments(slot)
-                        fin = time.perf_counter() - t0
-                        self.batches[k].remove(slot)
-                        node_steps += req.n * req.n * int(steps[slot])
-                        results.append(Result(req.rid, k, req.n, int(steps[slot]), req.arrival, adm, fin,
-                                              U if self.keep_results else None))
             if time.perf_counter() - t0 > max_seconds:
                 break
+            if not progressed:
+                # nothing finished and nothing arrived: wait briefly
+                wait = 0.0005
+                if nxt < len(pending):
+                    wait = min(wait, max(0.0, pending[nxt].arrival - (time.perf_counter() - t0)))
+                time.sleep(wait)
+        for k in KINDS:
+            if inflight[k] is not None:
+                inflight[k].synchronize()
         makespan = time.perf_counter() - t0
         lat = np.array([r.latency for r in results]) if results else np.zeros(1)
         stats = {

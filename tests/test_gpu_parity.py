@@ -260,3 +260,53 @@ def test_nonphysical_state_is_reported():
         s.moments()
     assert ei.value.code == lbmh.ERR_NONPHYSICAL
     assert s.info()["status"] & 1
+
+
+def _ms_per_step(s, n=20, reps=3):
+    import torch
+    best = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        s.step(n)
+        e1.record()
+        torch.cuda.synchronize()
+        best.append(e0.elapsed_time(e1) / n)
+    return float(np.median(best))
+
+
+def test_fp32_root_on_subnormal_mass_fraction():
+    """A burnt region: rho*Y decays geometrically towards 0 and reaches the FP32
+    subnormal range after ~10^3 steps of Example 5.12.  There the FP32 Arrhenius
+    root has to stop on its absolute floor: it may not fall back to FP64 on
+    every node (which made such steps ~4x slower), it reports no root failure,
+    and rho, momentum and energy match the FP64 path."""
+    n = 1024
+    pb, _ = W.reactive_circle(n)
+    X, Y = W.cell_centres(pb)
+    rho = 1.0 + 0.05 * np.sin(np.pi * X) * np.sin(np.pi * Y)
+    hot = 60.0  # p = 60: T ~ 60, exp(-Ti/T) ~ 0.43, a fast reaction
+
+    def state(rhoY):
+        return W.euler_conservative(pb, rho, 0.0, hot, v=0.0, Y=rhoY / rho)
+
+    ms = {}
+    for rhoY in (1e-20, 1e-40):
+        s = lbmh.Solver(pb, precision=lbmh.FP32, kernel=lbmh.KERNEL_FUSED).set_state(state(rhoY))
+        s.step(3)
+        ms[rhoY] = _ms_per_step(s)
+        U32 = s.moments()
+        assert not (s.info()["status"] & 2), "root failure on a burnt state"
+        s64 = lbmh.Solver(pb, precision=lbmh.FP64).set_state(state(rhoY)).step(s.nsteps)
+        U64 = s64.moments()
+        # density and energy: relative L1; momentum (zero in exact arithmetic:
+        # the state is at rest in pressure equilibrium) against the acoustic
+        # scale rho c
+        assert np.all(rel_l1(U32[[0, 3]], U64[[0, 3]]) <= FP32_L1)
+        rho_c = np.sum(U64[0] * np.sqrt(pb.gamma * hot / U64[0]))
+        assert np.all(np.abs(U32[1:3] - U64[1:3]).sum(axis=(1, 2)) <= FP32_L1 * rho_c)
+        assert np.abs(U32[4]).max() <= 2.0 * rhoY
+        s.close()
+        s64.close()
+    assert ms[1e-40] <= 1.5 * ms[1e-20], ms
