@@ -406,7 +406,8 @@ __global__ void k3_omega(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, cons
   om[e] = w;
 }
 
-// source of the 3D systems: Arrhenius on rho*Y (reactive, FP64), none otherwise
+// source of the 3D systems: Arrhenius on rho*Y (reactive; FP64 in the FP64
+// mode, FP32 in the FP32 mode, as in 1D and 2D), none otherwise
 template <int SYS, class R>
 __device__ __forceinline__ void source3(const Phys<R>& K, const R* U, R* S) {
   constexpr int M = Fields3<SYS>::M;
@@ -414,9 +415,52 @@ __device__ __forceinline__ void source3(const Phys<R>& K, const R* U, R* S) {
   for (int c = 0; c < M; c++) S[c] = R(0);
   if constexpr (SYS == SYS_REACT) {
     if (K.react) {
-      const double momsq = (double)U[1] * U[1] + (double)U[2] * U[2] + (double)U[3] * U[3];
-      S[5] = R(-arrhenius(K, (double)U[0], momsq, (double)U[4], (double)U[5]));
+      if constexpr (sizeof(R) == 4) {
+        S[5] = -arrhenius_f32(K, U[0], U[1] * U[1] + U[2] * U[2] + U[3] * U[3], U[4], U[5]);
+      } else {
+        const double momsq = (double)U[1] * U[1] + (double)U[2] * U[2] + (double)U[3] * U[3];
+        S[5] = R(-arrhenius(K, (double)U[0], momsq, (double)U[4], (double)U[5]));
+      }
     }
+  }
+}
+
+// The FP32 mode's FP64 fallback of the 3D root, out of line like the 2D one.
+static __device__ __noinline__ RootF64 react_root3_f64_fallback(float rho, float m1, float m2, float m3, float E,
+                                                                float zbar, double dt, double Kc, double gamma,
+                                                                double q, double Ti) {
+  const double d1 = (double)m1, d2 = (double)m2, d3 = (double)m3;
+  return react_root_f64((double)rho, d1 * d1 + d2 * d2 + d3 * d3, (double)E, (double)zbar, 0.5 * dt * Kc,
+                        gamma - 1.0, q, Ti);
+}
+
+// Eq. (2.8) for rho*Y in 3D: the root z of g(z) = z - zbar + dt/2 R(z).  FP64
+// in the FP64 mode; in the FP32 mode FP32 first and FP64 where the FP32
+// iteration does not converge.  Returns status bits; z = zbar where no root
+// is sought.
+template <class R>
+__device__ __forceinline__ unsigned react_implicit3(const Phys<R>& K, const R* Ubar, double dt, R hdt, R* z) {
+  if constexpr (sizeof(R) == 4) {
+    float zf;
+    const int rc = react_root_f32<3>(K, Ubar, hdt, &zf);
+    if (rc == 0) {
+      *z = zf;
+      return 0u;
+    }
+    if (rc == 2) {
+      *z = Ubar[5];
+      return ST_NOROOT;
+    }
+    const RootF64 rt = react_root3_f64_fallback(Ubar[0], Ubar[1], Ubar[2], Ubar[3], Ubar[4], Ubar[5], dt, K.K,
+                                                K.gamma_d, K.q_d, K.Ti);
+    *z = R(rt.z);
+    return rt.st;
+  } else {
+    const double mx = (double)Ubar[1], my = (double)Ubar[2], mz = (double)Ubar[3];
+    const RootF64 rt = react_root_f64((double)Ubar[0], mx * mx + my * my + mz * mz, (double)Ubar[4], (double)Ubar[5],
+                                      0.5 * dt * K.K, K.gamma_d - 1.0, K.q_d, K.Ti);
+    *z = R(rt.z);
+    return rt.st;
   }
 }
 
@@ -440,26 +484,35 @@ __device__ __forceinline__ void block_max1_to(R v, unsigned long long* d) {
   }
 }
 
-// rows (y) per block of the 3D collision kernel; lanes per block along x and
-// the output lanes among them (lane 0 and lane 127 are halo)
+// rows (y) per block of the 3D collision kernel; threads per block, and the
+// x nodes a block writes: each warp owns a 32-lane segment along x whose
+// lanes 1..30 are written (lanes 0 and 31 are halo)
 constexpr int kRows3 = 16;
-constexpr int kLanes3 = 128, kOut3 = kLanes3 - 2;
+constexpr int kLanes3 = 128, kSeg3 = 30, kOut3 = (kLanes3 / 32) * kSeg3;
 
-// post-collision value of direction q at a node with state U, relaxation w
-// and distributions fq[M] of that direction (Eq. 2.2 with half the source)
+// launch shape of the collision kernel per system and precision: resident
+// blocks per SM (4, at most 128 registers a thread, for FP32 advection and
+// Euler; 2 for reactive Euler and FP64) and whether operands are loaded one
+// row ahead.  FP64 (bound by the FP64 pipe) loads them where they
+// are used: prefetched doubles would spill.
 template <int SYS, class R>
-__device__ __forceinline__ void post_dir(const Phys<R>& K, const DevParams& P, const R* U, R w, const R* fq, int q,
-                                         R a0, R alq, R akq, R inv2l, R hdt, R* out) {
+struct K3Occupancy {
+  static constexpr bool prefetch = sizeof(R) == 4;
+  static constexpr int blocks = (sizeof(R) == 8 || SYS == SYS_REACT) ? 2 : 4;
+};
+
+// post-collision value of direction q at a node with state U (primitives pw,
+// source S), relaxation w and distributions fq[M] of that direction (Eq. 2.2
+// with half the source)
+template <int SYS, class R>
+__device__ __forceinline__ void post_q(const Phys<R>& K, const DevParams& P, const R* U, const Prim3<R>& pw,
+                                       const R* S, R w, const R* fq, int q, R a0, R alq, R akq, R inv2l, R hdt,
+                                       R* out) {
   constexpr int M = Fields3<SYS>::M;
   R F[M];
 #pragma unroll
   for (int c = 0; c < M; c++) F[c] = R(0);
-  if (q != 0) {
-    const Prim3<R> pw = prim3<SYS, R>(K, U);
-    flux3<SYS, R>(K, P, U, pw, (q - 1) % 3, F);
-  }
-  R S[M];
-  if constexpr (SYS == SYS_REACT) source3<SYS, R>(K, U, S);
+  if (q != 0) flux3<SYS, R>(K, P, U, pw, (q - 1) % 3, F);
 #pragma unroll
   for (int c = 0; c < M; c++) {
     const R feq = q == 0 ? a0 * U[c] : (q <= 3 ? (alq * U[c] + F[c]) * inv2l : (alq * U[c] - F[c]) * inv2l);
@@ -470,22 +523,29 @@ __device__ __forceinline__ void post_dir(const Phys<R>& K, const DevParams& P, c
 }
 
 // K3: collision with the first half-source (Eq. 2.2), pull streaming, the
-// implicit moment (2.8) in FP64 and the second half-source; writes f^{n+1};
-// side outputs (three speed bounds, FP64-quality sums, status).
+// implicit moment (2.8) and the second half-source; writes f^{n+1}; side
+// outputs (three speed bounds, FP64-quality sums, status).
 //
-// Grid (ceil(nx / 126), ceil(ny / kRows3), nz), 128 lanes along x (lane t at
-// x = 126 bx - 1 + t).  A block marches its rows in y: at row r every lane
-// computes its own post-collision values for e_0, +-x, +-y once; the +-x
-// values pass to the neighbouring lanes through shared memory, the +-y values
-// stay in the lane's registers for rows r +- 1, and row r - 1 is streamed.
-// The +-z values come from the planes k -+ 1 and are computed on the fly
-// (one direction each).
+// Grid (ceil(nx / 120), ceil(ny / kRows3), nz), 128 threads: warp w of block
+// bx is a 32-lane segment along x (lane l at x = 120 bx + 30 w - 1 + l) that
+// marches the block's rows in y by itself, with no block barrier.  At row r
+// every lane computes its own post-collision values for e_0, +-x, +-y once
+// (primitives and source once per node); the +-x values pass to the
+// neighbouring lanes by warp shuffles, the +-y values stay in the lane's
+// registers for rows r +- 1, and row r - 1 is streamed.  The +-z values come
+// from the planes k -+ 1 and are computed on the fly (one direction each).
+// In FP32 loads run one row ahead: the own operands of row r + 1 are issued
+// as soon as row r's posts are formed, the +-z operands of row r once row
+// r - 1 is written, so each row waits on one memory latency, already
+// overlapped with the other phase.  The prefetched operands cost registers: resident blocks
+// per SM are set per system and precision (K3Occupancy) so that no instance
+// spills.
 template <int SYS, class R>
-__global__ void __launch_bounds__(kLanes3) k3_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
-                                                             ExtGeom3 G, const R* Ue, const R* om, double* partials) {
+__global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks)) k3_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
+                                                                ExtGeom3 G, const R* Ue, const R* om,
+                                                                double* partials) {
   constexpr int M = Fields3<SYS>::M, Q = 7;
   constexpr bool SRC = SYS == SYS_REACT;
-  __shared__ R sx[3][2][M][kLanes3];  // post_{+x}, post_{-x} of three rows (ring)
   const StepCoef3 cf = step_coef3(P, ctl, slot);
   const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   if (!cf.active) {
@@ -495,9 +555,9 @@ __global__ void __launch_bounds__(kLanes3) k3_collide_stream(DevParams P, R* con
   const R* f = buf[ctl->parity[slot]];
   R* fo = buf[ctl->parity[slot] ^ 1];
   const long long n = (long long)G.ex * G.ey * G.ez;
-  const int t = threadIdx.x;
-  const int i = blockIdx.x * kOut3 - 1 + t, k = blockIdx.z;
-  const bool out_lane = t >= 1 && t <= kOut3 && i < P.nx;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * kOut3 + w * kSeg3 - 1 + lane, k = blockIdx.z;
+  const bool out_lane = lane >= 1 && lane <= kSeg3 && i < P.nx;
   const bool halo_or_out = i <= P.nx;  // lanes past x = nx are never read (and lie outside the extension)
   const int mi = map_index(i, P.nx, P.bc[0], P.bc[1]);
   const int mkm = map_index(k - 1, P.nz3, P.bc_z[0], P.bc_z[1]), mkp = map_index(k + 1, P.nz3, P.bc_z[0], P.bc_z[1]);
@@ -511,60 +571,96 @@ __global__ void __launch_bounds__(kLanes3) k3_collide_stream(DevParams P, R* con
   for (int c = 0; c < M; c++) acc[c].init();
   unsigned st = 0u;
   const int j0 = blockIdx.y * kRows3, j1 = min(j0 + kRows3, P.ny3);
-  // lane registers: post_0 and post_{+y} of row r-1, post_{+y} of row r-2
-  R p0_prev[M], py_prev[M], py_prev2[M];
-#pragma unroll
-  for (int c = 0; c < M; c++) p0_prev[c] = py_prev[c] = py_prev2[c] = R(0);
-  for (int r = j0 - 1; r <= j1; r++) {
-    // own post-collision values of row r (ghost rows: the mapped node, A6)
+  // own operands of a row (U, omega, f of e_0, +x, -x, +y, -y at the lane's
+  // node; ghost rows: the mapped node, A6), loaded one row ahead
+  R oU[M], ow, of[5][M];
+  auto load_own = [&](int r) {
     const long long e = G.idx(k + GH, r + GH, i + GH);
     const long long off = cell3(P, mi, map_index(r, P.ny3, P.bc[2], P.bc[3]), k);
-    R U[M], fq[M], p0[M], ppx[M], pmx[M], ppy[M], pmy[M];
 #pragma unroll
-    for (int c = 0; c < M; c++) U[c] = halo_or_out ? Ue[(long long)c * n + e] : R(1);
-    const R w = halo_or_out ? om[e] : R(1);
+    for (int c = 0; c < M; c++) oU[c] = halo_or_out ? Ue[(long long)c * n + e] : R(1);
+    ow = halo_or_out ? om[e] : R(1);
 #pragma unroll
     for (int q = 0; q < 5; q++) {
       const int qq = q == 0 ? 0 : (q == 1 ? 1 : (q == 2 ? 4 : (q == 3 ? 2 : 5)));  // 0, +x, -x, +y, -y
-      const int dir = qq == 0 ? 0 : (qq - 1) % 3;
 #pragma unroll
-      for (int c = 0; c < M; c++) fq[c] = halo_or_out ? f[(long long)(qq * M + c) * P.plane + off] : R(0);
-      R* o = q == 0 ? p0 : (q == 1 ? ppx : (q == 2 ? pmx : (q == 3 ? ppy : pmy)));
-      post_dir<SYS, R>(K, P, U, w, fq, qq, a0, al[dir], qq == 0 ? a0 : aj[dir], inv2l, hdt, o);
+      for (int c = 0; c < M; c++) of[q][c] = halo_or_out ? f[(long long)(qq * M + c) * P.plane + off] : R(0);
     }
-    const int slot3 = (r - j0 + 3) % 3;
+  };
+  // operands of the +-z posts of an output row: U, omega and f_{+z} at plane
+  // k - 1, U, omega and f_{-z} at plane k + 1
+  R zU[2][M], zw[2], zf[2][M];
+  auto load_z = [&](int y) {
+    const int my = map_index(y, P.ny3, P.bc[2], P.bc[3]);
+#pragma unroll
+    for (int s2 = 0; s2 < 2; s2++) {
+      const int kk = s2 == 0 ? k - 1 : k + 1, qq = s2 == 0 ? 3 : 6;
+      const long long ez = G.idx(kk + GH, y + GH, i + GH);
+      const long long offz = cell3(P, mi, my, s2 == 0 ? mkm : mkp);
+#pragma unroll
+      for (int c = 0; c < M; c++) {
+        zU[s2][c] = Ue[(long long)c * n + ez];
+        zf[s2][c] = f[(long long)(qq * M + c) * P.plane + offz];
+      }
+      zw[s2] = om[ez];
+    }
+  };
+  // lane registers: post_0, post_{+y} and the received F_{+x}, F_{-x} of row
+  // r-1, post_{+y} of row r-2
+  R p0_prev[M], py_prev[M], py_prev2[M], fxp_prev[M], fxm_prev[M];
+#pragma unroll
+  for (int c = 0; c < M; c++) p0_prev[c] = py_prev[c] = py_prev2[c] = fxp_prev[c] = fxm_prev[c] = R(0);
+  constexpr bool PF = K3Occupancy<SYS, R>::prefetch;
+  if constexpr (PF) load_own(j0 - 1);
+#pragma unroll 1
+  for (int r = j0 - 1; r <= j1; r++) {
+    if constexpr (!PF) load_own(r);
+    // own post-collision values of row r
+    R p0[M], ppx[M], pmx[M], ppy[M], pmy[M];
+    {
+      const Prim3<R> pw = prim3<SYS, R>(K, oU);
+      R S[M];
+      if constexpr (SRC) source3<SYS, R>(K, oU, S);
+#pragma unroll
+      for (int q = 0; q < 5; q++) {
+        const int qq = q == 0 ? 0 : (q == 1 ? 1 : (q == 2 ? 4 : (q == 3 ? 2 : 5)));
+        const int dir = qq == 0 ? 0 : (qq - 1) % 3;
+        R* o = q == 0 ? p0 : (q == 1 ? ppx : (q == 2 ? pmx : (q == 3 ? ppy : pmy)));
+        post_q<SYS, R>(K, P, oU, pw, S, ow, of[q], qq, a0, al[dir], qq == 0 ? a0 : aj[dir], inv2l, hdt, o);
+      }
+    }
+    if constexpr (PF) {
+      if (r < j1) load_own(r + 1);
+    }
+    // F_{+x}(x) = post_{+x}(x - e_x) from lane - 1, F_{-x}(x) = post_{-x}(x + e_x)
+    // from lane + 1 (lanes 0 and 31 receive their own value and write nothing)
+    R fxp[M], fxm[M];
 #pragma unroll
     for (int c = 0; c < M; c++) {
-      sx[slot3][0][c][t] = ppx[c];
-      sx[slot3][1][c][t] = pmx[c];
+      fxp[c] = __shfl_up_sync(0xffffffffu, ppx[c], 1);
+      fxm[c] = __shfl_down_sync(0xffffffffu, pmx[c], 1);
     }
-    __syncthreads();
     const int y = r - 1;
     if (y >= j0 && y < j1 && out_lane) {
-      const int ps = (r - 1 - j0 + 3) % 3;
       R Fk[Q][M];
 #pragma unroll
       for (int c = 0; c < M; c++) {
         Fk[0][c] = p0_prev[c];
-        Fk[1][c] = sx[ps][0][c][t - 1];  // F_{+x}(x) = post_{+x}(x - e_x)
-        Fk[4][c] = sx[ps][1][c][t + 1];  // F_{-x}(x) = post_{-x}(x + e_x)
-        Fk[2][c] = py_prev2[c];          // post_{+y} of row y - 1
-        Fk[5][c] = pmy[c];               // post_{-y} of row y + 1
+        Fk[1][c] = fxp_prev[c];
+        Fk[4][c] = fxm_prev[c];
+        Fk[2][c] = py_prev2[c];  // post_{+y} of row y - 1
+        Fk[5][c] = pmy[c];       // post_{-y} of row y + 1
       }
-      // +-z: post_{+z} at plane k - 1, post_{-z} at plane k + 1
-      const int my = map_index(y, P.ny3, P.bc[2], P.bc[3]);
+      // +-z: post_{+z} at plane k - 1, post_{-z} at plane k + 1 (operands
+      // loaded in the previous iteration, or here without prefetch)
+      if constexpr (!PF) load_z(y);
 #pragma unroll
       for (int s2 = 0; s2 < 2; s2++) {
-        const int kk = s2 == 0 ? k - 1 : k + 1, qq = s2 == 0 ? 3 : 6;
-        const long long ez = G.idx(kk + GH, y + GH, i + GH);
-        const long long offz = cell3(P, mi, my, s2 == 0 ? mkm : mkp);
-        R Uz[M], fz[M];
-#pragma unroll
-        for (int c = 0; c < M; c++) {
-          Uz[c] = Ue[(long long)c * n + ez];
-          fz[c] = f[(long long)(qq * M + c) * P.plane + offz];
-        }
-        post_dir<SYS, R>(K, P, Uz, om[ez], fz, qq, a0, al[2], aj[2], inv2l, hdt, Fk[qq]);
+        const int qq = s2 == 0 ? 3 : 6;
+        const Prim3<R> pz = prim3<SYS, R>(K, zU[s2]);
+        R Sz[M];
+        if constexpr (SRC) source3<SYS, R>(K, zU[s2], Sz);
+        post_q<SYS, R>(K, P, zU[s2], pz, Sz, zw[s2], zf[s2], qq, a0, al[2], aj[2], inv2l, hdt, Fk[qq]);
       }
       R Ubar[M];
 #pragma unroll
@@ -579,14 +675,10 @@ __global__ void __launch_bounds__(kLanes3) k3_collide_stream(DevParams P, R* con
       for (int c = 0; c < M; c++) Sn[c] = R(0);
       if constexpr (SRC) {
         if (K.react && Ubar[5] != R(0)) {
-          const double mx = (double)Ubar[1], my2 = (double)Ubar[2], mz = (double)Ubar[3];
-          const RootF64 rt = react_root_f64((double)Ubar[0], mx * mx + my2 * my2 + mz * mz, (double)Ubar[4],
-                                            (double)Ubar[5], 0.5 * cf.dt * K.K, K.gamma_d - 1.0, K.q_d, K.Ti);
           R Un[M];
 #pragma unroll
           for (int c = 0; c < M; c++) Un[c] = Ubar[c];
-          Un[5] = R(rt.z);
-          st |= rt.st;
+          st |= react_implicit3<R>(K, Ubar, cf.dt, hdt, &Un[5]);
           source3<SYS, R>(K, Un, Sn);
         }
       }
@@ -617,11 +709,17 @@ __global__ void __launch_bounds__(kLanes3) k3_collide_stream(DevParams P, R* con
       if constexpr (SYS != SYS_ADV) bad |= !(wn.rho > R(0)) || !(wn.p > R(0));
       if (bad) st |= ST_NONPHYSICAL;
     }
+    // the +-z operands of row r, used when row r is streamed (next iteration)
+    if constexpr (PF) {
+      if (r >= j0 && r < j1 && out_lane) load_z(r);
+    }
 #pragma unroll
     for (int c = 0; c < M; c++) {
       py_prev2[c] = py_prev[c];
       py_prev[c] = ppy[c];
       p0_prev[c] = p0[c];
+      fxp_prev[c] = fxp[c];
+      fxm_prev[c] = fxm[c];
     }
   }
   // side outputs: x, y bounds, sums and status through the fused kernels'

@@ -296,8 +296,9 @@ __device__ __forceinline__ void source(const Phys<R>& K, const R* U, R xr, R yr,
 template <int D>
 __device__ __forceinline__ int react_root_f32(const Phys<float>& K, const float* Ubar, float hdt, float* zout) {
   const float zbar = Ubar[D + 2], rho = Ubar[0], E = Ubar[D + 1];
-  const float m2 = D == 2 ? Ubar[2] : 0.0f;
-  const float momsq = Ubar[1] * Ubar[1] + m2 * m2;
+  const float m2 = D >= 2 ? Ubar[2] : 0.0f;
+  float momsq = Ubar[1] * Ubar[1] + m2 * m2;
+  if constexpr (D == 3) momsq += Ubar[3] * Ubar[3];
   const float irho = frcp(rho);
   const float hk = hdt * K.Kr;  // dt/2 K
   const float dTdz = -K.gm1 * K.q * irho;
