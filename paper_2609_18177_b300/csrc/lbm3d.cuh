@@ -464,31 +464,70 @@ __device__ __forceinline__ unsigned react_implicit3(const Phys<R>& K, const R* U
   }
 }
 
-// block maximum of one speed in the path's type into d (NaN propagates)
-template <class R>
-__device__ __forceinline__ void block_max1_to(R v, unsigned long long* d) {
-  __shared__ R red1[32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const R u = __shfl_xor_sync(0xffffffffu, v, o);
-    v = (u > v || u != u) ? u : v;
-  }
-  __syncthreads();
-  if (lane == 0) red1[w] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int i = 0; i < nw; i++) m = nanmax3(m, (double)red1[i]);
-    atomic_max_nonneg(d, m);
-  }
-}
-
 // rows (y) per block of the 3D collision kernel; threads per block, and the
 // x nodes a block writes: each warp owns a 32-lane segment along x whose
 // lanes 1..30 are written (lanes 0 and 31 are halo)
-constexpr int kRows3 = 16;
+constexpr int kRows3 = 32;
 constexpr int kLanes3 = 128, kSeg3 = 30, kOut3 = (kLanes3 / 32) * kSeg3;
+
+// Side outputs of one warp of the 3D collision kernel, with no block barrier:
+// maxima of the three speed bounds, FP64-quality sums of U (FP32: TwoSum
+// pairs reduced across the warp, combined in FP64 by lane 0; FP64: plain
+// sums) into the warp's own partial slot, status bits.  Lane 0 applies a
+// maximum only when it exceeds the stored one (a stale read just costs an
+// extra atomic, since the maxima only grow during the step).
+template <int M, class R>
+__device__ __forceinline__ void warp_side_outputs3(R sp0, R sp1, R sp2, const Acc<R>* acc, Ctl* ctl, int slot1,
+                                                   double* dst, unsigned st) {
+  const int lane = threadIdx.x & 31;
+  double sum[M];
+  if constexpr (sizeof(R) == 4) {
+    float hi[M], lo[M];
+#pragma unroll
+    for (int c = 0; c < M; c++) {
+      hi[c] = acc[c].hi;
+      lo[c] = acc[c].lo;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int c = 0; c < M; c++) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi[c], o);
+        const float ol = __shfl_xor_sync(0xffffffffu, lo[c], o);
+        const float s2 = hi[c] + oh, bp = s2 - hi[c];
+        const float err = (hi[c] - (s2 - bp)) + (oh - bp);
+        hi[c] = s2;
+        lo[c] += ol + err;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < M; c++) sum[c] = (double)hi[c] + (double)lo[c];
+  } else {
+#pragma unroll
+    for (int c = 0; c < M; c++) sum[c] = acc[c].value();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int c = 0; c < M; c++) sum[c] += __shfl_xor_sync(0xffffffffu, sum[c], o);
+    }
+  }
+  double m[3] = {(double)sp0, (double)sp1, (double)sp2};
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int d = 0; d < 3; d++) m[d] = nanmax3(m[d], __shfl_xor_sync(0xffffffffu, m[d], o));
+  }
+  const unsigned wst = __reduce_or_sync(0xffffffffu, st);
+  if (lane == 0) {
+    unsigned long long* dstm[3] = {&ctl->amax[slot1][0], &ctl->amax[slot1][1], &ctl->amax_z[slot1]};
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+      if (!(bits_to_double(__ldcg(dstm[d])) >= m[d])) atomic_max_nonneg(dstm[d], m[d]);
+#pragma unroll
+    for (int c = 0; c < M; c++) dst[c] = sum[c];
+    if (wst) atomicOr(&ctl->status, wst);
+  }
+}
 
 // launch shape of the collision kernel per system and precision: resident
 // blocks per SM (4, at most 128 registers a thread, for FP32 advection and
@@ -524,7 +563,8 @@ __device__ __forceinline__ void post_q(const Phys<R>& K, const DevParams& P, con
 
 // K3: collision with the first half-source (Eq. 2.2), pull streaming, the
 // implicit moment (2.8) and the second half-source; writes f^{n+1}; side
-// outputs (three speed bounds, FP64-quality sums, status).
+// outputs (three speed bounds, FP64-quality sums, status; one partial-sum
+// slot per warp).
 //
 // Grid (ceil(nx / 120), ceil(ny / kRows3), nz), 128 threads: warp w of block
 // bx is a 32-lane segment along x (lane l at x = 120 bx + 30 w - 1 + l) that
@@ -722,10 +762,9 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks)) k3_col
       fxm_prev[c] = fxm[c];
     }
   }
-  // side outputs: x, y bounds, sums and status through the fused kernels'
-  // reduction; the z bound through its own block maximum
-  fused_side_outputs_to<M, R>(sp0, sp1, acc, ctl, (slot + 1) % 3, partials + bid * M, st);
-  block_max1_to<R>(sp2, &ctl->amax_z[(slot + 1) % 3]);
+  // side outputs per warp (partial slot bid * 4 + w): no block barrier, so a
+  // warp that finished its rows does not wait for the others
+  warp_side_outputs3<M, R>(sp0, sp1, sp2, acc, ctl, (slot + 1) % 3, partials + (bid * (kLanes3 / 32) + w) * M, st);
   if (bid == 0 && threadIdx.x == 0) advance_ctl3(ctl, slot, cf);
 }
 

@@ -217,7 +217,7 @@ struct Impl3 {
     k3_omega<R><<<ge, kBlock3, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->nue, (R*)h->ome);
     k3_collide_stream<SYS, R><<<gn, kBlock3, 0, h->stream>>>(P, buf, h->ctl, slot, G, (const R*)h->Ue,
                                                              (const R*)h->ome, h->partials);
-    h->nblocks = (int)(gn.x * gn.y * gn.z);
+    h->nblocks = (int)(gn.x * gn.y * gn.z) * (kLanes3 / 32);  // one partial slot per warp
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "3D step launch");
     return LBMH_OK;
@@ -484,9 +484,9 @@ int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
   long long nn = (long long)P.nx * P.ny;
   size_t fbytes = (size_t)h->Q * h->m * P.plane * h->elem;
   h->max_blocks = (int)blocks_for(nn);
-  if (p->dim == 3) {  // one block per (x segment, y, z) row of the 3D step
+  if (p->dim == 3) {  // one partial slot per warp of the 3D collision kernel
     const dim3 g3 = grid3_nodes(P.nx, P.ny3, P.nz3);
-    h->max_blocks = std::max(h->max_blocks, (int)(g3.x * g3.y * g3.z));
+    h->max_blocks = std::max(h->max_blocks, (int)(g3.x * g3.y * g3.z) * (kLanes3 / 32));
   }
   h->utmp_bytes = 0;
   auto alloc = [&](void** ptr, size_t bytes) -> bool {
