@@ -9,8 +9,9 @@
 //
 // Implementation: four kernels over a ghost-extended copy of U (3 ghost
 // layers per side, periodic or outflow), the 3D counterpart of the unfused
-// 2D path: K0 moments, K1 indicator, K2 omega, K3 collision + streaming +
-// implicit moment + side outputs.  Distributions use the row layout of the
+// 2D path: K0 moments (or, when the previous step's K3 already wrote the
+// interior of U, only the ghost layers), K1 indicator, K2 omega, K3
+// collision + streaming + implicit moment + side outputs.  Distributions use the row layout of the
 // 2D path with rows = z * ny + y, so the row-wise kernels (moments,
 // checkpoints) serve 3D lattices unchanged.
 #pragma once
@@ -332,16 +333,28 @@ __device__ __forceinline__ bool ext_coords(const ExtGeom3& G, int& ei, int& ej, 
   return ei < G.ex;
 }
 
-// K0: U = sum_k f_k on the ghost-extended grid (wrapped / clamped reads)
+// U on the ghost-extended grid lives in two copies [2][m][ez][ey][ex]: copy
+// p holds the moments of f buffer p.  The collision kernel writes the
+// interior of the other copy (U^{n+1} = sum_k f_k^{n+1}, summed as below), so
+// a step normally only refills the ghost layers (k3_ghost_fill); the full
+// pass K0 runs after the distributions were set from outside.
+template <int M, class T>
+__device__ __forceinline__ T* ue_copy(T* Ue, const ExtGeom3& G, int par) {
+  return Ue + (long long)par * M * ((long long)G.ex * G.ey * G.ez);
+}
+
+// K0: U = sum_k f_k on the ghost-extended grid (wrapped / clamped reads).  It
+// also runs for a finished lattice, so that the copy is valid afterwards.
 template <int SYS, class R>
-__global__ void k3_moments_ext(DevParams P, R* const* buf, const Ctl* ctl, int slot, ExtGeom3 G, R* Ue) {
+__global__ void k3_moments_ext(DevParams P, R* const* buf, const Ctl* ctl, int slot, ExtGeom3 G, R* Ue2) {
   constexpr int M = Fields3<SYS>::M;
   const long long n = (long long)G.ex * G.ey * G.ez;
   int ei, ej, ek;
   long long e;
   if (!ext_coords(G, ei, ej, ek, e)) return;
-  if (P.T > 0.0 && ctl->t[slot] >= P.T) return;
-  const R* f = buf[ctl->parity[slot]];
+  const int par = ctl->parity[slot];
+  const R* f = buf[par];
+  R* Ue = ue_copy<M>(Ue2, G, par);
   const long long off = cell3(P, map_index(ei - GH, P.nx, P.bc[0], P.bc[1]), map_index(ej - GH, P.ny3, P.bc[2], P.bc[3]),
                               map_index(ek - GH, P.nz3, P.bc_z[0], P.bc_z[1]));
 #pragma unroll
@@ -353,15 +366,56 @@ __global__ void k3_moments_ext(DevParams P, R* const* buf, const Ctl* ctl, int s
   }
 }
 
+// The ghost layers of U copy p from the mapped interior nodes (periodic wrap
+// or outflow clamp, as K0 reads them).  Thread g enumerates the ghost nodes:
+// the 2 GH planes of z ghosts, then per interior plane the 2 GH rows of y
+// ghosts, then per interior row the 2 GH x ghosts.
+template <int SYS, class R>
+__global__ void k3_ghost_fill(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, R* Ue2) {
+  constexpr int M = Fields3<SYS>::M;
+  const long long n = (long long)G.ex * G.ey * G.ez;
+  const long long na = 2LL * GH * G.ey * G.ex, nb = 2LL * GH * G.ex * P.nz3, nc = 2LL * GH * P.ny3 * P.nz3;
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= na + nb + nc) return;
+  if (P.T > 0.0 && ctl->t[slot] >= P.T) return;
+  int ei, ej, ek;
+  if (g < na) {
+    const long long sl = g / ((long long)G.ey * G.ex), rem = g % ((long long)G.ey * G.ex);
+    ek = sl < GH ? (int)sl : P.nz3 + (int)sl;
+    ej = (int)(rem / G.ex);
+    ei = (int)(rem % G.ex);
+  } else if (g < na + nb) {
+    const long long h = g - na, per = 2LL * GH * G.ex;
+    ek = GH + (int)(h / per);
+    const int row = (int)((h % per) / G.ex);
+    ej = row < GH ? row : P.ny3 + row;
+    ei = (int)((h % per) % G.ex);
+  } else {
+    const long long h = g - na - nb;
+    const long long kr = h / (2 * GH);
+    ek = GH + (int)(kr / P.ny3);
+    ej = GH + (int)(kr % P.ny3);
+    const int sx = (int)(h % (2 * GH));
+    ei = sx < GH ? sx : P.nx + sx;
+  }
+  const int mi = map_index(ei - GH, P.nx, P.bc[0], P.bc[1]), mj = map_index(ej - GH, P.ny3, P.bc[2], P.bc[3]),
+            mk = map_index(ek - GH, P.nz3, P.bc_z[0], P.bc_z[1]);
+  R* Ue = ue_copy<M>(Ue2, G, ctl->parity[slot]);
+  const long long e = G.idx(ek, ej, ei), src = G.idx(mk + GH, mj + GH, mi + GH);
+#pragma unroll
+  for (int c = 0; c < M; c++) Ue[(long long)c * n + e] = Ue[(long long)c * n + src];
+}
+
 // K1: nu = sum_j sum_r theta^{(r,j)} one layer inside the extension
 template <int SYS, class R>
-__global__ void k3_indicator(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, const R* Ue, R* nu) {
+__global__ void k3_indicator(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, const R* Ue2, R* nu) {
   constexpr int M = Fields3<SYS>::M;
   const long long n = (long long)G.ex * G.ey * G.ez;
   int ei, ej, ek;
   long long e;
   if (!ext_coords(G, ei, ej, ek, e)) return;
   if (P.T > 0.0 && ctl->t[slot] >= P.T) return;
+  const R* Ue = ue_copy<M>(Ue2, G, ctl->parity[slot]);
   if (ei < 1 || ei >= G.ex - 1 || ej < 1 || ej >= G.ey - 1 || ek < 1 || ek >= G.ez - 1) return;
   const Phys<R> K = make_phys<R>(P);
   const long long stride[3] = {1, G.ex, (long long)G.ex * G.ey};
@@ -562,7 +616,8 @@ __device__ __forceinline__ void post_q(const Phys<R>& K, const DevParams& P, con
 }
 
 // K3: collision with the first half-source (Eq. 2.2), pull streaming, the
-// implicit moment (2.8) and the second half-source; writes f^{n+1}; side
+// implicit moment (2.8) and the second half-source; writes f^{n+1} and the
+// interior of the next U copy (U^{n+1} = sum_k f_k^{n+1}); side
 // outputs (three speed bounds, FP64-quality sums, status; one partial-sum
 // slot per warp).
 //
@@ -582,7 +637,7 @@ __device__ __forceinline__ void post_q(const Phys<R>& K, const DevParams& P, con
 // spills.
 template <int SYS, class R>
 __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks)) k3_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
-                                                                ExtGeom3 G, const R* Ue, const R* om,
+                                                                ExtGeom3 G, R* Ue2, const R* om,
                                                                 double* partials) {
   constexpr int M = Fields3<SYS>::M, Q = 7;
   constexpr bool SRC = SYS == SYS_REACT;
@@ -592,8 +647,11 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks)) k3_col
     if (bid == 0 && threadIdx.x == 0) advance_ctl3(ctl, slot, cf);
     return;
   }
-  const R* f = buf[ctl->parity[slot]];
-  R* fo = buf[ctl->parity[slot] ^ 1];
+  const int par = ctl->parity[slot];
+  const R* f = buf[par];
+  R* fo = buf[par ^ 1];
+  const R* Ue = ue_copy<M>(Ue2, G, par);
+  R* Uo_ext = ue_copy<M>(Ue2, G, par ^ 1);  // U^{n+1} of the interior, for the next step
   const long long n = (long long)G.ex * G.ey * G.ez;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i = blockIdx.x * kOut3 + w * kSeg3 - 1 + lane, k = blockIdx.z;
@@ -737,6 +795,9 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks)) k3_col
           Uo[c] += v;
         }
       }
+      const long long eo = G.idx(k + GH, y + GH, i + GH);
+#pragma unroll
+      for (int c = 0; c < M; c++) Uo_ext[(long long)c * n + eo] = Uo[c];
       const Prim3<R> wn = prim3<SYS, R>(K, Uo);
       sp0 = rmax(sp0, speed3<SYS, R>(K, P, wn, 0));
       sp1 = rmax(sp1, speed3<SYS, R>(K, P, wn, 1));

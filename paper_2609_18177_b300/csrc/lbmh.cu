@@ -37,7 +37,8 @@ struct lbmh_handle {
   cudaStream_t stream;
   void* fbuf[2];
   void** dbuf;              // device copy of fbuf
-  void* Ue;                 // unfused scratch: U_ext [m][ey][ex]
+  void* Ue;                 // unfused scratch: U_ext [m][ey][ex] (3D: two copies, by f parity)
+  bool u3_valid;            // 3D: the U copy of the current f holds its moments (interior)
   void* nue;                // nu_ext
   void* ome;                // omega_ext
   ExtGeom G;
@@ -212,11 +213,18 @@ struct Impl3 {
     const ExtGeom3 G = geom(h);
     const dim3 ge = grid3_ext(G.ex, G.ey, G.ez), gn = grid3_nodes(P.nx, P.ny3, P.nz3);
     R* const* buf = (R* const*)h->dbuf;
-    k3_moments_ext<SYS, R><<<ge, kBlock3, 0, h->stream>>>(P, buf, h->ctl, slot, G, (R*)h->Ue);
+    if (h->u3_valid) {  // the previous step's collision wrote the interior of U
+      const long long ng = (long long)G.ex * G.ey * G.ez - (long long)P.nx * P.ny3 * P.nz3;
+      k3_ghost_fill<SYS, R><<<(unsigned)((ng + kBlock3 - 1) / kBlock3), kBlock3, 0, h->stream>>>(P, h->ctl, slot, G,
+                                                                                               (R*)h->Ue);
+    } else {
+      k3_moments_ext<SYS, R><<<ge, kBlock3, 0, h->stream>>>(P, buf, h->ctl, slot, G, (R*)h->Ue);
+    }
     k3_indicator<SYS, R><<<ge, kBlock3, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->Ue, (R*)h->nue);
     k3_omega<R><<<ge, kBlock3, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->nue, (R*)h->ome);
-    k3_collide_stream<SYS, R><<<gn, kBlock3, 0, h->stream>>>(P, buf, h->ctl, slot, G, (const R*)h->Ue,
-                                                             (const R*)h->ome, h->partials);
+    k3_collide_stream<SYS, R><<<gn, kBlock3, 0, h->stream>>>(P, buf, h->ctl, slot, G, (R*)h->Ue, (const R*)h->ome,
+                                                             h->partials);
+    h->u3_valid = true;
     h->nblocks = (int)(gn.x * gn.y * gn.z) * (kLanes3 / 32);  // one partial slot per warp
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "3D step launch");
@@ -340,7 +348,7 @@ int ensure_utmp(lbmh_handle* h, size_t bytes) {
 int ensure_scratch(lbmh_handle* h) {
   if (h->Ue) return LBMH_OK;
   long long next = (long long)h->G.ex * h->G.ey * h->G.ez;
-  size_t b1 = (size_t)next * h->m * h->elem, b2 = (size_t)next * h->elem;
+  size_t b1 = (size_t)next * h->m * h->elem * (h->dim == 3 ? 2 : 1), b2 = (size_t)next * h->elem;
   if (cudaMalloc(&h->Ue, b1) != cudaSuccess || cudaMalloc(&h->nue, b2) != cudaSuccess ||
       cudaMalloc(&h->ome, b2) != cudaSuccess) {
     cudaGetLastError();
@@ -375,6 +383,10 @@ int capture_steps(lbmh_handle* h, double T) {
   cudaStream_t user = h->stream;
   h->stream = h->cap_stream;
   cudaGraph_t g = nullptr;
+  // a replay may follow any change of the distributions: its first step
+  // computes the 3D moments in full
+  const bool u3_before = h->u3_valid;
+  h->u3_valid = false;
   cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
   int rc = LBMH_OK;
   if (e == cudaSuccess) {
@@ -388,6 +400,7 @@ int capture_steps(lbmh_handle* h, double T) {
   if (e != cudaSuccess || rc != LBMH_OK) {
     cudaGetLastError();
     h->graph = nullptr;
+    h->u3_valid = u3_before;  // nothing ran
     h->graph_failed = true;  // fall back to single launches from now on
     h->err.clear();
     return LBMH_OK;
@@ -448,7 +461,7 @@ int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
   lbmh_handle* h = new lbmh_handle();
   memset(h->fbuf, 0, sizeof h->fbuf);
   h->dbuf = nullptr; h->Ue = h->nue = h->ome = nullptr; h->partials = nullptr; h->ctl = nullptr; h->Utmp = nullptr;
-  h->cap_stream = nullptr; h->graph = nullptr; h->graph_T = 0.0; h->graph_failed = false;
+  h->cap_stream = nullptr; h->graph = nullptr; h->graph_T = 0.0; h->graph_failed = false; h->u3_valid = false;
   h->prob = *p;
   h->dim = p->dim;
   h->sys = p->system;
@@ -552,6 +565,7 @@ int lbmh_set_state(lbmh_handle* h, const double* U, int on_device) {
     src = h->Utmp;
   }
   CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->stream));
+  h->u3_valid = false;
   int rc = h->ops->init(h, src);
   if (rc) return rc;
   if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
@@ -660,6 +674,7 @@ int lbmh_set_f(lbmh_handle* h, const double* f_in, int on_device, double t, int6
   c.t[0] = t;
   c.nsteps[0] = steps;
   CK(h, cudaMemcpyAsync(h->ctl, &c, sizeof c, cudaMemcpyHostToDevice, h->stream));
+  h->u3_valid = false;
   int rc = h->ops->set_f(h, src);
   if (rc) return rc;
   rc = sync(h);
