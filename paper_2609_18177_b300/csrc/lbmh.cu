@@ -221,7 +221,8 @@ struct Impl3 {
       k3_moments_ext<SYS, R><<<ge, kBlock3, 0, h->stream>>>(P, buf, h->ctl, slot, G, (R*)h->Ue);
     }
     k3_indicator<SYS, R><<<ge, kBlock3, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->Ue, (R*)h->nue);
-    k3_omega<R><<<ge, kBlock3, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->nue, (R*)h->ome);
+    k3_omega<R><<<grid3_omega(G.ex, G.ey, G.ez), kBlock3, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->nue,
+                                                                          (R*)h->ome);
     k3_collide_stream<SYS, R><<<gn, kBlock3, 0, h->stream>>>(P, buf, h->ctl, slot, G, (R*)h->Ue, (const R*)h->ome,
                                                              h->partials);
     h->u3_valid = true;
