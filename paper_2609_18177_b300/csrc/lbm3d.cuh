@@ -665,7 +665,7 @@ __device__ __forceinline__ void post_q(const Phys<R>& K, const DevParams& P, con
 // overlapped with the other phase.  The prefetched operands cost registers: resident blocks
 // per SM are set per system and precision (K3Occupancy) so that no instance
 // spills.
-template <int SYS, class R>
+template <int SYS, class R, class IX>
 __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks)) k3_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
                                                                 ExtGeom3 G, R* Ue2, const R* om,
                                                                 double* partials) {
@@ -682,7 +682,10 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks)) k3_col
   R* fo = buf[par ^ 1];
   const R* Ue = ue_copy<M>(Ue2, G, par);
   R* Uo_ext = ue_copy<M>(Ue2, G, par ^ 1);  // U^{n+1} of the interior, for the next step
-  const long long n = (long long)G.ex * G.ey * G.ez;
+  // offsets in IX: int where every offset of the lattice fits (chosen at launch), else long long
+  const IX n = (IX)G.ex * G.ey * G.ez, pl = (IX)P.plane;
+  auto eidx = [&](int ek, int ej, int ei) -> IX { return ((IX)ek * G.ey + ej) * G.ex + ei; };
+  auto fidx = [&](int ci, int cj, int ck) -> IX { return ((IX)ck * P.ny3 + cj) * P.pitch + ci + XPAD; };
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i = blockIdx.x * kOut3 + w * kSeg3 - 1 + lane, k = blockIdx.z;
   const bool out_lane = lane >= 1 && lane <= kSeg3 && i < P.nx;
@@ -703,16 +706,16 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks)) k3_col
   // node; ghost rows: the mapped node, A6), loaded one row ahead
   R oU[M], ow, of[5][M];
   auto load_own = [&](int r) {
-    const long long e = G.idx(k + GH, r + GH, i + GH);
-    const long long off = cell3(P, mi, map_index(r, P.ny3, P.bc[2], P.bc[3]), k);
+    const IX e = eidx(k + GH, r + GH, i + GH);
+    const IX off = fidx(mi, map_index(r, P.ny3, P.bc[2], P.bc[3]), k);
 #pragma unroll
-    for (int c = 0; c < M; c++) oU[c] = halo_or_out ? Ue[(long long)c * n + e] : R(1);
+    for (int c = 0; c < M; c++) oU[c] = halo_or_out ? Ue[(IX)c * n + e] : R(1);
     ow = halo_or_out ? om[e] : R(1);
 #pragma unroll
     for (int q = 0; q < 5; q++) {
       const int qq = q == 0 ? 0 : (q == 1 ? 1 : (q == 2 ? 4 : (q == 3 ? 2 : 5)));  // 0, +x, -x, +y, -y
 #pragma unroll
-      for (int c = 0; c < M; c++) of[q][c] = halo_or_out ? f[(long long)(qq * M + c) * P.plane + off] : R(0);
+      for (int c = 0; c < M; c++) of[q][c] = halo_or_out ? f[(IX)(qq * M + c) * pl + off] : R(0);
     }
   };
   // operands of the +-z posts of an output row: U, omega and f_{+z} at plane
@@ -723,12 +726,12 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks)) k3_col
 #pragma unroll
     for (int s2 = 0; s2 < 2; s2++) {
       const int kk = s2 == 0 ? k - 1 : k + 1, qq = s2 == 0 ? 3 : 6;
-      const long long ez = G.idx(kk + GH, y + GH, i + GH);
-      const long long offz = cell3(P, mi, my, s2 == 0 ? mkm : mkp);
+      const IX ez = eidx(kk + GH, y + GH, i + GH);
+      const IX offz = fidx(mi, my, s2 == 0 ? mkm : mkp);
 #pragma unroll
       for (int c = 0; c < M; c++) {
-        zU[s2][c] = Ue[(long long)c * n + ez];
-        zf[s2][c] = f[(long long)(qq * M + c) * P.plane + offz];
+        zU[s2][c] = Ue[(IX)c * n + ez];
+        zf[s2][c] = f[(IX)(qq * M + c) * pl + offz];
       }
       zw[s2] = om[ez];
     }
@@ -810,7 +813,7 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks)) k3_col
           source3<SYS, R>(K, Un, Sn);
         }
       }
-      const long long oo = cell3(P, i, y, k);
+      const IX oo = fidx(i, y, k);
       R Uo[M];
 #pragma unroll
       for (int c = 0; c < M; c++) Uo[c] = R(0);
@@ -821,13 +824,13 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks)) k3_col
         for (int c = 0; c < M; c++) {
           R v = Fk[q][c];
           if constexpr (SRC) v += hdt * akq * Sn[c];
-          fo[(long long)(q * M + c) * P.plane + oo] = v;
+          fo[(IX)(q * M + c) * pl + oo] = v;
           Uo[c] += v;
         }
       }
-      const long long eo = G.idx(k + GH, y + GH, i + GH);
+      const IX eo = eidx(k + GH, y + GH, i + GH);
 #pragma unroll
-      for (int c = 0; c < M; c++) Uo_ext[(long long)c * n + eo] = Uo[c];
+      for (int c = 0; c < M; c++) Uo_ext[(IX)c * n + eo] = Uo[c];
       const Prim3<R> wn = prim3<SYS, R>(K, Uo);
       sp0 = rmax(sp0, speed3<SYS, R>(K, P, wn, 0));
       sp1 = rmax(sp1, speed3<SYS, R>(K, P, wn, 1));
@@ -857,6 +860,14 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks)) k3_col
   // warp that finished its rows does not wait for the others
   warp_side_outputs3<M, R>(sp0, sp1, sp2, acc, ctl, (slot + 1) % 3, partials + (bid * (kLanes3 / 32) + w) * M, st);
   if (bid == 0 && threadIdx.x == 0) advance_ctl3(ctl, slot, cf);
+}
+
+// whether every offset the collision kernel forms fits in an int: Q m planes
+// of f and m copies of the extended U (two U copies are addressed from the
+// copy's own base)
+inline bool k3_offsets_fit_int(const DevParams& P, int m, long long next) {
+  const long long lim = 2147483647LL;
+  return 7LL * m * P.plane < lim && (long long)m * next < lim;
 }
 
 // launch shapes of the 3D kernels

@@ -39,6 +39,7 @@ struct lbmh_handle {
   void** dbuf;              // device copy of fbuf
   void* Ue;                 // unfused scratch: U_ext [m][ey][ex] (3D: two copies, by f parity)
   bool u3_valid;            // 3D: the U copy of the current f holds its moments (interior)
+  bool idx64_3d;            // 3D: 64-bit offsets in the collision kernel even where int offsets fit
   void* nue;                // nu_ext
   void* ome;                // omega_ext
   ExtGeom G;
@@ -223,8 +224,12 @@ struct Impl3 {
     k3_indicator<SYS, R><<<ge, kBlock3, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->Ue, (R*)h->nue);
     k3_omega<R><<<grid3_omega(G.ex, G.ey, G.ez), kBlock3, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->nue,
                                                                           (R*)h->ome);
-    k3_collide_stream<SYS, R><<<gn, kBlock3, 0, h->stream>>>(P, buf, h->ctl, slot, G, (R*)h->Ue, (const R*)h->ome,
-                                                             h->partials);
+    if (!h->idx64_3d && k3_offsets_fit_int(P, M, (long long)G.ex * G.ey * G.ez))
+      k3_collide_stream<SYS, R, int><<<gn, kBlock3, 0, h->stream>>>(P, buf, h->ctl, slot, G, (R*)h->Ue,
+                                                                    (const R*)h->ome, h->partials);
+    else
+      k3_collide_stream<SYS, R, long long><<<gn, kBlock3, 0, h->stream>>>(P, buf, h->ctl, slot, G, (R*)h->Ue,
+                                                                          (const R*)h->ome, h->partials);
     h->u3_valid = true;
     h->nblocks = (int)(gn.x * gn.y * gn.z) * (kLanes3 / 32);  // one partial slot per warp
     cudaError_t e = cudaGetLastError();
@@ -463,6 +468,10 @@ int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
   memset(h->fbuf, 0, sizeof h->fbuf);
   h->dbuf = nullptr; h->Ue = h->nue = h->ome = nullptr; h->partials = nullptr; h->ctl = nullptr; h->Utmp = nullptr;
   h->cap_stream = nullptr; h->graph = nullptr; h->graph_T = 0.0; h->graph_failed = false; h->u3_valid = false;
+  {  // LBMH_3D_INDEX64=1 selects the 64-bit-offset collision kernel at any size (for tests)
+    const char* e = getenv("LBMH_3D_INDEX64");
+    h->idx64_3d = e && e[0] == '1';
+  }
   h->prob = *p;
   h->dim = p->dim;
   h->sys = p->system;

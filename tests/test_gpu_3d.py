@@ -127,3 +127,19 @@ def test_3d_graph_replay_and_set_f_keep_moments_consistent(precision):
     assert np.array_equal(a.get_f(), c.get_f())
     for s in (a, b, c):
         s.close()
+
+
+def test_3d_int_and_64bit_offsets_give_the_same_bits(monkeypatch):
+    """The collision kernel indexes with int offsets where every offset of the
+    lattice fits (up to ~390^3) and with 64-bit offsets beyond; the two
+    instances do the same arithmetic.  LBMH_3D_INDEX64=1 forces the 64-bit
+    one on a small lattice."""
+    pb, U0 = case(W.REACTIVE, W.OUTFLOW)
+    for prec in (lbmh.FP64, lbmh.FP32):
+        monkeypatch.delenv("LBMH_3D_INDEX64", raising=False)
+        a = lbmh.Solver(pb, precision=prec).set_state(U0).step(12)
+        monkeypatch.setenv("LBMH_3D_INDEX64", "1")
+        b = lbmh.Solver(pb, precision=prec).set_state(U0).step(12)
+        assert np.array_equal(a.get_f(), b.get_f())
+        a.close()
+        b.close()
