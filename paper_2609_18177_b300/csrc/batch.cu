@@ -52,6 +52,10 @@ __global__ void __launch_bounds__(FT) k_batch2d(const BatchInst* insts, const Ba
   constexpr int M = Fields<SYS, 2>::M;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int s_abort;
+  // step coefficients of the current segment's lattice: FP64 arithmetic done
+  // once by thread 0, not by every thread of every segment
+  __shared__ StepCoef s_cf;
+  __shared__ Coef2D<R> s_cc;
   const int t = threadIdx.x;
   Pipe2D pp;
   pipe2d_init<SYS, R, PREF, 1>(pp, smem_raw, &s_abort);
@@ -61,7 +65,12 @@ __global__ void __launch_bounds__(FT) k_batch2d(const BatchInst* insts, const Ba
     const BatchInst& I = insts[sg.inst];
     const DevParams P = I.P;
     Ctl* ctl = I.ctl;
-    const StepCoef cf = step_coef<2>(P, ctl, slot);
+    if (t == 0) {
+      s_cf = step_coef<2>(P, ctl, slot);
+      s_cc = make_coef2d<R>(s_cf, P);
+    }
+    __syncthreads();  // (the previous segment's readers passed its side-output barrier)
+    const StepCoef cf = s_cf;
     R sp0 = R(0), sp1 = R(0);
     Acc<R> acc[M];
 #pragma unroll
@@ -76,7 +85,7 @@ __global__ void __launch_bounds__(FT) k_batch2d(const BatchInst* insts, const Ba
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tms) : "memory");
       }
       const Phys<R> K = make_phys<R>(P);
-      const Coef2D<R> cc = make_coef2d<R>(cf, P);
+      const Coef2D<R> cc = s_cc;
       run_segment2d<SYS, R, PREF, 1>(pp, tml, tms, (R*)I.buf[par ^ 1], P, K, cc, sg.strip, sg.yb, sg.ye, I.nxs, sp0,
                                      sp1, acc, st);
       if (pp.aborted) st |= ST_TIMEOUT;
