@@ -80,13 +80,23 @@ class Server:
     """One batch per system; requests are admitted by footprint and stepped
     together in chunks of `chunk` steps."""
 
-    def __init__(self, capacity_bytes=8 << 30, max_instances=256, chunk=32, autotune=False, keep_results=False):
-        import torch
-        self.torch = torch
-        self.streams = {k: torch.cuda.Stream() for k in KINDS}
-        self.batches = {k: lbmh.Batch(KIND_SYSTEM[k], precision=lbmh.FP32, capacity_bytes=capacity_bytes,
-                                      max_instances=max_instances, stream=self.streams[k].cuda_stream)
-                        for k in KINDS}
+    def __init__(self, capacity_bytes=8 << 30, max_instances=256, chunk=32, autotune=False, keep_results=False,
+                 batches=None, new_event=None):
+        """`batches` (one object per system with the lbmh.Batch methods add,
+        step, poll, moments, remove, autotune) and `new_event` (a factory of
+        objects with record(stream) and query()) replace the CUDA batches and
+        events, e.g. to exercise the scheduling on a host without a GPU."""
+        if batches is None:
+            import torch
+            self.streams = {k: torch.cuda.Stream() for k in KINDS}
+            self.batches = {k: lbmh.Batch(KIND_SYSTEM[k], precision=lbmh.FP32, capacity_bytes=capacity_bytes,
+                                          max_instances=max_instances, stream=self.streams[k].cuda_stream)
+                            for k in KINDS}
+            self.new_event = new_event or torch.cuda.Event
+        else:
+            self.streams = {k: None for k in KINDS}
+            self.batches = batches
+            self.new_event = new_event
         self.chunk = chunk
         self.autotune = autotune
         self.keep_results = keep_results
@@ -106,7 +116,6 @@ class Server:
         requests admitted, and the next chunk launched.  The batches do not
         wait for one another, so a system with heavier steps does not hold the
         others idle."""
-        torch = self.torch
         pending = sorted(trace, key=lambda r: r.arrival)
         queue: Dict[str, List[Request]] = {k: [] for k in KINDS}
         live: Dict[str, Dict[int, tuple]] = {k: {} for k in KINDS}  # slot -> (request, admitted time)
@@ -157,7 +166,7 @@ class Server:
                         self.batches[k].autotune(steps_per_candidate=2)
                         self.tuned.add(k)
                     self.batches[k].step(self.chunk)
-                    ev = torch.cuda.Event()
+                    ev = self.new_event()
                     ev.record(self.streams[k])
                     inflight[k] = ev
                     progressed = True

@@ -1,0 +1,121 @@
+"""Scheduling of the continuous-batching server, on the host: fake batches and
+events stand in for the CUDA ones (the GPU path itself is covered in
+test_gpu_serve.py).  Every request completes with its requested step count;
+a full arena defers admission instead of failing; and a system whose chunks
+take longer does not hold the other systems' batches idle."""
+import numpy as np
+
+from paper_2609_18177_b300 import serve as S
+
+
+class FakeBatch:
+    """Lattices advance by whole chunks; at most `slots` are resident."""
+
+    def __init__(self, slots, max_instances=16):
+        self.slots, self.max_instances = slots, max_instances
+        self.live = {}  # slot -> [steps done, steps wanted]
+        self.step_calls = 0
+
+    def add(self, pb, U0, max_steps=0, T=0.0):
+        if len(self.live) >= self.slots:
+            return None
+        slot = min(set(range(self.max_instances)) - set(self.live))
+        self.live[slot] = [0, max_steps]
+        return slot
+
+    def step(self, n):
+        self.step_calls += 1
+        for v in self.live.values():
+            v[0] = min(v[0] + n, v[1])
+
+    def poll(self):
+        done = np.full(self.max_instances, -1, dtype=np.int32)
+        steps = np.zeros(self.max_instances, dtype=np.int64)
+        for s, (k, want) in self.live.items():
+            done[s] = 1 if k >= want else 0
+            steps[s] = k
+        return done, np.zeros(self.max_instances), steps, np.zeros(self.max_instances, dtype=np.uint32)
+
+    def moments(self, slot):
+        return np.array([float(slot)])
+
+    def remove(self, slot):
+        del self.live[slot]
+
+    def autotune(self, steps_per_candidate=2):
+        return 0.0
+
+
+class FakeEvent:
+    """Done after `polls` queries (a chunk that takes a while on the device)."""
+
+    def __init__(self, polls=0):
+        self.left = polls
+
+    def record(self, stream):
+        pass
+
+    def query(self):
+        self.left -= 1
+        return self.left < 0
+
+    def synchronize(self):
+        self.left = -1
+
+
+def requests(kinds_steps, arrival=0.0):
+    return [S.Request(i, kind, 64, steps, i, arrival) for i, (kind, steps) in enumerate(kinds_steps)]
+
+
+def dummy_inputs(trace):
+    return {r.rid: (None, None) for r in trace}
+
+
+def test_every_request_completes_with_its_steps():
+    trace = requests([("euler", 96), ("swe", 40), ("reactive", 200), ("euler", 33), ("swe", 1)])
+    srv = S.Server(chunk=32, batches={k: FakeBatch(slots=4) for k in S.KINDS}, new_event=FakeEvent,
+                   keep_results=True)
+    results, stats = srv.run(trace, inputs=dummy_inputs(trace), max_seconds=10.0)
+    assert stats["completed"] == stats["submitted"] == len(trace)
+    by = {r.rid: r for r in results}
+    for req in trace:
+        assert by[req.rid].steps == req.steps and by[req.rid].kind == req.kind
+        assert by[req.rid].finished >= by[req.rid].admitted >= req.arrival
+    assert stats["deferred_admissions"] == 0
+
+
+def test_full_arena_defers_admission():
+    trace = requests([("swe", 64)] * 6)
+    batches = {k: FakeBatch(slots=2) for k in S.KINDS}
+    srv = S.Server(chunk=32, batches=batches, new_event=FakeEvent)
+    results, stats = srv.run(trace, inputs=dummy_inputs(trace), max_seconds=10.0)
+    assert stats["completed"] == 6
+    assert stats["deferred_admissions"] == 4  # two fit at first; the rest waited for removals
+    assert not batches["swe"].live  # everything harvested and removed
+
+
+def test_slow_system_does_not_hold_the_others():
+    """Reactive chunks stay in flight for many polls; the Euler batch must keep
+    stepping meanwhile (per-system cycles, no lockstep over the three)."""
+    trace = requests([("reactive", 64), ("euler", 320)])
+    batches = {k: FakeBatch(slots=4) for k in S.KINDS}
+    # every reactive chunk stays in flight for 200 polls, the others for none
+    events = {"reactive": lambda: FakeEvent(polls=200), "euler": lambda: FakeEvent(0), "swe": lambda: FakeEvent(0)}
+    # route the factory by the batch being stepped: the server records the event
+    # right after stepping a batch, so the last stepped batch names the stream
+    last = {"k": None}
+    for k, b in batches.items():
+        orig = b.step
+
+        def step(n, _k=k, _orig=orig):
+            last["k"] = _k
+            _orig(n)
+        b.step = step
+    srv = S.Server(chunk=32, batches=batches, new_event=lambda: events[last["k"]](), keep_results=True)
+    results, stats = srv.run(trace, inputs=dummy_inputs(trace), max_seconds=20.0)
+    by = {r.kind: r for r in results}
+    assert stats["completed"] == 2
+    # Euler needs 10 chunks, reactive 2; with a lockstep over systems Euler
+    # could not finish before reactive, whose chunks each wait 200 polls
+    assert by["euler"].finished < by["reactive"].finished
+    assert batches["euler"].step_calls == 10 and batches["reactive"].step_calls == 2
