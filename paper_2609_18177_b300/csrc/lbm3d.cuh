@@ -616,8 +616,9 @@ __device__ __forceinline__ void warp_side_outputs3(R sp0, R sp1, R sp2, const Ac
 // launch shape of the collision kernel per system and precision: resident
 // blocks per SM (4, at most 128 registers a thread, for FP32 advection and
 // Euler; 2 for reactive Euler and FP64) and whether operands are loaded one
-// row ahead.  FP64 (bound by the FP64 pipe) loads them where they
-// are used: prefetched doubles would spill.
+// row ahead.  FP64 (bound by the FP64 pipe) loads them where they are used:
+// prefetched doubles would spill.  At 4 blocks FP32 Euler spills ~24 bytes a
+// thread, and still runs faster than at 3 blocks without spills.
 template <int SYS, class R>
 struct K3Occupancy {
   static constexpr bool prefetch = sizeof(R) == 4;
@@ -662,13 +663,12 @@ __device__ __forceinline__ void post_q(const Phys<R>& K, const DevParams& P, con
 // In FP32 loads run one row ahead: the own operands of row r + 1 are issued
 // as soon as row r's posts are formed, the +-z operands of row r once row
 // r - 1 is written, so each row waits on one memory latency, already
-// overlapped with the other phase.  The prefetched operands cost registers: resident blocks
-// per SM are set per system and precision (K3Occupancy) so that no instance
-// spills.
+// overlapped with the other phase.  The prefetched operands cost registers:
+// resident blocks per SM are set per system and precision (K3Occupancy).
 template <int SYS, class R, class IX>
-__global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks)) k3_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
-                                                                ExtGeom3 G, R* Ue2, const R* om,
-                                                                double* partials) {
+__global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks))
+    k3_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot, ExtGeom3 G, R* Ue2, const R* om,
+                      double* partials) {
   constexpr int M = Fields3<SYS>::M, Q = 7;
   constexpr bool SRC = SYS == SYS_REACT;
   const StepCoef3 cf = step_coef3(P, ctl, slot);
