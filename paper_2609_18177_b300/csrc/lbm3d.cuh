@@ -617,8 +617,8 @@ __device__ __forceinline__ void warp_side_outputs3(R sp0, R sp1, R sp2, const Ac
 // blocks per SM (4, at most 128 registers a thread, for FP32 advection and
 // Euler; 2 for reactive Euler and FP64) and whether operands are loaded one
 // row ahead.  FP64 (bound by the FP64 pipe) loads them where they are used:
-// prefetched doubles would spill.  At 4 blocks FP32 Euler spills ~24 bytes a
-// thread, and still runs faster than at 3 blocks without spills.
+// prefetched doubles would spill.  At 4 blocks FP32 Euler spills a few bytes
+// a thread, and still runs faster than at 3 blocks without spills.
 template <int SYS, class R>
 struct K3Occupancy {
   static constexpr bool prefetch = sizeof(R) == 4;
@@ -671,7 +671,23 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks))
                       double* partials) {
   constexpr int M = Fields3<SYS>::M, Q = 7;
   constexpr bool SRC = SYS == SYS_REACT;
-  const StepCoef3 cf = step_coef3(P, ctl, slot);
+  // step coefficients (FP64) and their conversions, by one thread per block
+  __shared__ StepCoef3 s_cf;
+  __shared__ R s_k[9];  // a0, 1/(2 lambda), dt/2, alpha_0..2, a_1..3
+  if (threadIdx.x == 0) {
+    const StepCoef3 c = step_coef3(P, ctl, slot);
+    s_cf = c;
+    s_k[0] = R(c.a0);
+    s_k[1] = R(1.0 / (2.0 * c.lam));
+    s_k[2] = R(0.5 * c.dt);
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      s_k[3 + j] = R(c.alpha[j]);
+      s_k[6 + j] = R(c.aj[j]);
+    }
+  }
+  __syncthreads();
+  const StepCoef3 cf = s_cf;
   const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   if (!cf.active) {
     if (bid == 0 && threadIdx.x == 0) advance_ctl3(ctl, slot, cf);
@@ -693,9 +709,9 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks))
   const int mi = map_index(i, P.nx, P.bc[0], P.bc[1]);
   const int mkm = map_index(k - 1, P.nz3, P.bc_z[0], P.bc_z[1]), mkp = map_index(k + 1, P.nz3, P.bc_z[0], P.bc_z[1]);
   const Phys<R> K = make_phys<R>(P);
-  const R a0 = R(cf.a0), inv2l = R(1.0 / (2.0 * cf.lam)), hdt = R(0.5 * cf.dt);
-  const R al[3] = {R(cf.alpha[0]), R(cf.alpha[1]), R(cf.alpha[2])};
-  const R aj[3] = {R(cf.aj[0]), R(cf.aj[1]), R(cf.aj[2])};
+  const R a0 = s_k[0], inv2l = s_k[1], hdt = s_k[2];
+  const R al[3] = {s_k[3], s_k[4], s_k[5]};
+  const R aj[3] = {s_k[6], s_k[7], s_k[8]};
   R sp0 = R(0), sp1 = R(0), sp2 = R(0);
   Acc<R> acc[M];
 #pragma unroll
