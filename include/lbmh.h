@@ -142,6 +142,7 @@ typedef struct lbmh_info {
   int m, Q;            /* fields and velocities */
   int kernel;          /* implementation in use: LBMH_KERNEL_FUSED or _UNFUSED */
   int64_t device_bytes; /* device memory owned by the handle */
+  double abar_z;       /* 3D: speed bound along z of the current state (2.19); 0 in 1D/2D */
 } lbmh_info;
 
 /* Validate the problem and allocate device memory for it.  *out receives a

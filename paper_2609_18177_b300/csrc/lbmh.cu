@@ -730,6 +730,7 @@ int lbmh_get_info(lbmh_handle* h, lbmh_info* out) {
   out->steps = c.nsteps[slot];
   out->abar[0] = bits_to_host(c.amax[slot][0]);
   out->abar[1] = bits_to_host(c.amax[slot][1]);
+  out->abar_z = h->dim == 3 ? bits_to_host(c.amax_z[slot]) : 0.0;
   out->last_dt = c.last_dt;
   out->last_lambda = c.last_lambda;
   out->status = c.status;

@@ -63,13 +63,14 @@ class Info(ctypes.Structure):
         ("sum_U", ctypes.c_double * 8),
         ("status", ctypes.c_uint32), ("m", ctypes.c_int), ("Q", ctypes.c_int),
         ("kernel", ctypes.c_int), ("device_bytes", ctypes.c_int64),
+        ("abar_z", ctypes.c_double),
     ]
 
     def as_dict(self):
         return {"t": self.t, "steps": self.steps, "abar": list(self.abar),
                 "last_dt": self.last_dt, "last_lambda": self.last_lambda,
                 "sum_U": list(self.sum_U)[: self.m], "status": self.status, "m": self.m,
-                "Q": self.Q, "kernel": self.kernel, "device_bytes": self.device_bytes}
+                "Q": self.Q, "kernel": self.kernel, "device_bytes": self.device_bytes, "abar_z": self.abar_z}
 
 
 _lib = None

@@ -143,3 +143,23 @@ def test_3d_int_and_64bit_offsets_give_the_same_bits(monkeypatch):
         assert np.array_equal(a.get_f(), b.get_f())
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("precision", [lbmh.FP64, lbmh.FP32], ids=["fp64", "fp32"])
+def test_3d_speed_bounds_reported(precision):
+    """lbmh_get_info reports the speed bound of the current state along x, y
+    and z (Eq. 2.19): max over nodes of |u_j| + c, recomputed here from the
+    state's moments."""
+    pb, U0 = case(W.EULER, W.OUTFLOW)
+    pb = pb.with_(precision=precision)
+    s = lbmh.Solver(pb, precision=precision).set_state(U0).step(7)
+    U = s.moments().reshape(5, -1)
+    rho, m, E = U[0], U[1:4], U[4]
+    p = (pb.gamma - 1.0) * (E - 0.5 * (m * m).sum(axis=0) / rho)
+    c = np.sqrt(pb.gamma * p / rho)
+    want = [float((np.abs(m[j] / rho) + c).max()) for j in range(3)]
+    inf = s.info()
+    got = [inf["abar"][0], inf["abar"][1], inf["abar_z"]]
+    tol = 1e-12 if precision == lbmh.FP64 else 1e-5
+    assert np.allclose(got, want, rtol=tol, atol=0.0), (got, want)
+    s.close()
