@@ -5,7 +5,6 @@ import ctypes
 import os
 import re
 import subprocess
-import tempfile
 
 import pytest
 
@@ -51,21 +50,26 @@ def test_struct_layout_matches_header():
 #include <stdio.h>
 #include "lbmh.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(lbmh_problem), offsetof(lbmh_problem, A),
-         offsetof(lbmh_problem, cuda_stream), sizeof(lbmh_info), offsetof(lbmh_info, status),
-         offsetof(lbmh_info, device_bytes));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(lbmh_problem), offsetof(lbmh_problem, A),
+         offsetof(lbmh_problem, cuda_stream), offsetof(lbmh_problem, sponge_width),
+         offsetof(lbmh_problem, u_in), offsetof(lbmh_problem, nz), offsetof(lbmh_problem, adv_z),
+         sizeof(lbmh_info), offsetof(lbmh_info, status), offsetof(lbmh_info, device_bytes),
+         offsetof(lbmh_info, abar_z));
   return 0;
 }
 '''
-    with tempfile.TemporaryDirectory() as d:
-        c = os.path.join(d, "t.c")
-        exe = os.path.join(d, "t")
-        open(c, "w").write(src)
-        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", exe, c])
-        vals = [int(v) for v in subprocess.check_output([exe], text=True).split()]
+    d = os.path.join(ROOT, "_build", "abi_check")  # git-ignored build folder
+    os.makedirs(d, exist_ok=True)
+    c = os.path.join(d, "t.c")
+    exe = os.path.join(d, "t")
+    with open(c, "w") as fh:
+        fh.write(src)
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", exe, c])
+    vals = [int(v) for v in subprocess.check_output([exe], text=True).split()]
     P, I = lbmh._Problem, lbmh.Info
-    assert vals == [ctypes.sizeof(P), P.A.offset, P.cuda_stream.offset, ctypes.sizeof(I),
-                    I.status.offset, I.device_bytes.offset]
+    assert vals == [ctypes.sizeof(P), P.A.offset, P.cuda_stream.offset, P.sponge_width.offset, P.u_in.offset,
+                    P.nz.offset, P.adv_z.offset, ctypes.sizeof(I), I.status.offset, I.device_bytes.offset,
+                    I.abar_z.offset]
 
 
 def _create(lib, pb, **kw):
