@@ -1,0 +1,55 @@
+"""Accuracy pin of the oracle's 3D (D3Q7) step: smooth periodic advection of
+sin(2 pi x) sin(2 pi y) sin(2 pi z) with a = (0.7, -0.45, 0.35), CFL 0.5, to
+t >= 0.1, against the exact solution (the translated initial profile).
+
+- omega fixed at 2: the scheme of Section 2 is second-order consistent; the
+  observed order reaches 2.
+- omega fixed at 1: the step is a Lax-Friedrichs step, first order.
+- adaptive omega (Eqs. 2.13-2.16): the error lies below the omega = 1 error,
+  and the observed order rises with resolution.  In 3D the box sum of Eq.
+  2.15 adds 27 nodes x 3 directions of indicator terms, so omega stays well
+  below 2 at these sizes.  That regime is pre-asymptotic, like the 2D orders
+  1.51 -> 1.91 of Table 5.3.
+"""
+import math
+
+import numpy as np
+
+import oracle
+from paper_2609_18177_b300 import workloads as W
+
+A = (0.7, -0.45, 0.35)
+
+
+def rel_l2_error(n, T=0.1, **kw):
+    pb = W.cube(W.ADVECTION, n, cfl=0.5, adv=A, bc=(W.PERIODIC,) * 4, bc_z=(W.PERIODIC, W.PERIODIC), **kw)
+    X, Y, Z = W.cell_centres_3d(pb)
+
+    def profile(t):
+        return (np.sin(2 * np.pi * (X - A[0] * t)) * np.sin(2 * np.pi * (Y - A[1] * t))
+                * np.sin(2 * np.pi * (Z - A[2] * t)))
+
+    r = oracle.Run(pb, profile(0.0)[None])
+    while r.t < T:
+        r.step(1)
+    ex = profile(r.t)
+    return float(np.linalg.norm(r.moments()[0] - ex) / np.linalg.norm(ex))
+
+
+def orders(errs):
+    return [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+
+
+SIZES = (16, 32, 64)
+
+
+def test_3d_smooth_advection_orders():
+    e2 = [rel_l2_error(n, omega_mode=1, omega_fixed=2.0) for n in SIZES]
+    e1 = [rel_l2_error(n, omega_mode=1, omega_fixed=1.0) for n in SIZES]
+    ea = [rel_l2_error(n) for n in SIZES]
+    o2, o1, oa = orders(e2), orders(e1), orders(ea)
+    assert o2[-1] > 1.9, (e2, o2)                      # second order at omega = 2
+    assert all(0.85 < o < 1.1 for o in o1), (e1, o1)   # Lax-Friedrichs: first order
+    assert all(a < b for a, b in zip(ea, e1)), (ea, e1)
+    assert all(a > c for a, c in zip(ea, e2)), (ea, e2)
+    assert oa[0] < oa[1] and oa[0] > 0.9, (ea, oa)     # pre-asymptotic, order rising
