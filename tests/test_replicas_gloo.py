@@ -30,7 +30,7 @@ def _rank(rank, world, port, out):
 
 def test_two_replicas_time_by_slowest_rank_and_count_all_updates():
     world = 2
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:  # no fork of this multi-threaded process
         out = mgr.dict()
         mp.spawn(_rank, args=(world, _free_port(), out), nprocs=world, join=True)
         res = dict(out)
