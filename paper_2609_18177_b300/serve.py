@@ -7,7 +7,9 @@ overlap on the device.  A request is admitted as soon as it has arrived and its
 lattice fits in its system's arena (first fit, by footprint); admitted lattices
 stay resident on the device until they finish, and finished ones are harvested
 (moments copied to the host) and removed between step chunks, which frees
-space for the next admissions.  Latency = harvest time - arrival time.
+space for the next admissions.  Latency = harvest time - arrival time.  A
+request withdrawn by its client (cancel_at) leaves the queue at once, or, if
+its lattice is resident, is removed at its batch's next harvest point.
 
 The scheduling logic is plain host code; every step runs in the CUDA library.
 """
@@ -32,6 +34,7 @@ class Request:
     steps: int
     seed: int
     arrival: float  # seconds after the start of the run
+    cancel_at: Optional[float] = None  # seconds after the start: withdrawn by its client then
 
 
 def make_problem(req: Request):
@@ -70,6 +73,7 @@ class Result:
     admitted: float
     finished: float
     U: Optional[np.ndarray] = None
+    cancelled: bool = False  # withdrawn before it finished: steps = those done (admitted NaN if never)
 
     @property
     def latency(self):
@@ -131,6 +135,15 @@ class Server:
                 queue[pending[nxt].kind].append(pending[nxt])
                 nxt += 1
             progressed = False
+            # withdrawn requests that were not admitted yet leave the queue
+            for k in KINDS:
+                keep = []
+                for req in queue[k]:
+                    if req.cancel_at is not None and req.cancel_at <= now:
+                        results.append(Result(req.rid, k, req.n, 0, req.arrival, float("nan"), now, None, True))
+                    else:
+                        keep.append(req)
+                queue[k] = keep
             for k in KINDS:
                 ev = inflight[k]
                 if ev is not None:
@@ -141,14 +154,16 @@ class Server:
                     # harvest finished lattices
                     done, t, steps, status = self.batches[k].poll()
                     for slot in list(live[k].keys()):
-                        if done[slot] == 1:
+                        req = live[k][slot][0]
+                        withdrawn = req.cancel_at is not None and req.cancel_at <= time.perf_counter() - t0
+                        if done[slot] == 1 or withdrawn:
                             req, adm = live[k].pop(slot)
-                            U = self.batches[k].moments(slot)
+                            U = self.batches[k].moments(slot) if done[slot] == 1 else None
                             fin = time.perf_counter() - t0
                             self.batches[k].remove(slot)
                             node_steps += req.n * req.n * int(steps[slot])
                             results.append(Result(req.rid, k, req.n, int(steps[slot]), req.arrival, adm, fin,
-                                                  U if self.keep_results else None))
+                                                  U if self.keep_results else None, bool(done[slot] != 1)))
                 # the batch is idle: admit (first fit by footprint, in arrival order)
                 kept = []
                 for req in queue[k]:
@@ -185,12 +200,14 @@ class Server:
             if inflight[k] is not None:
                 inflight[k].synchronize()
         makespan = time.perf_counter() - t0
-        lat = np.array([r.latency for r in results]) if results else np.zeros(1)
+        served = [r for r in results if not r.cancelled]
+        lat = np.array([r.latency for r in served]) if served else np.zeros(1)
         stats = {
-            "completed": len(results),
+            "completed": len(served),
+            "cancelled": len(results) - len(served),
             "submitted": len(trace),
             "makespan_s": makespan,
-            "solves_per_s": len(results) / makespan if makespan > 0 else 0.0,
+            "solves_per_s": len(served) / makespan if makespan > 0 else 0.0,
             "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)),
             "node_updates_per_s": node_steps / makespan if makespan > 0 else 0.0,

@@ -119,3 +119,31 @@ def test_slow_system_does_not_hold_the_others():
     # could not finish before reactive, whose chunks each wait 200 polls
     assert by["euler"].finished < by["reactive"].finished
     assert batches["euler"].step_calls == 10 and batches["reactive"].step_calls == 2
+
+
+def test_withdrawn_requests_leave_queue_and_batch():
+    """A request withdrawn before admission leaves the queue; one withdrawn
+    while resident is removed at its batch's next harvest point with the steps
+    it had done; the others are served as usual."""
+    trace = [S.Request(0, "swe", 64, 64, 0, 0.0),
+             S.Request(1, "swe", 64, 64, 1, 0.0, cancel_at=0.0),      # waits for the single slot
+             S.Request(2, "euler", 64, 3200, 2, 0.0, cancel_at=0.05)]  # 100 slow chunks
+    batches = {"euler": FakeBatch(slots=4), "swe": FakeBatch(slots=1), "reactive": FakeBatch(slots=4)}
+    last = {"k": None}
+    for k, b in batches.items():
+        orig = b.step
+
+        def step(n, _k=k, _orig=orig):
+            last["k"] = _k
+            _orig(n)
+        b.step = step
+    events = {"euler": lambda: FakeEvent(polls=20), "swe": lambda: FakeEvent(0), "reactive": lambda: FakeEvent(0)}
+    srv = S.Server(chunk=32, batches=batches, new_event=lambda: events[last["k"]](), keep_results=True)
+    results, stats = srv.run(trace, inputs=dummy_inputs(trace), max_seconds=20.0)
+    by = {r.rid: r for r in results}
+    assert stats["completed"] == 1 and stats["cancelled"] == 2 and len(results) == 3
+    assert not by[0].cancelled and by[0].steps == 64 and by[0].U is not None
+    assert by[1].cancelled and by[1].steps == 0 and by[1].admitted != by[1].admitted  # never admitted (NaN)
+    assert by[2].cancelled and 0 < by[2].steps < 3200 and by[2].steps % 32 == 0 and by[2].U is None
+    assert by[2].finished >= 0.05
+    assert all(not b.live for b in batches.values())
