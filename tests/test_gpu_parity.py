@@ -310,3 +310,16 @@ def test_fp32_root_on_subnormal_mass_fraction():
         s.close()
         s64.close()
     assert ms[1e-40] <= 1.5 * ms[1e-20], ms
+
+
+def test_device_allocation_failure_is_reported():
+    """A lattice whose distributions cannot be allocated (8.6e9 nodes: ~1.4 TB
+    for the two FP32 copies) fails in lbmh_create with LBMH_ERR_OOM, before any
+    kernel runs, and leaves the device usable."""
+    pb = W.Problem(system=W.EULER, dim=2, nx=92682, ny=92682, y1=1.0, bc=(W.OUTFLOW,) * 4)
+    with pytest.raises(lbmh.LbmhError) as ei:
+        lbmh.Solver(pb.with_(precision=lbmh.FP32), precision=lbmh.FP32)
+    assert ei.value.code == lbmh.ERR_OOM
+    pb2, U0 = make_case(W.EULER, 2, W.OUTFLOW)
+    s = lbmh.Solver(pb2, precision=lbmh.FP64).set_state(U0).step(2)
+    assert np.isfinite(s.moments()).all()
