@@ -143,6 +143,10 @@ typedef struct lbmh_info {
   int kernel;          /* implementation in use: LBMH_KERNEL_FUSED or _UNFUSED */
   int64_t device_bytes; /* device memory owned by the handle */
   double abar_z;       /* 3D: speed bound along z of the current state (2.19); 0 in 1D/2D */
+  /* slabs (lbmh_create_slab); zero for other handles */
+  int64_t halo_bytes;  /* bytes of one block of three halo rows (lbmh_halo_get / _set) */
+  int halo_rows[2];    /* halo rows below and above the rows the slab writes (0 or 3) */
+  int row0;            /* global row index of the slab's local row 0 */
 } lbmh_info;
 
 /* Validate the problem and allocate device memory for it.  *out receives a
@@ -182,9 +186,69 @@ LBMH_API int lbmh_get_info(lbmh_handle *h, lbmh_info *out);
 /* Free everything owned by the handle.  NULL is accepted. */
 LBMH_API int lbmh_destroy(lbmh_handle *h);
 
-/* Message of the last error on h (or of the last lbmh_create failure when h
- * is NULL).  Never NULL. */
+/* Message of the last error on h (or, when h is NULL, of the calling host
+ * thread's last failure without a handle: lbmh_create, lbmh_step_static).
+ * Never NULL. */
 LBMH_API const char *lbmh_last_error(const lbmh_handle *h);
+
+/* ------------------------------------------------------------------------
+ * Slabs: one 2D lattice decomposed along y into row ranges, one handle per
+ * range (one per GPU, the paper's "parallel multidimensional computations",
+ * Section 6).  The step of Eq. (2.2) needs f^n up to three nodes away, and its
+ * only global quantity is the speed bound abar_j of Eq. (2.19), a maximum
+ * over all nodes.  So a slab stores its rows plus three halo rows on each
+ * side that borders another slab, writes only its own rows, and per step:
+ *   1. the caller takes the maximum over the slabs of lbmh_get_speed_bound
+ *      and hands it to every slab with lbmh_set_speed_bound;
+ *   2. lbmh_step(h, 1) on every slab;
+ *   3. lbmh_halo_get of each side with a neighbour is passed to that
+ *      neighbour's lbmh_halo_set of the facing side.
+ * The initial state: each slab computes lbmh_state_speed_bound of its U0
+ * rows, the caller takes the maximum and calls lbmh_set_state_bound.  Node
+ * positions follow global rows and every node runs the arithmetic of the
+ * single-lattice step, so the slabs' rows hold the bits of the whole lattice
+ * stepped as one.  Slabs run the fused kernel (FP32 or FP64).
+ * ------------------------------------------------------------------------ */
+
+/* Create the slab holding rows [row_begin, row_end) (at least 3) of the 2D
+ * lattice `global`.  Its local lattice has (row_end - row_begin) rows plus 3
+ * halo rows on each side that borders another slab (a y-periodic lattice cut
+ * into several slabs: both sides); lbmh_get_info reports them.  U, f and
+ * moments of the handle cover the local lattice, halo rows included (their
+ * values after a step are those of the last lbmh_halo_set). */
+LBMH_API int lbmh_create_slab(const lbmh_problem *global, int row_begin, int row_end, lbmh_handle **out);
+
+/* Speed bound (Eq. 2.19) of a conservative state U (layout of
+ * lbmh_set_state) over the handle's nodes into abar_out[0..d-1].  The
+ * handle's state is unchanged.  Synchronises.  1D and 2D. */
+LBMH_API int lbmh_state_speed_bound(lbmh_handle *h, const double *U, int on_device, double *abar_out);
+
+/* As lbmh_set_state, with alpha^0 and lambda^0 of the initial equilibrium
+ * (Eq. 2.20, 2.21) taken from abar[0..d-1] (positive, finite) instead of U's
+ * own speed bound: a slab passes the maximum over all slabs.  1D and 2D. */
+LBMH_API int lbmh_set_state_bound(lbmh_handle *h, const double *U, int on_device, const double *abar);
+
+/* The speed bound the next step will use (Eq. 2.19: the side output of the
+ * previous step, over the nodes this handle writes) into abar_out[0..d-1].
+ * Synchronises. */
+LBMH_API int lbmh_get_speed_bound(lbmh_handle *h, double *abar_out);
+
+/* Replace the speed bound the next step uses to form dt, lambda and alpha_j
+ * (Eq. 2.19-2.21) by abar[0..d-1] (non-negative).  Enqueued on the handle's
+ * stream.  1D and 2D. */
+LBMH_API int lbmh_set_speed_bound(lbmh_handle *h, const double *abar);
+
+/* Slabs: the three rows of the current state next to side `side` (0: low y,
+ * 1: high y) among the rows the slab writes -- the rows the neighbour across
+ * that side keeps as its halo -- copied into `rows` (lbmh_info.halo_bytes
+ * bytes: all Q*m planes, three whole padded rows each, in the storage
+ * precision; host or device).  A host copy synchronises.
+ * LBMH_ERR_INVALID_ARG on a side without a neighbour. */
+LBMH_API int lbmh_halo_get(lbmh_handle *h, int side, void *rows, int on_device);
+
+/* Slabs: store a neighbour's lbmh_halo_get block as the halo rows beyond side
+ * `side`.  Synchronises. */
+LBMH_API int lbmh_halo_set(lbmh_handle *h, int side, const void *rows, int on_device);
 
 /* ------------------------------------------------------------------------
  * Batches: many 2D lattices of one system and precision, of uneven sizes,
@@ -250,23 +314,31 @@ LBMH_API const char *lbmh_batch_last_error(const lbmh_batch *b);
  * frozen pool, or real-time loops that cannot afford the implicit device
  * synchronisation an allocation may cause.  No handle is needed.
  *
- * f_in, f_out: distinct device arrays, FP64 [Q][m][ny][nx] (the layout of
- * lbmh_get_f); the step reads f_in and writes f_out.  The speed bound, time
- * step and lambda are computed from f_in (Eq. 2.19, 2.21).  dt_out: NULL, or
- * a host pointer that receives the step's dt; when given, the call
+ * f_in, f_out: distinct, non-overlapping device arrays of exactly
+ * Q*m*ny*nx doubles each, FP64 [Q][m][ny][nx] (the layout of lbmh_get_f;
+ * ny = 1 in 1D), on the current device; the step reads f_in and writes f_out.
+ * The library cannot check their sizes: a smaller array makes the kernels
+ * read or write past it.  dt, lambda and the speed bound are computed from
+ * f_in exactly as lbmh_step computes them for a handle's state.
+ * dt_out, status_out: NULL, or host pointers that receive the step's dt and
+ * its status bits (those of lbmh_info.status: non-physical state, reaction
+ * root not converged, negative depth); when either is given the call
  * synchronises the stream and returns LBMH_ERR_NONPHYSICAL if the new state
  * is non-physical.  Only LBMH_FP64 is accepted.
  *
  * The intermediate arrays live in one static device array of 16 MiB that
  * every GPU loading this library holds until the process exits; grids whose
  * ghost-extended scratch does not fit ((nx+6)(ny+6)(m+2) doubles plus a few
- * KB) are rejected with LBMH_ERR_INVALID_ARG.  The first call on a device
- * looks the array up (cudaGetSymbolAddress), so make that first call before
- * any stream capture.  All calls share the array and each call clears the
- * part that must start from zero: calls that may overlap on the GPU (other
- * streams, other host threads) race with each other and must be serialised
- * by the caller. */
-LBMH_API int lbmh_step_static(const lbmh_problem *p, const double *f_in, double *f_out, double *dt_out);
+ * KB) are rejected with LBMH_ERR_INVALID_ARG.  Outside a stream capture each
+ * call looks the array's device address up (cudaGetSymbolAddress); under a
+ * capture the address found by an earlier call on the same device is used,
+ * so make one call on each device before capturing.  All calls share the
+ * array and each call clears the part that must start from zero: calls that
+ * may overlap on the GPU (other streams, other host threads) race with each
+ * other and must be serialised by the caller.  Errors are reported through
+ * lbmh_last_error(NULL), which keeps one message per host thread. */
+LBMH_API int lbmh_step_static(const lbmh_problem *p, const double *f_in, double *f_out, double *dt_out,
+                              uint32_t *status_out);
 
 /* Library version string. */
 LBMH_API const char *lbmh_version(void);

@@ -22,6 +22,12 @@ struct Fields {
 // [nx, nx+4)) are ghost nodes: the fused 2D kernel keeps them equal to the
 // wrapped / clamped node after each step, so a row of any strip can be
 // fetched with one in-bounds, aligned TMA box.
+// The unfused kernels (unfused.cuh) address only columns [0, nx): every
+// column they read or write is cell(P, i, j) with i = map_index(...) in
+// [0, nx) for periodic, outflow and reflecting sides.  The allocation-free
+// step relies on this to run them on unpadded [..][ny][nx] arrays, with
+// pitch = nx and the base pointers shifted by -XPAD, which they never
+// dereference.
 constexpr int XPAD = 8;
 constexpr int NGHOST = 4;
 
@@ -65,6 +71,14 @@ struct DevParams {
   int ny3, nz3;
   int bc_z[2];
   double z0, adv_z;
+  // Rows the 2D single-lattice step writes: [ywin0, ywin1) (the whole lattice,
+  // 0..ny, except for a slab of a lattice decomposed along y, whose three rows
+  // next to a neighbouring slab are halo rows: read, never written).  row0 is
+  // the global index of local row 0 (0 except for slabs): node positions (the
+  // bed source) use global rows, so a slab computes the bits of the whole
+  // lattice.
+  int ywin0, ywin1;
+  int row0;
   PhysConstF pf;
 };
 

@@ -519,7 +519,7 @@ __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml
           flux<SYS, 2, R>(K, U2[j], w2[j], 1, Fy);
           if constexpr (SRC) {
             const int my2 = pos_index(r - 2, P.ny, P.bc[2], P.bc[3]);
-            source<SYS, 2, R>(K, U2[j], xr_ghost[j], K.yb + R(my2) * K.dx, Sr);
+            source<SYS, 2, R>(K, U2[j], xr_ghost[j], K.yb + R(my2 + P.row0) * K.dx, Sr);
           }
   #pragma unroll
           for (int c = 0; c < M; c++) {
@@ -570,7 +570,7 @@ __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml
           R Us[M];  // moments of the stored f^{n+1}, summed k = 0..Q-1 as the next step does
           if constexpr (SRC) {
             R Un[M], Sn[M];
-            const R yr = K.yb + R(y) * K.dx;
+            const R yr = K.yb + R(y + P.row0) * K.dx;
             unsigned stn = 0u;
             if (outc[j]) {
               stn = implicit_moment<SYS, 2, R>(K, Ubar, xr_out[j], yr, cc.dt, hdt, Un);
@@ -712,17 +712,18 @@ __global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensor
   for (int c = 0; c < M; c++) acc[c].init();
   unsigned st = 0u;
 
-  const long long total = (long long)strips * P.ny;
+  const int nyw = P.ywin1 - P.ywin0;  // rows written: the window [ywin0, ywin1)
+  const long long total = (long long)strips * nyw;
   const long long wb = total * blockIdx.x / gridDim.x, we = total * (blockIdx.x + 1) / gridDim.x;
-  const int nbands = (P.ny + band - 1) / band;
-  const int last_rows = P.ny - (nbands - 1) * band;
+  const int nbands = (nyw + band - 1) / band;
+  const int last_rows = nyw - (nbands - 1) * band;
   for (long long w = wb; w < we && !pp.aborted;) {
     const int b = (int)(w / ((long long)strips * band));
     const int rb = b == nbands - 1 ? last_rows : band;
     const long long local = w - (long long)b * strips * band;
     const int strip = (int)(local / rb);
-    const int yb = b * band + (int)(local % rb);
-    const int ye = (int)min((long long)(b * band + rb), (long long)yb + (we - w));
+    const int yb = P.ywin0 + b * band + (int)(local % rb);
+    const int ye = (int)min((long long)(P.ywin0 + b * band + rb), (long long)yb + (we - w));
     w += ye - yb;
     run_segment2d<SYS, R, PREF, CPT>(pp, tml, tms, fout, P, K, cc, strip, yb, ye, nxs, sp0, sp1, acc, st);
   }
@@ -940,11 +941,12 @@ inline int fused2d_prepare(FusedPlan& fp, const DevParams& P, void* const* fbuf,
   // one resident wave; every CTA gets the same number of (strip, row) units,
   // at least 16 rows each
   long long slots = (long long)per_sm * sms;
-  long long total = (long long)fp.strips * P.ny;
+  const int nyw = P.ywin1 - P.ywin0;
+  long long total = (long long)fp.strips * nyw;
   long long cap = total / 16 > 0 ? total / 16 : 1;
   fp.blocks = (int)(slots < cap ? slots : cap);
   long long chunk = (total + fp.blocks - 1) / fp.blocks;
-  fp.band = (int)(chunk < 16 ? 16 : (chunk > P.ny ? P.ny : chunk));
+  fp.band = (int)(chunk < 16 ? 16 : (chunk > nyw ? nyw : chunk));
   return encode_maps<R>(fp, P, fbuf, QM, L::NC, L::WOUT);
   return 0;
 }

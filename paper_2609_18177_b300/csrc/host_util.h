@@ -98,6 +98,9 @@ inline DevParams make_devparams(const lbmh_problem* p, int pitch) {
   P.ny = P.ny3 * P.nz3;  // rows (z outer) in 3D
   P.pitch = pitch;
   P.plane = (long long)P.ny * P.pitch;
+  P.ywin0 = 0;
+  P.ywin1 = P.ny;
+  P.row0 = 0;
   for (int s = 0; s < 4; s++) P.bc[s] = p->bc[s];
   if (p->dim == 1) P.bc[2] = P.bc[3] = LBMH_BC_PERIODIC;
   P.bc_z[0] = p->dim == 3 ? p->bc_z[0] : LBMH_BC_PERIODIC;

@@ -2,6 +2,7 @@
 // the template dispatch over (system, dimension, precision).
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -60,12 +61,15 @@ struct lbmh_handle {
   cudaGraphExec_t graph;
   double graph_T;
   bool graph_failed;
+  int halo_lo, halo_hi;     // slab of a lattice decomposed along y: halo rows below / above the window
   std::string err;
 };
 
 namespace {
 
-std::string g_create_error;
+// message of the last failure that had no handle (lbmh_create, lbmh_step_static),
+// kept per host thread so that concurrent callers do not read each other's
+thread_local std::string g_create_error;
 
 int fail(lbmh_handle* h, int code, const std::string& msg) {
   if (h) h->err = msg; else g_create_error = msg;
@@ -75,6 +79,10 @@ int fail(lbmh_handle* h, int code, const std::string& msg) {
 int cuda_fail(lbmh_handle* h, cudaError_t e, const char* what) {
   return fail(h, LBMH_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
+
+int set_state_impl(lbmh_handle* h, const double* U, int on_device, const double* abar);
+size_t halo_bytes(const lbmh_handle* h);
+__global__ void k_set_bound(Ctl* ctl, int slot, unsigned long long b0, unsigned long long b1);
 
 #define CK(h, call)                                    \
   do {                                                 \
@@ -90,7 +98,7 @@ int cuda_fail(lbmh_handle* h, cudaError_t e, const char* what) {
 struct Ops {
   int (*launch_step)(lbmh_handle*, int slot, double T);
   int (*launch_unfused_diag)(lbmh_handle*, int slot);  // K0..K2 only
-  int (*init)(lbmh_handle*, const double* U0dev);
+  int (*init)(lbmh_handle*, const double* U0dev, bool bound_given);  // bound_given: ctl->ainit is set
   int (*moments)(lbmh_handle*, int slot, double* Udev);
   int (*get_f)(lbmh_handle*, int slot, double* dev);
   int (*set_f)(lbmh_handle*, const double* dev);
@@ -145,10 +153,10 @@ struct Impl {
     return LBMH_OK;
   }
 
-  static int init(lbmh_handle* h, const double* U0dev) {
+  static int init(lbmh_handle* h, const double* U0dev, bool bound_given) {
     long long nn = (long long)h->P.nx * h->P.ny;
     unsigned nb = reduce_blocks_for(nn);
-    k_init_speed<SYS, D><<<nb, kBlock, 0, h->stream>>>(h->P, U0dev, h->ctl);
+    if (!bound_given) k_init_speed<SYS, D><<<nb, kBlock, 0, h->stream>>>(h->P, U0dev, h->ctl);
     k_init_eq<SYS, D, R><<<nb, kBlock, 0, h->stream>>>(h->P, U0dev, (R*)h->fbuf[0], h->ctl);
     fill_pads(h, (R*)h->fbuf[0]);
     cudaError_t e = cudaGetLastError();
@@ -241,10 +249,10 @@ struct Impl3 {
     return fail(h, LBMH_ERR_UNSUPPORTED, "the omega diagnostic is not provided for 3D lattices");
   }
 
-  static int init(lbmh_handle* h, const double* U0dev) {
+  static int init(lbmh_handle* h, const double* U0dev, bool bound_given) {
     const long long nn = (long long)h->P.nx * h->P.ny;
     const unsigned nb = reduce_blocks_for(nn);
-    k3_init_speed<SYS><<<nb, kBlock, 0, h->stream>>>(h->P, U0dev, h->ctl);
+    if (!bound_given) k3_init_speed<SYS><<<nb, kBlock, 0, h->stream>>>(h->P, U0dev, h->ctl);
     k3_init_eq<SYS, R><<<nb, kBlock, 0, h->stream>>>(h->P, U0dev, (R*)h->fbuf[0], h->ctl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "3D init launch");
@@ -458,7 +466,17 @@ const char* lbmh_version(void) { return "lbmh 0.1 sm_103a"; }
 
 const char* lbmh_last_error(const lbmh_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
-int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
+}  // extern "C"
+
+namespace {
+
+// rows of a slab of a lattice decomposed along y, in its local lattice
+struct SlabGeom {
+  int halo_lo, halo_hi;  // halo rows below / above the rows it writes (0 or 3)
+  int row0;              // global row of local row 0
+};
+
+int create_impl(const lbmh_problem* p, const SlabGeom* sg, lbmh_handle** out) {
   if (!out) return fail(nullptr, LBMH_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   std::string why;
@@ -468,6 +486,7 @@ int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
   memset(h->fbuf, 0, sizeof h->fbuf);
   h->dbuf = nullptr; h->Ue = h->nue = h->ome = nullptr; h->partials = nullptr; h->ctl = nullptr; h->Utmp = nullptr;
   h->cap_stream = nullptr; h->graph = nullptr; h->graph_T = 0.0; h->graph_failed = false; h->u3_valid = false;
+  h->halo_lo = h->halo_hi = 0;
   {  // LBMH_3D_INDEX64=1 selects the 64-bit-offset collision kernel at any size (for tests)
     const char* e = getenv("LBMH_3D_INDEX64");
     h->idx64_3d = e && e[0] == '1';
@@ -488,6 +507,13 @@ int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
   h->P = make_devparams(p, padded_pitch(p->nx, h->elem));
   DevParams& P = h->P;
   h->plane = P.plane;
+  h->halo_lo = sg ? sg->halo_lo : 0;
+  h->halo_hi = sg ? sg->halo_hi : 0;
+  if (sg) {
+    P.ywin0 = sg->halo_lo;
+    P.ywin1 = P.ny - sg->halo_hi;
+    P.row0 = sg->row0;
+  }
 
   bool want_fused = p->kernel != LBMH_KERNEL_UNFUSED;
   if (p->kernel == LBMH_KERNEL_FUSED && !h->ops->has_fused) {
@@ -554,6 +580,12 @@ int lbmh_create(const lbmh_problem* p, lbmh_handle** out) {
   return LBMH_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int lbmh_create(const lbmh_problem* p, lbmh_handle** out) { return create_impl(p, nullptr, out); }
+
 int lbmh_destroy(lbmh_handle* h) {
   if (!h) return LBMH_OK;
   cudaStreamSynchronize(h->stream);
@@ -561,7 +593,24 @@ int lbmh_destroy(lbmh_handle* h) {
   return LBMH_OK;
 }
 
-int lbmh_set_state(lbmh_handle* h, const double* U, int on_device) {
+int lbmh_set_state(lbmh_handle* h, const double* U, int on_device) { return set_state_impl(h, U, on_device, nullptr); }
+
+int lbmh_set_state_bound(lbmh_handle* h, const double* U, int on_device, const double* abar) {
+  if (!h) return LBMH_ERR_INVALID_ARG;
+  if (!abar) return fail(h, LBMH_ERR_INVALID_ARG, "abar is NULL");
+  if (h->dim == 3) return fail(h, LBMH_ERR_UNSUPPORTED, "lbmh_set_state_bound serves 1D and 2D lattices");
+  for (int j = 0; j < h->dim; j++)
+    if (!(abar[j] > 0.0) || !std::isfinite(abar[j])) return fail(h, LBMH_ERR_INVALID_ARG, "abar must be positive and finite");
+  return set_state_impl(h, U, on_device, abar);
+}
+
+}  // extern "C"
+
+namespace {
+
+// f := f^eq(U) (Eq. 2.20) with alpha^0, lambda^0 from U's speed bound, or from
+// abar when given (then already in host memory: staged by the copy below)
+int set_state_impl(lbmh_handle* h, const double* U, int on_device, const double* abar) {
   if (!h) return LBMH_ERR_INVALID_ARG;
   if (!U) return fail(h, LBMH_ERR_INVALID_ARG, "U is NULL");
   h->err.clear();
@@ -575,8 +624,11 @@ int lbmh_set_state(lbmh_handle* h, const double* U, int on_device) {
     src = h->Utmp;
   }
   CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->stream));
+  if (abar)
+    CK(h, cudaMemcpyAsync((char*)h->ctl + offsetof(Ctl, ainit), abar, h->dim * sizeof(double), cudaMemcpyHostToDevice,
+                          h->stream));
   h->u3_valid = false;
-  int rc = h->ops->init(h, src);
+  int rc = h->ops->init(h, src, abar != nullptr);
   if (rc) return rc;
   if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
   h->launched = 0;
@@ -584,6 +636,10 @@ int lbmh_set_state(lbmh_handle* h, const double* U, int on_device) {
   h->nblocks = 0;
   return LBMH_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int lbmh_step(lbmh_handle* h, int64_t n) {
   if (!h) return LBMH_ERR_INVALID_ARG;
@@ -721,6 +777,12 @@ int lbmh_get_info(lbmh_handle* h, lbmh_info* out) {
   out->Q = h->Q;
   out->kernel = h->kernel;
   out->device_bytes = h->device_bytes;
+  if (h->halo_lo || h->halo_hi) {
+    out->halo_bytes = (int64_t)halo_bytes(h);
+    out->halo_rows[0] = h->halo_lo;
+    out->halo_rows[1] = h->halo_hi;
+    out->row0 = h->P.row0;
+  }
   if (!h->has_state) return LBMH_OK;
   Ctl c;
   int rc = read_ctl(h, &c);
@@ -741,6 +803,175 @@ int lbmh_get_info(lbmh_handle* h, lbmh_info* out) {
       for (int c2 = 0; c2 < h->m && c2 < 8; c2++) out->sum_U[c2] += part[(size_t)b * h->m + c2];
   }
   return LBMH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Slabs: one 2D lattice decomposed along y into row ranges, one handle per
+// range (one per GPU).  A slab stores its rows plus three halo rows on each
+// side that borders another slab, and writes only its own rows; per step the
+// caller (1) takes the maximum of the slabs' speed bounds (Eq. 2.19: the
+// maximum over x is global), (2) steps every slab, (3) copies each slab's
+// three outermost rows into the neighbour's halo.  Node positions use global
+// rows and every node runs the single-lattice arithmetic, so the slabs hold
+// the bits of the whole lattice.
+// ---------------------------------------------------------------------------
+
+int lbmh_create_slab(const lbmh_problem* g, int row_begin, int row_end, lbmh_handle** out) {
+  if (!out) return fail(nullptr, LBMH_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  int rc = validate(g, why);
+  if (rc) return fail(nullptr, rc, why);
+  if (g->dim != 2) return fail(nullptr, LBMH_ERR_UNSUPPORTED, "slabs decompose 2D lattices");
+  if (g->kernel == LBMH_KERNEL_UNFUSED) return fail(nullptr, LBMH_ERR_UNSUPPORTED, "slabs run the fused kernel");
+  if (row_begin < 0 || row_end > g->ny || row_end - row_begin < 3)
+    return fail(nullptr, LBMH_ERR_INVALID_ARG, "a slab needs rows [row_begin, row_end) within the lattice, at least 3");
+  const bool whole = row_begin == 0 && row_end == g->ny;
+  const bool periodic = g->bc[2] == LBMH_BC_PERIODIC;
+  SlabGeom sg;
+  sg.halo_lo = !whole && (row_begin > 0 || periodic) ? 3 : 0;
+  sg.halo_hi = !whole && (row_end < g->ny || periodic) ? 3 : 0;
+  sg.row0 = row_begin - sg.halo_lo;
+  lbmh_problem lp = *g;
+  const double dy = (g->y1 - g->y0) / g->ny;
+  lp.ny = row_end - row_begin + sg.halo_lo + sg.halo_hi;
+  lp.y1 = g->y0 + lp.ny * dy;  // positions come from global rows: y0 stays the lattice's
+  if (sg.halo_lo) lp.bc[2] = LBMH_BC_OUTFLOW;  // never read: the rows beyond a halo are not needed
+  if (sg.halo_hi) lp.bc[3] = LBMH_BC_OUTFLOW;
+  lp.kernel = LBMH_KERNEL_FUSED;
+  return create_impl(&lp, &sg, out);
+}
+
+int lbmh_state_speed_bound(lbmh_handle* h, const double* U, int on_device, double* abar_out) {
+  if (!h) return LBMH_ERR_INVALID_ARG;
+  if (!U || !abar_out) return fail(h, LBMH_ERR_INVALID_ARG, "U and abar_out must not be NULL");
+  if (h->dim == 3) return fail(h, LBMH_ERR_UNSUPPORTED, "lbmh_state_speed_bound serves 1D and 2D lattices");
+  h->err.clear();
+  const long long nn = (long long)h->P.nx * h->P.ny;
+  const size_t bytes = (size_t)nn * h->m * sizeof(double);
+  const double* src = U;
+  if (!on_device) {
+    int rc0 = ensure_utmp(h, bytes);
+    if (rc0) return rc0;
+    CK(h, cudaMemcpyAsync(h->Utmp, U, bytes, cudaMemcpyHostToDevice, h->stream));
+    src = h->Utmp;
+  }
+  // ctl->ainit is read only while a state is initialised, so it serves as the
+  // reduction target here
+  CK(h, cudaMemsetAsync((char*)h->ctl + offsetof(Ctl, ainit), 0, 2 * sizeof(double), h->stream));
+  const unsigned nb = reduce_blocks_for(nn);
+  switch (h->sys * 2 + (h->dim - 1)) {
+    case SYS_ADV * 2 + 0: k_init_speed<SYS_ADV, 1><<<nb, kBlock, 0, h->stream>>>(h->P, src, h->ctl); break;
+    case SYS_ADV * 2 + 1: k_init_speed<SYS_ADV, 2><<<nb, kBlock, 0, h->stream>>>(h->P, src, h->ctl); break;
+    case SYS_EULER * 2 + 0: k_init_speed<SYS_EULER, 1><<<nb, kBlock, 0, h->stream>>>(h->P, src, h->ctl); break;
+    case SYS_EULER * 2 + 1: k_init_speed<SYS_EULER, 2><<<nb, kBlock, 0, h->stream>>>(h->P, src, h->ctl); break;
+    case SYS_SWE * 2 + 0: k_init_speed<SYS_SWE, 1><<<nb, kBlock, 0, h->stream>>>(h->P, src, h->ctl); break;
+    case SYS_SWE * 2 + 1: k_init_speed<SYS_SWE, 2><<<nb, kBlock, 0, h->stream>>>(h->P, src, h->ctl); break;
+    case SYS_REACT * 2 + 0: k_init_speed<SYS_REACT, 1><<<nb, kBlock, 0, h->stream>>>(h->P, src, h->ctl); break;
+    case SYS_REACT * 2 + 1: k_init_speed<SYS_REACT, 2><<<nb, kBlock, 0, h->stream>>>(h->P, src, h->ctl); break;
+    default: return fail(h, LBMH_ERR_INVALID_ARG, "unknown system");
+  }
+  CK(h, cudaGetLastError());
+  double a[2] = {0.0, 0.0};
+  CK(h, cudaMemcpyAsync(a, (char*)h->ctl + offsetof(Ctl, ainit), sizeof a, cudaMemcpyDeviceToHost, h->stream));
+  int rc = sync(h);
+  if (rc) return rc;
+  for (int j = 0; j < h->dim; j++) abar_out[j] = a[j];
+  return LBMH_OK;
+}
+
+int lbmh_get_speed_bound(lbmh_handle* h, double* abar_out) {
+  if (!h || !abar_out) return LBMH_ERR_INVALID_ARG;
+  if (!h->has_state) return fail(h, LBMH_ERR_INVALID_ARG, "no state");
+  Ctl c;
+  int rc = read_ctl(h, &c);
+  if (rc) return rc;
+  const int slot = current_slot(h);
+  abar_out[0] = bits_to_host(c.amax[slot][0]);
+  if (h->dim >= 2) abar_out[1] = bits_to_host(c.amax[slot][1]);
+  if (h->dim == 3) abar_out[2] = bits_to_host(c.amax_z[slot]);
+  return LBMH_OK;
+}
+
+int lbmh_set_speed_bound(lbmh_handle* h, const double* abar) {
+  if (!h || !abar) return LBMH_ERR_INVALID_ARG;
+  if (!h->has_state) return fail(h, LBMH_ERR_INVALID_ARG, "no state");
+  if (h->dim == 3) return fail(h, LBMH_ERR_UNSUPPORTED, "lbmh_set_speed_bound serves 1D and 2D lattices");
+  for (int j = 0; j < h->dim; j++)
+    if (!(abar[j] >= 0.0)) return fail(h, LBMH_ERR_INVALID_ARG, "abar must be non-negative");
+  union {
+    double d;
+    unsigned long long u;
+  } b0, b1;
+  b0.d = abar[0];
+  b1.d = h->dim == 2 ? abar[1] : 0.0;
+  k_set_bound<<<1, 1, 0, h->stream>>>(h->ctl, current_slot(h), b0.u, b1.u);
+  CK(h, cudaGetLastError());
+  return LBMH_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// the speed bound the step reading `slot` uses (bit patterns of non-negative
+// doubles, as the side outputs store them)
+__global__ void k_set_bound(Ctl* ctl, int slot, unsigned long long b0, unsigned long long b1) {
+  ctl->amax[slot][0] = b0;
+  ctl->amax[slot][1] = b1;
+}
+
+// three rows of every plane of the current state <-> a contiguous block
+int halo_copy(lbmh_handle* h, int row, void* dev_rows, bool to_rows) {
+  const long long n = 3ll * h->P.pitch * h->Q * h->m;
+  if (h->prec == LBMH_FP32)
+    k_halo_rows<float><<<blocks_for(n), kBlock, 0, h->stream>>>(h->P, h->Q * h->m, (float* const*)h->dbuf, h->ctl,
+                                                                current_slot(h), row, (float*)dev_rows, to_rows);
+  else
+    k_halo_rows<double><<<blocks_for(n), kBlock, 0, h->stream>>>(h->P, h->Q * h->m, (double* const*)h->dbuf, h->ctl,
+                                                                 current_slot(h), row, (double*)dev_rows, to_rows);
+  CK(h, cudaGetLastError());
+  return LBMH_OK;
+}
+
+size_t halo_bytes(const lbmh_handle* h) { return (size_t)3 * h->P.pitch * h->Q * h->m * h->elem; }
+
+}  // namespace
+
+extern "C" {
+
+int lbmh_halo_get(lbmh_handle* h, int side, void* rows, int on_device) {
+  if (!h) return LBMH_ERR_INVALID_ARG;
+  if (!rows || (side != 0 && side != 1)) return fail(h, LBMH_ERR_INVALID_ARG, "rows is NULL or side is not 0/1");
+  if (!h->has_state) return fail(h, LBMH_ERR_INVALID_ARG, "no state");
+  if ((side == 0 ? h->halo_lo : h->halo_hi) == 0) return fail(h, LBMH_ERR_INVALID_ARG, "no neighbouring slab on that side");
+  h->err.clear();
+  const size_t bytes = halo_bytes(h);
+  const int row = side == 0 ? h->P.ywin0 : h->P.ywin1 - 3;
+  if (on_device) return halo_copy(h, row, rows, true);
+  int rc = ensure_utmp(h, bytes);
+  if (rc) return rc;
+  rc = halo_copy(h, row, h->Utmp, true);
+  if (rc) return rc;
+  CK(h, cudaMemcpyAsync(rows, h->Utmp, bytes, cudaMemcpyDeviceToHost, h->stream));
+  return sync(h);
+}
+
+int lbmh_halo_set(lbmh_handle* h, int side, const void* rows, int on_device) {
+  if (!h) return LBMH_ERR_INVALID_ARG;
+  if (!rows || (side != 0 && side != 1)) return fail(h, LBMH_ERR_INVALID_ARG, "rows is NULL or side is not 0/1");
+  if (!h->has_state) return fail(h, LBMH_ERR_INVALID_ARG, "no state");
+  if ((side == 0 ? h->halo_lo : h->halo_hi) == 0) return fail(h, LBMH_ERR_INVALID_ARG, "no neighbouring slab on that side");
+  h->err.clear();
+  const size_t bytes = halo_bytes(h);
+  const int row = side == 0 ? h->P.ywin0 - 3 : h->P.ywin1;
+  if (on_device) return halo_copy(h, row, const_cast<void*>(rows), false);
+  int rc = ensure_utmp(h, bytes);
+  if (rc) return rc;
+  CK(h, cudaMemcpyAsync(h->Utmp, rows, bytes, cudaMemcpyHostToDevice, h->stream));
+  rc = halo_copy(h, row, h->Utmp, false);
+  if (rc) return rc;
+  return sync(h);  // the staging buffer is reused by the next host transfer
 }
 
 }  // extern "C"
@@ -790,7 +1021,8 @@ void static_step_launch(const DevParams& P, const ExtGeom& G, Ctl* ctl, double* 
 
 }  // namespace
 
-extern "C" int lbmh_step_static(const lbmh_problem* p, const double* f_in, double* f_out, double* dt_out) {
+extern "C" int lbmh_step_static(const lbmh_problem* p, const double* f_in, double* f_out, double* dt_out,
+                                uint32_t* status_out) {
   std::string why;
   int rc = validate(p, why);
   if (rc) return fail(nullptr, rc, why);
@@ -823,15 +1055,26 @@ extern "C" int lbmh_step_static(const lbmh_problem* p, const double* f_in, doubl
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(nullptr, LBMH_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, LBMH_ERR_UNSUPPORTED, "device index beyond the static table");
+  cudaStream_t stream = (cudaStream_t)p->cuda_stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess) return fail(nullptr, LBMH_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
   void* base = nullptr;
   {
+    // Outside a capture the array's device address is looked up on every call
+    // (a context torn down and recreated may place the module elsewhere); under
+    // a capture, where the lookup may not run, the address cached by an earlier
+    // call on this device is used.
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {  // first call on this device: look the array up once
-      e = cudaGetSymbolAddress(&g_static_addr[dev], g_static_scratch);
-      if (e != cudaSuccess) {
-        g_static_addr[dev] = nullptr;
+    if (cap == cudaStreamCaptureStatusNone) {
+      void* a = nullptr;
+      e = cudaGetSymbolAddress(&a, g_static_scratch);
+      if (e != cudaSuccess)
         return fail(nullptr, LBMH_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      }
+      g_static_addr[dev] = a;
+    } else if (!g_static_addr[dev]) {
+      return fail(nullptr, LBMH_ERR_INVALID_ARG,
+                  "lbmh_step_static under stream capture needs an earlier call on this device outside a capture");
     }
     base = g_static_addr[dev];
   }
@@ -842,7 +1085,6 @@ extern "C" int lbmh_step_static(const lbmh_problem* p, const double* f_in, doubl
   double* Ue = (double*)(b + off_U);
   double* nue = (double*)(b + off_nu);
   double* ome = (double*)(b + off_om);
-  cudaStream_t stream = (cudaStream_t)p->cuda_stream;
 
   // the kernels address node (i, j) of plane q at q*plane + j*pitch + i + XPAD;
   // shifting the base pointers by -XPAD maps that onto the unpadded arrays
@@ -860,12 +1102,13 @@ extern "C" int lbmh_step_static(const lbmh_problem* p, const double* f_in, doubl
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(nullptr, LBMH_ERR_CUDA, std::string("static step launch: ") + cudaGetErrorString(e));
-  if (dt_out) {
+  if (dt_out || status_out) {
     Ctl c;
     e = cudaMemcpyAsync(&c, ctl, sizeof c, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return fail(nullptr, LBMH_ERR_CUDA, std::string("static step readback: ") + cudaGetErrorString(e));
-    *dt_out = c.last_dt;
+    if (dt_out) *dt_out = c.last_dt;
+    if (status_out) *status_out = c.status;
     if (c.status & ST_NONPHYSICAL) return fail(nullptr, LBMH_ERR_NONPHYSICAL, "the step produced a non-physical state");
   }
   (void)Q;

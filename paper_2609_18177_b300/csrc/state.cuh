@@ -215,4 +215,22 @@ __global__ void k_extract_interior(DevParams P, ExtGeom G, const R* src_ext, dou
   out[node] = (double)src_ext[G.idx(j + G.gy, i + GH)];
 }
 
+// Slabs of a lattice decomposed along y: copy the three padded rows
+// [row, row + 3) of every distribution plane of the current state between the
+// lattice and a contiguous block rows[QM][3][pitch] (to_rows: lattice -> block)
+template <class R>
+__global__ void k_halo_rows(DevParams P, int QM, R* const* buf, const Ctl* ctl, int slot, int row, R* rows,
+                            int to_rows) {
+  const long long per = 3ll * P.pitch;
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= per * QM) return;
+  R* f = buf[ctl->parity[slot]];
+  const long long q = idx / per, r = idx % per;
+  R* a = f + q * P.plane + (long long)row * P.pitch + r;
+  if (to_rows)
+    rows[idx] = *a;
+  else
+    *a = rows[idx];
+}
+
 }  // namespace lbmh

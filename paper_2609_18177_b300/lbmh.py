@@ -64,13 +64,15 @@ class Info(ctypes.Structure):
         ("status", ctypes.c_uint32), ("m", ctypes.c_int), ("Q", ctypes.c_int),
         ("kernel", ctypes.c_int), ("device_bytes", ctypes.c_int64),
         ("abar_z", ctypes.c_double),
+        ("halo_bytes", ctypes.c_int64), ("halo_rows", ctypes.c_int * 2), ("row0", ctypes.c_int),
     ]
 
     def as_dict(self):
         return {"t": self.t, "steps": self.steps, "abar": list(self.abar),
                 "last_dt": self.last_dt, "last_lambda": self.last_lambda,
                 "sum_U": list(self.sum_U)[: self.m], "status": self.status, "m": self.m,
-                "Q": self.Q, "kernel": self.kernel, "device_bytes": self.device_bytes, "abar_z": self.abar_z}
+                "Q": self.Q, "kernel": self.kernel, "device_bytes": self.device_bytes, "abar_z": self.abar_z,
+                "halo_bytes": self.halo_bytes, "halo_rows": list(self.halo_rows), "row0": self.row0}
 
 
 _lib = None
@@ -91,7 +93,16 @@ SIGNATURES = [
     ("lbmh_omega", ctypes.c_int, [_H, _DP, ctypes.c_int]),
     ("lbmh_get_info", ctypes.c_int, [_H, ctypes.POINTER(Info)]),
     ("lbmh_destroy", ctypes.c_int, [_H]),
-    ("lbmh_step_static", ctypes.c_int, [ctypes.POINTER(_Problem), _DP, _DP, ctypes.POINTER(ctypes.c_double)]),
+    ("lbmh_step_static", ctypes.c_int, [ctypes.POINTER(_Problem), _DP, _DP, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_uint32)]),
+    ("lbmh_create_slab", ctypes.c_int, [ctypes.POINTER(_Problem), ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    ("lbmh_state_speed_bound", ctypes.c_int, [_H, _DP, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    ("lbmh_set_state_bound", ctypes.c_int, [_H, _DP, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    ("lbmh_get_speed_bound", ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double)]),
+    ("lbmh_set_speed_bound", ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double)]),
+    ("lbmh_halo_get", ctypes.c_int, [_H, ctypes.c_int, _DP, ctypes.c_int]),
+    ("lbmh_halo_set", ctypes.c_int, [_H, ctypes.c_int, _DP, ctypes.c_int]),
     ("lbmh_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
                                          ctypes.POINTER(ctypes.c_void_p)]),
     ("lbmh_batch_footprint", ctypes.c_int64, [ctypes.POINTER(_Problem)]),
@@ -282,6 +293,88 @@ class Solver:
         self.close()
 
 
+def _raw_ptr(a):
+    """(pointer, on_device) of a contiguous numpy array or torch tensor of any dtype."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise TypeError("host arrays must be C-contiguous")
+        return a.ctypes.data, 0
+    import torch
+    if isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise TypeError("tensors must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _vec(values, n=3):
+    v = (ctypes.c_double * n)()
+    for i, x in enumerate(list(values)[:n]):
+        v[i] = float(x)
+    return v
+
+
+class Slab(Solver):
+    """Rows [row_begin, row_end) of a 2D lattice decomposed along y (a slab
+    handle of the C ABI): the local lattice holds those rows plus three halo
+    rows on each side that borders another slab.  U and f arrays cover the
+    local lattice, halo rows included."""
+
+    def __init__(self, pb, row_begin, row_end, precision=None, stream=None):
+        lib = load()
+        self.pb_global = pb
+        self.precision = pb.precision if precision is None else precision
+        self._stream = _current_stream() if stream is None else stream
+        self._s = _c_problem(pb, self.precision, KERNEL_FUSED, self._stream)
+        h = ctypes.c_void_p()
+        rc = lib.lbmh_create_slab(ctypes.byref(self._s), int(row_begin), int(row_end), ctypes.byref(h))
+        if rc != OK:
+            raise LbmhError(rc, lib.lbmh_last_error(None).decode())
+        self._h = h
+        self.m = pb.nfields
+        self.Q = 2 * pb.dim + 1
+        inf = Info()
+        self._check(lib.lbmh_get_info(self._h, ctypes.byref(inf)))
+        self.halo = tuple(inf.halo_rows)
+        self.row0 = inf.row0
+        self.halo_bytes = inf.halo_bytes
+        self.rows = (row_begin, row_end)
+        ny_local = row_end - row_begin + self.halo[0] + self.halo[1]
+        self.pb = pb.with_(ny=ny_local, y1=pb.y0 + ny_local * pb.dx)
+
+    def state_speed_bound(self, U):
+        U = np.ascontiguousarray(U, dtype=np.float64).reshape(self.shape_U) if isinstance(U, np.ndarray) else U
+        p, dev = _ptr(U)
+        out = (ctypes.c_double * 3)()
+        self._check(load().lbmh_state_speed_bound(self._h, p, dev, out))
+        return list(out)[: self.pb.dim]
+
+    def set_state_bound(self, U, abar):
+        U = np.ascontiguousarray(U, dtype=np.float64).reshape(self.shape_U) if isinstance(U, np.ndarray) else U
+        p, dev = _ptr(U)
+        self._check(load().lbmh_set_state_bound(self._h, p, dev, _vec(abar)))
+        return self
+
+    def get_speed_bound(self):
+        out = (ctypes.c_double * 3)()
+        self._check(load().lbmh_get_speed_bound(self._h, out))
+        return list(out)[: self.pb.dim]
+
+    def set_speed_bound(self, abar):
+        self._check(load().lbmh_set_speed_bound(self._h, _vec(abar)))
+        return self
+
+    def halo_get(self, side, out):
+        p, dev = _raw_ptr(out)
+        self._check(load().lbmh_halo_get(self._h, int(side), p, dev))
+        return out
+
+    def halo_set(self, side, rows):
+        p, dev = _raw_ptr(rows)
+        self._check(load().lbmh_halo_set(self._h, int(side), p, dev))
+        return self
+
+
 class Batch:
     """Many 2D lattices of one system and precision advanced together (a batch
     of the C ABI).  Lattices are admitted into a fixed device arena."""
@@ -372,20 +465,50 @@ class Batch:
             pass
 
 
-def step_static(pb, f_in, f_out, stream=None, want_dt=True):
+def _check_static_arrays(pb, f_in, f_out):
+    """The C entry point cannot see array sizes: before any launch, require two
+    contiguous FP64 tensors of exactly the lattice's shape [Q][m][ny][nx] on the
+    current CUDA device, with storage that does not overlap."""
+    import torch
+    shape = (pb.nvel, pb.nfields, pb.ny if pb.dim == 2 else 1, pb.nx)
+    for name, a in (("f_in", f_in), ("f_out", f_out)):
+        if not isinstance(a, torch.Tensor):
+            raise TypeError(f"step_static: {name} must be a torch tensor")
+        if tuple(a.shape) != shape and not (pb.dim == 1 and tuple(a.shape) == shape[:2] + shape[3:]):
+            raise TypeError(f"step_static: {name} has shape {tuple(a.shape)}, the lattice needs {shape}")
+    for name, a in (("f_in", f_in), ("f_out", f_out)):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError(f"step_static: {name} must be contiguous float64")
+        if not a.is_cuda:
+            raise TypeError(f"step_static: {name} must be a CUDA tensor")
+        if a.device.index != torch.cuda.current_device():
+            raise TypeError(f"step_static: {name} is on {a.device}, the current device is "
+                            f"cuda:{torch.cuda.current_device()}")
+    nbytes = f_in.numel() * 8
+    a0, b0 = f_in.data_ptr(), f_out.data_ptr()
+    if a0 < b0 + nbytes and b0 < a0 + nbytes:
+        raise TypeError("step_static: f_in and f_out overlap")
+
+
+def step_static(pb, f_in, f_out, stream=None, want_dt=True, want_status=False):
     """One FP64 step f_in -> f_out on device tensors [Q][m][ny][nx] through the
     allocation-free entry point (scratch in the library's static device
-    array).  Returns dt when want_dt (which synchronises the stream)."""
+    array).  Returns dt when want_dt, (dt, status bits) when want_status too
+    (either synchronises the stream)."""
+    if pb.dim not in (1, 2):
+        raise TypeError("step_static serves 1D and 2D lattices")
+    _check_static_arrays(pb, f_in, f_out)
     lib = load()
     s = _c_problem(pb, FP64, KERNEL_UNFUSED, _current_stream() if stream is None else stream)
-    pi, di = _ptr(f_in)
-    po, do = _ptr(f_out)
-    if not (di and do):
-        raise TypeError("step_static takes device tensors")
     dt = ctypes.c_double(0.0)
-    rc = lib.lbmh_step_static(ctypes.byref(s), pi, po, ctypes.byref(dt) if want_dt else None)
+    st = ctypes.c_uint32(0)
+    rc = lib.lbmh_step_static(ctypes.byref(s), f_in.data_ptr(), f_out.data_ptr(),
+                              ctypes.byref(dt) if (want_dt or want_status) else None,
+                              ctypes.byref(st) if want_status else None)
     if rc != OK:
         raise LbmhError(rc, lib.lbmh_last_error(None).decode())
+    if want_status:
+        return dt.value, st.value
     return dt.value if want_dt else None
 
 

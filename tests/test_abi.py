@@ -113,3 +113,20 @@ def test_null_arguments(lib):
     assert lib.lbmh_step(None, 1) == lbmh.ERR_INVALID_ARG
     assert lib.lbmh_destroy(None) == lbmh.OK
     assert lib.lbmh_version().decode().startswith("lbmh")
+
+
+@pytest.mark.parametrize("shape", [(5, 4, 29, 66), (5, 4, 29 * 67), (3, 4, 29, 67)])
+def test_step_static_rejects_wrong_shapes_before_any_launch(shape):
+    """The C entry point cannot see array sizes, so the binding refuses arrays
+    that are not exactly [Q][m][ny][nx] of the problem before it reaches the
+    library (here on the CPU, where no launch could happen at all)."""
+    import torch
+    pb = W.Problem(system=W.EULER, dim=2, nx=67, ny=29, y1=29 / 67)
+    good = torch.zeros((5, 4, 29, 67), dtype=torch.float64)
+    bad = torch.zeros(shape, dtype=torch.float64)
+    with pytest.raises(TypeError, match="shape"):
+        lbmh.step_static(pb, bad, good)
+    with pytest.raises(TypeError, match="shape"):
+        lbmh.step_static(pb, good, bad)
+    with pytest.raises(TypeError, match="CUDA"):  # right shape, but host memory
+        lbmh.step_static(pb, good, good.clone())
