@@ -3,6 +3,8 @@ clock record of the timed region (a throttled run must be recognisable), the
 recorded DRAM traffic (valid only for the kernel sources, lattice, size and
 precision it was captured on) and the roofline denominator."""
 import json
+
+import numpy as np
 import os
 import shutil
 import sys
@@ -85,3 +87,38 @@ def test_measured_peak_or_fallback(fake_root):
     with open(os.path.join(fake_root, "MEASURED_PEAKS.json"), "w") as fh:
         json.dump({"hbm_gbs": 6484.6}, fh)
     assert bench.measured_peaks() == (6484.6, "measured")
+
+
+def test_contract_norm_weighs_momentum_as_a_vector():
+    """The accuracy contract's norm: scalar fields by sum|e|/sum|ref|, the
+    momentum by sum ||e_m|| / sum ||m|| per node, so a near-zero component is
+    measured against the whole momentum."""
+    from paper_2609_18177_b300 import accuracy as A
+    ref = np.zeros((3, 2, 2))
+    ref[0] = 1.0                       # h
+    ref[1] = [[3.0, 3.0], [3.0, 3.0]]  # hu
+    ref[2] = [[4.0, 0.0], [0.0, 0.0]]  # hv: non-zero at one node only
+    got = ref.copy()
+    got[0, 0, 0] += 0.04
+    got[2, 1, 1] += 1e-3              # 2.5e-4 of sum|hv| alone; 1e-3 / 14 of the momentum
+    e = A.contract_l1(got, ref, A.SWE, 2)
+    assert e["h"] == pytest.approx(0.04 / 4.0)
+    # ||m|| per node: 5, 3, 3, 3 -> 14; the error vector (0, 1e-3) at one node
+    assert e["momentum"] == pytest.approx(1e-3 / 14.0)
+    assert e["max"] == pytest.approx(0.01)
+    # Euler 2D: rho, momentum, E; reactive adds rho*Y
+    assert [k for k, _ in A.quantities(A.EULER, 2)] == ["rho", "momentum", "E"]
+    assert [k for k, _ in A.quantities(A.REACTIVE, 2)] == ["rho", "momentum", "E", "rhoY"]
+    assert A.quantities(A.EULER, 1)[1] == ("momentum", [1])
+
+
+def test_contract_norm_torch_matches_numpy():
+    import torch
+    from paper_2609_18177_b300 import accuracy as A
+    rng = np.random.default_rng(3)
+    ref = rng.uniform(0.5, 2.0, (4, 9, 7))
+    got = ref * (1 + 1e-3 * rng.standard_normal(ref.shape))
+    a = A.contract_l1(got, ref, A.EULER, 2)
+    b = A.contract_l1_torch(torch.from_numpy(got), torch.from_numpy(ref), A.EULER, 2)
+    for k in a:
+        assert b[k] == pytest.approx(a[k], rel=1e-12)

@@ -146,10 +146,13 @@ def fv_flux(pb, U):
     rho = U[0]
     vel = [U[1 + j] / rho for j in range(d)]
     E = U[d + 1]
-    p = (pb.gamma - 1) * (E - 0.5 * rho * sum(v * v for v in vel))
+    chem = pb.q * U[d + 2] if pb.system == W.REACTIVE else 0.0  # heat of the unburnt gas
+    p = (pb.gamma - 1) * (E - 0.5 * rho * sum(v * v for v in vel) - chem)
     for j in range(d):
         F = [rho * vel[j]] + [U[1 + i] * vel[j] + (p if i == j else 0.0) for i in range(d)]
         F.append(vel[j] * (E + p))
+        if pb.system == W.REACTIVE:
+            F.append(U[d + 2] * vel[j])
         out.append(np.stack(F))
     return out
 
@@ -163,7 +166,8 @@ def fv_speed(pb, U):
         return [float(np.max(np.abs(U[1 + j] / U[0]) + c)) for j in range(d)]
     rho = U[0]
     vel = [U[1 + j] / rho for j in range(d)]
-    p = (pb.gamma - 1) * (U[d + 1] - 0.5 * rho * sum(v * v for v in vel))
+    chem = pb.q * U[d + 2] if pb.system == W.REACTIVE else 0.0
+    p = (pb.gamma - 1) * (U[d + 1] - 0.5 * rho * sum(v * v for v in vel) - chem)
     c = np.sqrt(pb.gamma * p / rho)
     return [float(np.max(np.abs(vel[j]) + c)) for j in range(d)]
 
@@ -214,6 +218,98 @@ def test_omega_one_is_global_lax_friedrichs(name, make):
         r.step(1)
         U = lf_step(pb, U)
         assert np.allclose(r.moments(), U, rtol=1e-12, atol=1e-12 * np.abs(U).max())
+
+
+# ---------------------------------------------------------------------------
+# inflow sides (Example 5.13) and the sponge, pinned without the push-form
+# stepper: omega = 1 with an inflow side is the global Lax-Friedrichs scheme
+# whose ghost node holds the inflow state (its flux enters the face between
+# the ghost and the first node with the step's alpha), and a uniform inflow
+# state is a steady solution
+# ---------------------------------------------------------------------------
+
+def shift_inflow(pb, A, j, s, ghost):
+    """A at index i + s along axis j; an index beyond an INFLOW side reads
+    `ghost` (one node's values, broadcast), others per the side's BC."""
+    axis = A.ndim - 1 - j
+    n = A.shape[axis]
+    lo, hi = (pb.bc[0], pb.bc[1]) if j == 0 else (pb.bc[2], pb.bc[3])
+    idx = np.arange(n) + s
+    out = np.take(A, np.clip(idx, 0, n - 1) if lo != W.PERIODIC else idx % n, axis=axis)
+    shape = [1] * A.ndim
+    shape[0] = A.shape[0]
+    g = np.asarray(ghost, dtype=np.float64).reshape(shape)
+    for side, bad in ((lo, idx < 0), (hi, idx >= n)):
+        if side == W.INFLOW and bad.any():
+            sel = [slice(None)] * A.ndim
+            sel[axis] = np.nonzero(bad)[0]
+            out[tuple(sel)] = np.broadcast_to(g, out[tuple(sel)].shape)
+    return out
+
+
+def lf_step_inflow(pb, U):
+    speeds = fv_speed(pb, U)
+    dt = pb.cfl * pb.dx / sum(speeds)
+    alpha = [s + pb.eps for s in speeds]
+    m = U.shape[0]
+    u_in = np.array(pb.u_in[:m])
+    F = fv_flux(pb, U)
+    Fin = [f.reshape(m) for f in fv_flux(pb, u_in.reshape((m,) + (1,) * (U.ndim - 1)))]
+    Un = U.copy()
+    for j in range(pb.dim):
+        Up, Um = shift_inflow(pb, U, j, +1, u_in), shift_inflow(pb, U, j, -1, u_in)
+        Fp, Fm = shift_inflow(pb, F[j], j, +1, Fin[j]), shift_inflow(pb, F[j], j, -1, Fin[j])
+        Un = Un - dt / (2 * pb.dx) * (Fp - Fm) + alpha[j] * dt / (2 * pb.dx) * (Up - 2 * U + Um)
+    return Un
+
+
+INFLOW_CASES = [
+    ("euler1d_inflow_hi", W.Problem(system=W.EULER, dim=1, nx=48, bc=(W.OUTFLOW, W.INFLOW, 0, 0),
+                                    u_in=(1.3, -0.9, 4.0))),
+    ("euler1d_inflow_lo_sponge", W.Problem(system=W.EULER, dim=1, nx=40, bc=(W.INFLOW, W.OUTFLOW, 0, 0),
+                                           u_in=(0.8, 0.6, 2.5), sponge_width=0.3)),
+    ("swe2d_inflow_lo", W.Problem(system=W.SWE, dim=2, nx=16, ny=12, y1=0.75,
+                                  bc=(W.INFLOW, W.OUTFLOW, W.OUTFLOW, W.OUTFLOW), u_in=(1.4, 0.7, -0.2))),
+    ("reactive2d_inflow_hi_sponge", W.Problem(system=W.REACTIVE, dim=2, nx=14, ny=10, y1=10 / 14, gamma=1.2,
+                                              q=2.0, K=5.0, Ti=3.0, bc=(W.OUTFLOW, W.INFLOW, W.PERIODIC, W.PERIODIC),
+                                              u_in=(1.0, -1.2, 0.1, 6.0, 1.0), sponge_width=0.2)),
+]
+
+
+@pytest.mark.parametrize("name,pb", INFLOW_CASES, ids=[c[0] for c in INFLOW_CASES])
+def test_omega_one_with_inflow_sides_is_lax_friedrichs_with_the_inflow_ghost(name, pb):
+    """omega = 1 (fixed; with a sponge, omega' = 1 + (1 - 1)(1 - sigma) = 1 too):
+    the step is the global Lax-Friedrichs update whose neighbour beyond an
+    inflow side is u_in.  A wrong alpha or lambda in the ghost's f^eq(u_in), or
+    a ghost state other than u_in, changes the face flux and fails this."""
+    if pb.system == W.REACTIVE:
+        pb = pb.with_(K=0.0)  # no source: the identity is the homogeneous LF scheme
+    U0 = W.random_state(pb, seed=8)
+    pb = pb.with_(omega_mode=1, omega_fixed=1.0, cfl=0.8)
+    r = oracle.Run(pb, U0)
+    U = U0.reshape((pb.nfields,) + pb.shape()).copy()
+    for _ in range(5):
+        r.step(1)
+        U = lf_step_inflow(pb, U)
+        assert np.allclose(r.moments(), U, rtol=1e-12, atol=1e-12 * np.abs(U).max())
+
+
+@pytest.mark.parametrize("name,pb", INFLOW_CASES, ids=[c[0] for c in INFLOW_CASES])
+def test_uniform_inflow_state_is_steady(name, pb):
+    """A lattice filled with the inflow state keeps that state with its inflow
+    sides (and a sponge): f = f^eq everywhere, the ghosts hold f^eq(u_in) with
+    the same alpha and lambda, streaming moves equal values.  Only rounding
+    (sum_k f^eq_k(U) is U up to an ulp) moves it, and it does not grow.
+    Without a source only (the Arrhenius source would burn the gas)."""
+    pb = pb.with_(K=0.0)
+    m = pb.nfields
+    U0 = np.broadcast_to(np.array(pb.u_in[:m]).reshape((m,) + (1,) * len(pb.shape())),
+                         (m,) + pb.shape()).copy()
+    r = oracle.Run(pb, U0)
+    for _ in range(4):
+        r.step(10)
+        U = r.moments()
+        assert np.all(np.abs(U - U0) <= 4e-15 * np.abs(U0).max()), np.abs(U - U0).max()
 
 
 # ---------------------------------------------------------------------------
