@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--kernel", default="auto", choices=["auto", "fused", "unfused"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the FP64 run that measures the FP32 result's error (outside the timed region)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-n", type=int, default=384)
     ap.add_argument("--workload", default="riemann2d",
@@ -54,7 +56,7 @@ def parse():
                     help="lines1d: run one case only, NAME:N:DTYPE (e.g. sod:262144:f32)")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--sample", type=int, default=16)
-    ap.add_argument("--requests", type=int, default=60)
+    ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--autotune", action="store_true",
                     help="served: let each system's batch time its kernel variants once it holds two lattices")
@@ -180,11 +182,9 @@ def workload(n, seed, precision, lattice="riemann2d"):
     return pb, U0
 
 
-def cpu_baseline(args, seconds):
-    """The FP64 oracle as it stands, on a bounded sample of the same workload."""
+def _time_oracle(pb, U0, seconds, min_steps=3):
+    """Node updates per second of the oracle stepping (pb, U0) for ~seconds."""
     import oracle
-    n = args.ref_n
-    pb, U0 = workload(n, args.seed, "fp64", args.lattice)
     r = oracle.Run(pb, U0)
     r.step(1)
     steps = 0
@@ -193,20 +193,58 @@ def cpu_baseline(args, seconds):
         r.step(1)
         steps += 1
         el = time.perf_counter() - t0
-        if el >= seconds and steps >= 3:
+        if el >= seconds and steps >= min_steps:
             break
-    mlups = pb.nodes * steps / el / 1e6
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return pb.nodes * steps / el / 1e6, steps, el
+
+
+def _native_oracle():
+    """The oracle tuned for this host's CPU (-march=native, built here)."""
+    import oracle
+    if oracle._lib is None:
+        oracle.use_native_build()
+    return oracle
+
+
+def cpu_baseline(args, seconds):
+    """The FP64 oracle as it stands, on a bounded sample of the same workload:
+    on all host cores (OpenMP over rows) and on one core."""
+    oracle = _native_oracle()
+    n = args.ref_n
+    pb, U0 = workload(n, args.seed, "fp64", args.lattice)
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    mlups, steps, el = _time_oracle(pb, U0, seconds)
+    oracle.set_threads(1)
+    n1 = max(64, n // 2)
+    pb1, U1 = workload(n1, args.seed, "fp64", args.lattice)
+    mlups1, steps1, el1 = _time_oracle(pb1, U1, seconds / 3)
+    oracle.set_threads(cores)
     return {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n}x{n} grid of the same workload ({args.lattice}), FP64, {steps} steps "
-                      f"({el:.1f} s), OpenMP over rows"}
+                      f"({el:.1f} s), OpenMP over rows on {cores} threads; oracle built -O3 -march=native "
+                      "-ffp-contract=off on this host",
+            "single_thread": {"value": mlups1, "unit": UNIT, "cores": 1,
+                              "sample": f"{n1}x{n1} grid, {steps1} steps ({el1:.1f} s)"},
+            "cpu": _cpu_model()}
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    import oracle
+    oracle = _native_oracle()
+    oracle.set_threads(os.cpu_count() or 1)
     n = args.ref_n
     pb, U0 = workload(n, args.seed, "fp64", args.lattice)
     r = oracle.Run(pb, U0)
@@ -215,7 +253,7 @@ def run_reference(args):
     r.step(args.steps)
     el = time.perf_counter() - t0
     value = pb.nodes * args.steps / el / 1e6
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.set_threads(0)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
@@ -229,6 +267,29 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def headline_accuracy(solver, pb, U0_dev, steps, kernel):
+    """Error of the FP32 lattice after `steps` steps from U0 (the timed step
+    count, at most 200) against the FP64 fused path over the same steps, in the
+    contract norm (paper_2609_18177_b300.accuracy).  Outside the timed region."""
+    import torch
+    from paper_2609_18177_b300 import accuracy as A
+    from paper_2609_18177_b300 import lbmh
+    u32 = torch.empty((pb.nfields,) + pb.shape(), dtype=torch.float64, device=U0_dev.device)
+    solver.set_state(U0_dev).step(steps)
+    solver.moments(out=u32, check=False)
+    t32 = solver.info()["t"]
+    with lbmh.Solver(pb.with_(precision=0), precision=lbmh.FP64, kernel=kernel) as s64:
+        s64.set_state(U0_dev).step(steps)
+        u64 = torch.empty_like(u32)
+        s64.moments(out=u64, check=False)
+        t64 = s64.info()["t"]
+    err = A.contract_l1_torch(u32, u64, pb.system, pb.dim)
+    del u32, u64
+    return {"norm": "relative L1 per quantity, momentum as a vector per node", "steps": steps,
+            "t_fp32": t32, "t_fp64": t64, "errors": err, "tolerance": A.TOL_SHOCK,
+            "meets_tolerance": err["max"] <= A.TOL_SHOCK, "reference": "FP64 fused GPU path (oracle parity 1e-12)"}
 
 
 def rel_l1_fields(a, b):
@@ -315,17 +376,19 @@ def run_batched(args):
     info = b.info()
     b.close()
     # plain per-grid FP64 GPU path on a seeded sample, and FP32 accuracy against it
+    from paper_2609_18177_b300 import accuracy as A
     pick = rng.choice(len(cases), size=min(args.sample, len(cases)), replace=False)
-    t64, errs, floor = 0.0, [], []
+    t64, ns64, errs, floor = 0.0, 0, [], []
     for i in pick:
         pb, U0 = cases[i]
-        U64, el, _n = fp64_per_grid(pb, U0, T=T)
+        U64, el, n64 = fp64_per_grid(pb, U0, T=T)
         t64 += el
-        errs.append(rel_l1_fields(results[slots[i]], U64))
+        ns64 += pb.nodes * n64
+        errs.append(A.contract_l1(results[slots[i]], U64, pb.system, pb.dim))
         # conditioning floor: the FP64 solve from an FP32-sized input perturbation
         U64r, _el, _n = fp64_per_grid(pb, perturbed_input(U0), T=T)
-        floor.append(rel_l1_fields(U64r, U64))
-    # the FP64 GPU path against the CPU oracle on the smallest sampled lattice
+        floor.append(A.contract_l1(U64r, U64, pb.system, pb.dim))
+    # the FP64 GPU path and the FP32 batch against the CPU oracle on the smallest sampled lattice
     small = min(pick, key=lambda i: sizes[i])
     pb, U0 = cases[small]
     r = oracle.Run(pb, U0).step(20)
@@ -335,7 +398,10 @@ def run_batched(args):
         r.step(1)
     U64, _el, n64 = fp64_per_grid(pb, U0, T=T)
     solves = len(cases) / wall
-    fp64_solves = len(pick) / t64
+    # the per-grid FP64 path would need (node updates of all lattices) / (its measured rate)
+    fp64_rate = ns64 / t64
+    fp64_solves = len(cases) / (node_steps / fp64_rate)
+    names = [k for k, _ in A.quantities(W.SWE, 2)]
     return {
         "metric": METRIC, "workload": "batched", "value": solves, "unit": "solves/s",
         "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
@@ -346,27 +412,66 @@ def run_batched(args):
         "mlups_stepping": node_steps / (device_ms / 1e3) / 1e6,
         "hbm_gbs_stepping": node_steps * 2 * 15 * 4 / (device_ms / 1e3) / 1e9,
         "batch_variant": info["variant"], "grid": info["grid"],
-        "fp64_per_grid_solves_per_s": fp64_solves, "fp64_sample": len(pick),
+        "fp64_per_grid_solves_per_s": fp64_solves, "fp64_per_grid_mlups": fp64_rate / 1e6,
+        "fp64_sample": len(pick),
+        "fp64_note": "one fused FP64 handle per lattice, run back to back; rate measured on the sample, "
+                     "solves/s = lattices / (node updates of all lattices / rate)",
         "speedup_vs_fp64_per_grid": solves / fp64_solves,
-        "l1_err_vs_fp64": {"fields": "h, hu, hv", "max": float(np.max(errs)),
-                           "median": float(np.median(np.max(errs, axis=1))),
-                           "per_field_max": [float(v) for v in np.max(errs, axis=0)],
-                           "per_field_median": [float(v) for v in np.median(errs, axis=0)],
-                           "floor_fp64_input_perturbed_2^-24_per_field_max":
-                               [float(v) for v in np.max(floor, axis=0)],
-                           "floor_per_field_median": [float(v) for v in np.median(floor, axis=0)],
-                           "tolerance": 1e-3},
-        "fp64_gpu_vs_oracle": {"n": sizes[small], "rel_max_per_field_after_20_steps": oracle_20,
-                               "steps_to_T": n64, "rel_l1_per_field_at_T": rel_l1_fields(U64, r.moments()),
-                               "oracle_steps": r.nsteps},
+        "l1_err_vs_fp64": {"norm": "relative L1 per quantity, momentum as a vector per node",
+                           "quantities": names,
+                           "max": float(max(e["max"] for e in errs)),
+                           "per_quantity_max": {k: float(max(e[k] for e in errs)) for k in names},
+                           "per_quantity_median": {k: float(np.median([e[k] for e in errs])) for k in names},
+                           "floor_fp64_input_perturbed_2^-24_max": {k: float(max(e[k] for e in floor))
+                                                                    for k in names},
+                           "tolerance": A.TOL_SHOCK,
+                           "meets_tolerance": bool(max(e["max"] for e in errs) <= A.TOL_SHOCK)},
+        "vs_oracle_smallest": {"n": sizes[small],
+                               "fp64_gpu_rel_max_per_field_after_20_steps": oracle_20,
+                               "fp64_gpu_at_T": A.contract_l1(U64, r.moments(), pb.system, pb.dim),
+                               "fp32_batch_at_T": A.contract_l1(results[slots[small]], r.moments(), pb.system,
+                                                                pb.dim),
+                               "steps_to_T": n64, "oracle_steps": r.nsteps},
     }
+
+
+def served_sample(trace, seed=0):
+    """Requests whose results are checked against FP64: per system the two
+    smallest (node updates) and one drawn from the seed among those the FP64
+    path finishes in seconds (the FP64 reactive step runs on the FP64 pipe)."""
+    rng = np.random.default_rng(seed)
+    budget = {"euler": 3e9, "swe": 3e9, "reactive": 3e8}
+    pick = []
+    for kind in ("euler", "swe", "reactive"):
+        reqs = sorted((r for r in trace if r.kind == kind), key=lambda r: r.n * r.n * r.steps)
+        pick += reqs[:2]
+        rest = [r for r in reqs[2:] if r.n * r.n * r.steps <= budget[kind]]
+        if rest:
+            pick.append(rest[int(rng.integers(len(rest)))])
+    return pick
+
+
+def fp64_rate(kind, n, steps=40):
+    """Node updates per second of the plain per-grid FP64 path (one fused FP64
+    handle) on a lattice of the given kind and size."""
+    import torch
+    from paper_2609_18177_b300 import lbmh
+    from paper_2609_18177_b300 import serve as S
+    pb, U0 = S.make_problem(S.Request(0, kind, n, steps, 1, 0.0))
+    with lbmh.Solver(pb.with_(precision=0), precision=lbmh.FP64, kernel=lbmh.KERNEL_FUSED) as s:
+        s.set_state(U0).step(3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(steps)
+        torch.cuda.synchronize()
+        return pb.nodes * steps / (time.perf_counter() - t0)
 
 
 def run_served(args):
     """Poisson arrivals of mixed solves (2D Euler Riemann, shallow-water dam
     break, reactive Euler circle), n ~ U{128..2048}, 200..5000 steps."""
-    import torch
-    from paper_2609_18177_b300 import lbmh
+    import oracle
+    from paper_2609_18177_b300 import accuracy as A
     from paper_2609_18177_b300 import serve as S
     out = {}
     plan = [("offered", args.rate, args.requests)]
@@ -374,27 +479,59 @@ def run_served(args):
              (float(v) for v in args.sweep_rates.split(",") if v.strip())]
     for idx, (label, rate, nreq) in enumerate(plan):
         trace = S.poisson_trace(nreq, rate, seed=args.seed + idx)
-        inputs = {r.rid: S.make_problem(r) for r in trace}
-        srv = S.Server(capacity_bytes=24 << 30, max_instances=256, chunk=32, keep_results=(label == "offered"),
-                       autotune=args.autotune)
-        results, stats = srv.run(trace, inputs=inputs)
+        sample = served_sample(trace, seed=args.seed) if label == "offered" else []
+        srv = S.Server(capacity_bytes=24 << 30, max_instances=256, chunk=32,
+                       keep_results={r.rid for r in sample}, autotune=args.autotune)
+        feed = S.InputPrefetcher(trace)  # the clients' inputs, built on host threads as they arrive
+        results, stats = srv.run(trace, inputs=feed)
+        feed.close()
         srv.close()
         stats["rate_req_per_s"] = rate
+        print(f"served {label}: {json.dumps(stats)}", file=sys.stderr, flush=True)
         if label == "offered":
-            # accuracy of the served FP32 results against the FP64 per-grid path
             by = {r.rid: r for r in results}
-            smallest = sorted(trace, key=lambda r: r.n * r.n * r.steps)[:4]
             errs = []
-            for req in smallest:
-                pb, U0 = inputs[req.rid]
+            smallest = {}
+            for req in sample:
+                smallest.setdefault(req.kind, []).append(req)
+            for req in sample:
+                pb, U0 = S.make_problem(req)
                 U64, _el, _n = fp64_per_grid(pb, U0, steps=req.steps)
-                U64r, _el, _n = fp64_per_grid(pb, perturbed_input(U0), steps=req.steps)
-                errs.append({"kind": req.kind, "n": req.n, "steps": req.steps,
-                             "rel_l1_per_field": rel_l1_fields(by[req.rid].U, U64),
-                             "floor_fp64_input_perturbed_2^-24": rel_l1_fields(U64r, U64)})
-            stats["l1_err_vs_fp64"] = errs
+                e = {"kind": req.kind, "n": req.n, "steps": req.steps,
+                     "l1_vs_fp64": A.contract_l1(by[req.rid].U, U64, pb.system, pb.dim)}
+                if req in smallest[req.kind][:2]:  # the scheme's own spread, on the two smallest per system
+                    U64r, _el, _n = fp64_per_grid(pb, perturbed_input(U0), steps=req.steps)
+                    e["floor_fp64_input_perturbed_2^-24"] = A.contract_l1(U64r, U64, pb.system, pb.dim)
+                errs.append(e)
+                print(f"served accuracy: {json.dumps(e)}", file=sys.stderr, flush=True)
+            # the smallest request of each system also against the CPU oracle
+            for kind, reqs in smallest.items():
+                req = reqs[0]
+                pb, U0 = S.make_problem(req)
+                U_or = oracle.Run(pb, U0).step(req.steps).moments()
+                for e in errs:
+                    if (e["kind"], e["n"], e["steps"]) == (req.kind, req.n, req.steps):
+                        e["l1_vs_oracle"] = A.contract_l1(by[req.rid].U, U_or, pb.system, pb.dim)
+            stats["l1_err_vs_fp64"] = {
+                "norm": "relative L1 per quantity, momentum as a vector per node",
+                "max": float(max(e["l1_vs_fp64"]["max"] for e in errs)),
+                "tolerance": A.TOL_SHOCK,
+                "meets_tolerance": bool(max(e["l1_vs_fp64"]["max"] for e in errs) <= A.TOL_SHOCK),
+                "requests": errs}
+            # the plain per-grid FP64 path serving the same trace back to back:
+            # its rate per system on a lattice of the trace's mean size
+            rate64 = {}
+            for kind in ("euler", "swe", "reactive"):
+                ns = [r.n for r in trace if r.kind == kind]
+                if ns:
+                    rate64[kind] = fp64_rate(kind, int(round(np.mean(ns))))
+            t64 = sum(r.n * r.n * r.steps / rate64[r.kind] for r in trace)
+            stats["fp64_per_grid_solves_per_s"] = len(trace) / t64
+            stats["fp64_per_grid_mlups"] = {k: v / 1e6 for k, v in rate64.items()}
+            stats["fp64_note"] = ("one fused FP64 handle per request, run back to back with no arrival gaps; "
+                                  "rate per system measured over 40 steps on a lattice of the trace's mean size; "
+                                  "time = sum of node updates / rate")
         out[label] = stats
-        del inputs
     off = out["offered"]
     return {
         "metric": METRIC, "workload": "served", "value": off["solves_per_s"], "unit": "solves/s",
@@ -404,6 +541,9 @@ def run_served(args):
                                "(one batch per system, admission by arena footprint)",
                    "requests": args.requests, "rate": args.rate},
         "p50_latency_s": off["p50_latency_s"], "p99_latency_s": off["p99_latency_s"],
+        "fp64_per_grid_solves_per_s": off["fp64_per_grid_solves_per_s"],
+        "speedup_vs_fp64_per_grid": off["solves_per_s"] / off["fp64_per_grid_solves_per_s"],
+        "l1_err_vs_fp64": {k: off["l1_err_vs_fp64"][k] for k in ("norm", "max", "tolerance", "meets_tolerance")},
         "offered": off, "load_sweep": [v for k, v in out.items() if k != "offered"],
     }
 
@@ -593,6 +733,10 @@ def main():
                "note": "per solve: set_state from pinned host U0, K steps, moments to pinned host; "
                        "bytes are per step averaged over the K steps of one solve"}
 
+    accuracy = None
+    if rank == 0 and prec == lbmh.FP32 and not args.no_accuracy:
+        accuracy = headline_accuracy(solver, pb, U0_dev, min(args.steps, 200), kernel)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, args.cpu_seconds)
@@ -616,6 +760,7 @@ def main():
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "l1_err_vs_fp64": accuracy,
             "status": info["status"],
             "sim_time": info["t"],
         }

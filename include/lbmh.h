@@ -52,6 +52,7 @@ extern "C" {
 #define LBMH_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up */
 #define LBMH_ERR_CUDA (-5)         /* a CUDA runtime call failed */
 #define LBMH_ERR_UNSUPPORTED (-6)  /* valid request this build does not provide */
+#define LBMH_ERR_BOUNDS (-7)       /* bounds-checked build only: an index left its array (it was clamped) */
 
 /* Physical systems, Section 5: scalar advection u_t + a.grad u = 0; Euler
  * (gamma-law gas); shallow water (g) with optional Gaussian bed-slope source;
@@ -137,8 +138,10 @@ typedef struct lbmh_info {
   double last_dt, last_lambda; /* of the last executed step */
   double sum_U[8];     /* FP64 sum over nodes of U after the last executed step */
   uint32_t status;     /* bit 0: non-physical state (NaN/inf, rho<=0, p<=0); bit 1: reaction
-                          root not converged; bit 3: negative depth h < -1e-12 (reported
-                          only: the scheme is not positivity preserving at wet-dry fronts) */
+                          root not converged; bit 2: a bounded device wait gave up; bit 3:
+                          negative depth h < -1e-12 (reported only: the scheme is not
+                          positivity preserving at wet-dry fronts); bit 4: an index left its
+                          array (bounds-checked build only) */
   int m, Q;            /* fields and velocities */
   int kernel;          /* implementation in use: LBMH_KERNEL_FUSED or _UNFUSED */
   int64_t device_bytes; /* device memory owned by the handle */
@@ -253,7 +256,9 @@ LBMH_API int lbmh_halo_set(lbmh_handle *h, int side, const void *rows, int on_de
 /* ------------------------------------------------------------------------
  * Batches: many 2D lattices of one system and precision, of uneven sizes,
  * advanced together by one persistent kernel launch per step (replayed from
- * a captured CUDA graph three steps at a time).  Each lattice keeps its own
+ * a captured CUDA graph three steps at a time); the resident CTAs take
+ * segments of rows from a shared counter, so lattices that finish early free
+ * their share of the GPU at once.  Each lattice keeps its own
  * time step (Eq. 2.21 from its own speed bound), time and step count, and
  * stops by itself at its step target or end time.  Lattices live in a device
  * arena of fixed capacity allocated at creation; lbmh_batch_add admits a
@@ -284,8 +289,8 @@ LBMH_API int lbmh_batch_remove(lbmh_batch *b, int slot);
 /* Enqueue n batched steps (lattices that reached their target are skipped). */
 LBMH_API int lbmh_batch_step(lbmh_batch *b, int64_t n);
 
-/* Time each kernel variant (ring depth 1 or 2 rows ahead; segments of one
- * chunk or half a chunk) on the live batch for steps_per_candidate steps and
+/* Time each kernel variant (ring depth 1 or 2 rows ahead; segments of 64,
+ * 128, 256 or 512 rows) on the live batch for steps_per_candidate steps and
  * keep the fastest.  Every timed launch is a real step of the batch.
  * *best_ms (may be NULL) receives the chosen variant's time per step. */
 LBMH_API int lbmh_batch_autotune(lbmh_batch *b, int steps_per_candidate, double *best_ms);
@@ -300,7 +305,7 @@ LBMH_API int lbmh_batch_poll(lbmh_batch *b, int *done, double *t, int64_t *steps
 LBMH_API int lbmh_batch_moments(lbmh_batch *b, int slot, double *U_out, int on_device);
 
 /* Arena use, capacity, live lattices, grid size and the chosen variant
- * (10 * rows ahead + segments per chunk). */
+ * (1000 * rows ahead + rows per segment). */
 LBMH_API int lbmh_batch_info(lbmh_batch *b, int64_t *used_bytes, int64_t *capacity_bytes, int *active, int *grid,
                              int *variant);
 

@@ -50,35 +50,54 @@ class _Problem(ctypes.Structure):
 _lib = None
 
 
-def lib():
+def use_native_build():
+    """Load the copy of the oracle tuned for this machine's CPU (-march=native,
+    built here on first use) instead of the portable one: for timing the
+    oracle as a CPU baseline.  Must be called before any other oracle call."""
     global _lib
+    if _lib is not None:
+        raise RuntimeError("the oracle library is already loaded")
+    _load(_build.build(native=True))
+
+
+def set_threads(n):
+    """OpenMP threads of the oracle's loops; returns the number in effect."""
+    return lib().orc_set_threads(int(n))
+
+
+def lib():
     if _lib is None:
-        path = _build.build()
-        L = ctypes.CDLL(path)
-        P = ctypes.POINTER(_Problem)
-        dp = ctypes.POINTER(ctypes.c_double)
-        L.orc_nfields.argtypes = [P]
-        L.orc_flux.argtypes = [P, ctypes.c_int, dp, dp]
-        L.orc_flux.restype = None
-        L.orc_eigvals.argtypes = [P, ctypes.c_int, dp, dp]
-        L.orc_eigvals.restype = None
-        L.orc_max_speed.argtypes = [P, ctypes.c_int, dp]
-        L.orc_max_speed.restype = ctypes.c_double
-        L.orc_right_eigvecs.argtypes = [P, ctypes.c_int, dp, dp]
-        L.orc_right_eigvecs.restype = None
-        L.orc_left_eigvecs.argtypes = [P, ctypes.c_int, dp, dp]
-        L.orc_source.argtypes = [P, dp, ctypes.c_double, ctypes.c_double, dp]
-        L.orc_source.restype = None
-        L.orc_equilibrium.argtypes = [P, dp, dp, ctypes.c_double, dp]
-        L.orc_equilibrium.restype = None
-        L.orc_moments.argtypes = [P, dp, dp]
-        L.orc_alpha_bar_U.argtypes = [P, dp, dp]
-        L.orc_init.argtypes = [P, dp, dp, dp]
-        L.orc_step.argtypes = [P, dp, dp, ctypes.c_double, dp, dp, dp]
-        L.orc_advance.argtypes = [P, dp, dp, ctypes.c_double, ctypes.c_long,
-                                  ctypes.POINTER(ctypes.c_long)]
-        _lib = L
+        _load(_build.build())
     return _lib
+
+
+def _load(path):
+    global _lib
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER(_Problem)
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.orc_nfields.argtypes = [P]
+    L.orc_flux.argtypes = [P, ctypes.c_int, dp, dp]
+    L.orc_flux.restype = None
+    L.orc_eigvals.argtypes = [P, ctypes.c_int, dp, dp]
+    L.orc_eigvals.restype = None
+    L.orc_max_speed.argtypes = [P, ctypes.c_int, dp]
+    L.orc_max_speed.restype = ctypes.c_double
+    L.orc_right_eigvecs.argtypes = [P, ctypes.c_int, dp, dp]
+    L.orc_right_eigvecs.restype = None
+    L.orc_left_eigvecs.argtypes = [P, ctypes.c_int, dp, dp]
+    L.orc_source.argtypes = [P, dp, ctypes.c_double, ctypes.c_double, dp]
+    L.orc_source.restype = None
+    L.orc_equilibrium.argtypes = [P, dp, dp, ctypes.c_double, dp]
+    L.orc_equilibrium.restype = None
+    L.orc_moments.argtypes = [P, dp, dp]
+    L.orc_alpha_bar_U.argtypes = [P, dp, dp]
+    L.orc_init.argtypes = [P, dp, dp, dp]
+    L.orc_step.argtypes = [P, dp, dp, ctypes.c_double, dp, dp, dp]
+    L.orc_advance.argtypes = [P, dp, dp, ctypes.c_double, ctypes.c_long,
+                              ctypes.POINTER(ctypes.c_long)]
+    L.orc_set_threads.argtypes = [ctypes.c_int]
+    _lib = L
 
 
 def _dp(a):

@@ -55,6 +55,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_ADVECTION 0
 #define ORC_EULER 1
@@ -925,4 +928,17 @@ int orc_advance(const orc_problem *p, double *f, double *t, double T, long nstep
     free(g);
     if (nsteps) *nsteps = s;
     return flags;
+}
+
+/* Threads of the OpenMP loops (for timing the oracle on one core or on all of
+ * them); returns the number in effect.  Results do not depend on it: every
+ * loop writes disjoint nodes and the one reduction is a bitwise OR. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

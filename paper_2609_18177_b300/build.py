@@ -14,6 +14,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "_lbmh.so")
+# the same library with every global-memory index of the step kernels guarded
+# (LBMH_CHECK_BOUNDS): an index outside its array sets a status bit and is
+# clamped; for the debug runs of the test suite, not for timing
+LIB_CHECKED = os.path.join(HERE, "_lbmh_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
@@ -34,18 +38,21 @@ def up_to_date(target, inputs):
     return all(os.path.getmtime(p) <= t for p in inputs)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date(LIB, deps()):
-        return LIB
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(lib, deps()):
+        return lib
     cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
            "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr",
-           "-I", os.path.join(ROOT, "include"), "-o", LIB + ".tmp", *sources(), "-lcuda"]
+           "-I", os.path.join(ROOT, "include"), "-o", lib + ".tmp", *sources(), "-lcuda"]
+    if checked:
+        cmd.insert(1, "-DLBMH_CHECK_BOUNDS")
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

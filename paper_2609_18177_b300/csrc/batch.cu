@@ -3,8 +3,10 @@
 //
 // Device side: an instance table (problem constants, TMA descriptors of both
 // distribution buffers, control block) and a work list of strip segments
-// (instance, strip, rows) cut into gridDim equal chunks, so every CTA gets the
-// same number of rows whatever the mix of grid sizes.  Each instance keeps its
+// (instance, strip, band of rows) that the resident CTAs take one at a time
+// from a shared counter, so the load balances whatever the mix of grid sizes,
+// and the segments of lattices that have already finished cost the CTA that
+// takes them only a read of their control block.  Each instance keeps its
 // own time step (Eq. 2.21 from its own speed bound), time and step count in its
 // control block, and stops by itself once it reached its step target or end
 // time.  Host side: admission into a fixed device arena by footprint (first-fit
@@ -46,12 +48,25 @@ struct BatchSeg {
   int inst, strip, yb, ye, owner, pad[3];
 };
 
+// queue[0]: next segment to take; queue[1]: CTAs done; queue[2]: segments in
+// the list (written by the host with the list, so a captured graph stays valid
+// when lattices come and go).  The last CTA to finish resets the two counters
+// for the next launch (every CTA has stopped taking segments by then), so the
+// launches of a captured graph need no host work in between.
+// resident CTAs per SM the register allocation must leave room for: four for
+// the FP32 advection, Euler and shallow-water steps (128 registers, what the
+// step needs without spilling), two for FP32 reactive Euler (its ring and
+// staged row allow two), whatever fits in FP64
+template <int SYS, class R>
+constexpr int batch_min_blocks() { return sizeof(R) == 8 ? 1 : (SYS == SYS_REACT ? 2 : 4); }
+
 template <int SYS, class R, int PREF>
-__global__ void __launch_bounds__(FT) k_batch2d(const BatchInst* insts, const BatchSeg* segs, const int* cta_begin,
-                                                int slot, double* seg_sums) {
+__global__ void __launch_bounds__(FT, batch_min_blocks<SYS, R>()) k_batch2d(const BatchInst* insts, const BatchSeg* segs, int* queue, int slot,
+                                                double* seg_sums) {
   constexpr int M = Fields<SYS, 2>::M;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int s_abort;
+  __shared__ int s_seg;
   // step coefficients of the current segment's lattice: FP64 arithmetic done
   // once by thread 0, not by every thread of every segment
   __shared__ StepCoef s_cf;
@@ -59,8 +74,13 @@ __global__ void __launch_bounds__(FT) k_batch2d(const BatchInst* insts, const Ba
   const int t = threadIdx.x;
   Pipe2D pp;
   pipe2d_init<SYS, R, PREF, 1>(pp, smem_raw, &s_abort);
-  const int sb = cta_begin[blockIdx.x], se = cta_begin[blockIdx.x + 1];
-  for (int i = sb; i < se; i++) {
+  const int nsegs = queue[2];
+  for (;;) {
+    // (every thread read the previous s_seg before the s_cf barrier below)
+    if (t == 0) s_seg = atomicAdd(&queue[0], 1);
+    __syncthreads();
+    const int i = s_seg;
+    if (i >= nsegs) break;
     const BatchSeg sg = segs[i];
     const BatchInst& I = insts[sg.inst];
     const DevParams P = I.P;
@@ -69,14 +89,18 @@ __global__ void __launch_bounds__(FT) k_batch2d(const BatchInst* insts, const Ba
       s_cf = step_coef<2>(P, ctl, slot);
       s_cc = make_coef2d<R>(s_cf, P);
     }
-    __syncthreads();  // (the previous segment's readers passed its side-output barrier)
+    __syncthreads();  // (the previous segment's readers passed the segment barrier above)
     const StepCoef cf = s_cf;
+    if (!cf.active) {  // a finished lattice: only its owner segment moves the control block on
+      if (sg.owner && t == 0) advance_ctl<2>(ctl, slot, cf);
+      continue;
+    }
     R sp0 = R(0), sp1 = R(0);
     Acc<R> acc[M];
 #pragma unroll
     for (int c = 0; c < M; c++) acc[c].init();
     unsigned st = 0u;
-    if (cf.active && !pp.aborted) {
+    if (!pp.aborted) {
       const int par = ctl->parity[slot];
       const CUtensorMap* tml = &I.tml[par];
       const CUtensorMap* tms = &I.tms[par ^ 1];
@@ -87,19 +111,28 @@ __global__ void __launch_bounds__(FT) k_batch2d(const BatchInst* insts, const Ba
       const Phys<R> K = make_phys<R>(P);
       const Coef2D<R> cc = s_cc;
       run_segment2d<SYS, R, PREF, 1>(pp, tml, tms, (R*)I.buf[par ^ 1], P, K, cc, sg.strip, sg.yb, sg.ye, I.nxs, sp0,
-                                     sp1, acc, st);
+                                     sp1, acc, st, &ctl->status);
       if (pp.aborted) st |= ST_TIMEOUT;
+    } else {
+      st |= ST_TIMEOUT;  // an earlier wait of this CTA gave up: this segment's rows were not written
     }
     // this segment's side outputs: speed bound of its instance, FP64 sums
     fused_side_outputs_to<M, R>(sp0, sp1, acc, ctl, (slot + 1) % 3, seg_sums + (long long)i * M, st);
     if (sg.owner && t == 0) advance_ctl<2>(ctl, slot, cf);
   }
   pipe2d_drain<SYS, R, PREF, 1>(pp);
+  if (t == 0) {
+    __threadfence();
+    if (atomicAdd(&queue[1], 1) == (int)gridDim.x - 1) {
+      queue[0] = 0;
+      queue[1] = 0;
+    }
+  }
 }
 
 // U = sum_k f_k of one batch instance into FP64 [m][ny][nx]
 template <int M, class R>
-__global__ void k_batch_moments(DevParams P, const R* f, double* U) {
+__global__ void k_batch_moments(DevParams P, const R* f, double* U, Ctl* ctl) {
   long long nn = (long long)P.nx * P.ny;
   long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (node >= nn) return;
@@ -109,7 +142,7 @@ __global__ void k_batch_moments(DevParams P, const R* f, double* U) {
   for (int c = 0; c < M; c++) {
     R s = R(0);
 #pragma unroll
-    for (int k = 0; k < 5; k++) s += f[(long long)(k * M + c) * P.plane + off];
+    for (int k = 0; k < 5; k++) s += f[chk((long long)(k * M + c) * P.plane + off, 5ll * M * P.plane, &ctl->status)];
     U[c * nn + node] = (double)s;
   }
 }
@@ -135,7 +168,7 @@ using namespace lbmh;
 namespace {
 
 constexpr int kPrefVariants[2] = {1, 2};
-constexpr int kSegFactors[2] = {1, 2};  // segments per chunk: chunk / factor rows
+constexpr int kBands[4] = {64, 128, 256, 512};  // rows per segment
 
 struct InstHost {
   bool used = false;
@@ -167,7 +200,7 @@ struct lbmh_batch {
   Ctl* d_ctl;
   BatchSeg* d_segs;
   int seg_cap;
-  int* d_cta;
+  int* d_queue;  // segment counter and finished-CTA counter of the running launch
   double* d_sums;
   double* staging;
   size_t staging_bytes;
@@ -177,7 +210,7 @@ struct lbmh_batch {
   long long launched;
   int grid[2];     // resident CTAs per PREF variant
   int variant;     // index into kPrefVariants
-  int seg_factor;  // segments per chunk
+  int band;        // index into kBands
   bool tuned;
   cudaStream_t cap_stream;  // private stream the step graph is captured on
   cudaGraphExec_t graph;
@@ -277,51 +310,25 @@ size_t smem_of(const lbmh_batch* b, int variant) {
   return b->prec == LBMH_FP32 ? batch_smem<float>(b->sys, pref) : batch_smem<double>(b->sys, pref);
 }
 
-// work list: the rows of every strip of every live instance, band-major per
-// instance, cut into `grid` equal chunks (a chunk may split a segment)
+// work list: bands of rows of every strip of every live instance, larger
+// lattices first (their segments are taken first, the small ones fill the
+// tail of the step), band-major within a lattice so that neighbouring strips
+// of a band run side by side and share their halo sectors in L2
 int rebuild_worklist(lbmh_batch* b) {
-  const int G = b->grid[b->variant];
-  std::vector<BatchSeg> base;
-  long long total = 0;
+  const int band = kBands[b->band];
+  std::vector<int> order;
   for (int i = 0; i < b->max_inst; i++)
-    if (b->inst[i].used) total += (long long)b->inst[i].strips * b->inst[i].P.ny;
-  if (total == 0) {
-    b->nsegs = 0;
-    std::vector<int> cta(G + 1, 0);
-    BCK(b, cudaMemcpyAsync(b->d_cta, cta.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, b->stream));
-    return LBMH_OK;
-  }
-  long long chunk = (total + G - 1) / G;
-  int band = (int)std::max<long long>(16, chunk / b->seg_factor);
-  for (int i = 0; i < b->max_inst; i++) {
-    const InstHost& ih = b->inst[i];
-    if (!ih.used) continue;
-    int ny = ih.P.ny;
-    for (int y0 = 0; y0 < ny; y0 += band)
-      for (int s = 0; s < ih.strips; s++) base.push_back(BatchSeg{i, s, y0, std::min(ny, y0 + band), 0, {0, 0, 0}});
-  }
-  // cut the concatenated rows into G chunks
+    if (b->inst[i].used) order.push_back(i);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    return (long long)b->inst[a].strips * b->inst[a].P.ny > (long long)b->inst[c].strips * b->inst[c].P.ny;
+  });
   std::vector<BatchSeg> segs;
-  std::vector<int> cta(G + 1, 0);
-  long long pos = 0;
-  int cur_cta = 0;
-  long long cta_end = total * 1 / G;
-  for (const BatchSeg& sg : base) {
-    int y = sg.yb;
-    while (y < sg.ye) {
-      while (cur_cta < G && pos >= cta_end) {
-        cur_cta++;
-        cta[cur_cta] = (int)segs.size();
-        cta_end = total * (cur_cta + 1) / G;
-      }
-      int take = (int)std::min<long long>(sg.ye - y, cta_end - pos);
-      if (take <= 0) take = sg.ye - y;  // last CTA takes the rest
-      segs.push_back(BatchSeg{sg.inst, sg.strip, y, y + take, 0, {0, 0, 0}});
-      y += take;
-      pos += take;
-    }
+  for (int i : order) {
+    const InstHost& ih = b->inst[i];
+    const int ny = ih.P.ny;
+    for (int y0 = 0; y0 < ny; y0 += band)
+      for (int s = 0; s < ih.strips; s++) segs.push_back(BatchSeg{i, s, y0, std::min(ny, y0 + band), 0, {0, 0, 0}});
   }
-  for (int c = cur_cta + 1; c <= G; c++) cta[c] = (int)segs.size();
   std::vector<char> seen(b->max_inst, 0);
   for (BatchSeg& sg : segs)
     if (!seen[sg.inst]) {
@@ -342,8 +349,9 @@ int rebuild_worklist(lbmh_batch* b) {
   }
   b->h_segs = segs;
   b->nsegs = (int)segs.size();
-  BCK(b, cudaMemcpyAsync(b->d_segs, segs.data(), sizeof(BatchSeg) * segs.size(), cudaMemcpyHostToDevice, b->stream));
-  BCK(b, cudaMemcpyAsync(b->d_cta, cta.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, b->stream));
+  if (!segs.empty())
+    BCK(b, cudaMemcpyAsync(b->d_segs, segs.data(), sizeof(BatchSeg) * segs.size(), cudaMemcpyHostToDevice, b->stream));
+  BCK(b, cudaMemcpyAsync(b->d_queue + 2, &b->nsegs, sizeof(int), cudaMemcpyHostToDevice, b->stream));
   // the host vectors must outlive the asynchronous copies
   BCK(b, cudaStreamSynchronize(b->stream));
   return LBMH_OK;
@@ -352,7 +360,7 @@ int rebuild_worklist(lbmh_batch* b) {
 int launch_one(lbmh_batch* b, int variant, cudaStream_t stream) {
   const int G = b->grid[variant];
   int slot = (int)(b->launched % 3);
-  void* args[] = {(void*)&b->d_insts, (void*)&b->d_segs, (void*)&b->d_cta, (void*)&slot, (void*)&b->d_sums};
+  void* args[] = {(void*)&b->d_insts, (void*)&b->d_segs, (void*)&b->d_queue, (void*)&slot, (void*)&b->d_sums};
   BCK(b, cudaLaunchKernel(kernel_of(b, variant), dim3(G), dim3(FT), args, smem_of(b, variant), stream));
   b->launched++;
   return LBMH_OK;
@@ -401,7 +409,7 @@ void free_batch(lbmh_batch* b) {
   cudaFree(b->d_insts);
   cudaFree(b->d_ctl);
   cudaFree(b->d_segs);
-  cudaFree(b->d_cta);
+  cudaFree(b->d_queue);
   cudaFree(b->d_sums);
   cudaFree(b->staging);
   delete b;
@@ -432,7 +440,7 @@ int init_instance(lbmh_batch* b, int i, const double* U0dev) {
   k_init_speed<SYS, 2><<<reduce_blocks_for(nn), kBlock, 0, b->stream>>>(P, U0dev, ctl);
   k_init_eq<SYS, 2, R><<<reduce_blocks_for(nn), kBlock, 0, b->stream>>>(P, U0dev, f0, ctl);
   long long npad = (long long)P.ny * b->Q * b->m * 2 * NGHOST;
-  k_fill_pads<R><<<blocks_for(npad), kBlock, 0, b->stream>>>(P, b->Q * b->m, f0);
+  k_fill_pads<R><<<blocks_for(npad), kBlock, 0, b->stream>>>(P, b->Q * b->m, f0, ctl);
   k_ctl_to_slot<<<1, 1, 0, b->stream>>>(ctl, (int)(b->launched % 3));
   BCK(b, cudaGetLastError());
   return LBMH_OK;
@@ -457,10 +465,10 @@ int moments_of(lbmh_batch* b, int i, int par, double* Udev) {
   long long nn = (long long)ih.P.nx * ih.P.ny;
   const R* f = (const R*)(b->arena + ih.off[par]);
   switch (b->m) {
-    case 1: k_batch_moments<1, R><<<blocks_for(nn), kBlock, 0, b->stream>>>(ih.P, f, Udev); break;
-    case 3: k_batch_moments<3, R><<<blocks_for(nn), kBlock, 0, b->stream>>>(ih.P, f, Udev); break;
-    case 4: k_batch_moments<4, R><<<blocks_for(nn), kBlock, 0, b->stream>>>(ih.P, f, Udev); break;
-    case 5: k_batch_moments<5, R><<<blocks_for(nn), kBlock, 0, b->stream>>>(ih.P, f, Udev); break;
+    case 1: k_batch_moments<1, R><<<blocks_for(nn), kBlock, 0, b->stream>>>(ih.P, f, Udev, b->d_ctl + i); break;
+    case 3: k_batch_moments<3, R><<<blocks_for(nn), kBlock, 0, b->stream>>>(ih.P, f, Udev, b->d_ctl + i); break;
+    case 4: k_batch_moments<4, R><<<blocks_for(nn), kBlock, 0, b->stream>>>(ih.P, f, Udev, b->d_ctl + i); break;
+    case 5: k_batch_moments<5, R><<<blocks_for(nn), kBlock, 0, b->stream>>>(ih.P, f, Udev, b->d_ctl + i); break;
     default: return bfail(b, LBMH_ERR_INVALID_ARG, "unsupported field count");
   }
   BCK(b, cudaGetLastError());
@@ -495,7 +503,7 @@ int lbmh_batch_create(int system, int precision, int64_t capacity_bytes, int max
   b->d_insts = nullptr;
   b->d_ctl = nullptr;
   b->d_segs = nullptr;
-  b->d_cta = nullptr;
+  b->d_queue = nullptr;
   b->d_sums = nullptr;
   b->staging = nullptr;
   b->staging_bytes = 0;
@@ -503,7 +511,7 @@ int lbmh_batch_create(int system, int precision, int64_t capacity_bytes, int max
   b->seg_cap = 4096;
   b->launched = 0;
   b->variant = 1;  // PREF 2
-  b->seg_factor = 1;
+  b->band = 2;  // 256 rows
   b->tuned = false;
   b->graph_ok = false;
   b->graph_variant = -1;
@@ -529,19 +537,18 @@ int lbmh_batch_create(int system, int precision, int64_t capacity_bytes, int max
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     b->grid[v] = per_sm * sms;
   }
-  int gmax = std::max(b->grid[0], b->grid[1]);
   if (cudaMalloc((void**)&b->arena, b->capacity) != cudaSuccess ||
       cudaMalloc((void**)&b->d_insts, sizeof(BatchInst) * max_instances) != cudaSuccess ||
       cudaMalloc((void**)&b->d_ctl, sizeof(Ctl) * max_instances) != cudaSuccess ||
       cudaMalloc((void**)&b->d_segs, sizeof(BatchSeg) * b->seg_cap) != cudaSuccess ||
-      cudaMalloc((void**)&b->d_cta, sizeof(int) * (gmax + 1)) != cudaSuccess ||
+      cudaMalloc((void**)&b->d_queue, sizeof(int) * 4) != cudaSuccess ||
       cudaMalloc((void**)&b->d_sums, sizeof(double) * b->m * b->seg_cap) != cudaSuccess) {
     cudaGetLastError();
     free_batch(b);
     return bfail(nullptr, LBMH_ERR_OOM, "batch device allocation failed");
   }
   cudaMemset(b->d_ctl, 0, sizeof(Ctl) * max_instances);
-  cudaMemset(b->d_cta, 0, sizeof(int) * (gmax + 1));
+  cudaMemset(b->d_queue, 0, sizeof(int) * 4);
   b->free_list.push_back(Block{0, b->capacity});
   *out = b;
   return LBMH_OK;
@@ -585,6 +592,7 @@ int lbmh_batch_add(lbmh_batch* b, const lbmh_problem* p, const double* U0, int o
   ih.used = true;
   ih.prob = *p;
   ih.P = make_devparams(p, padded_pitch(p->nx, b->elem));
+  apply_wait_hook(ih.P);
   ih.P.max_steps = max_steps > 0 ? max_steps : 0;
   ih.P.T = T > 0.0 ? T : 0.0;
   ih.bytes = (size_t)b->Q * b->m * ih.P.plane * b->elem;
@@ -673,11 +681,11 @@ int lbmh_batch_autotune(lbmh_batch* b, int steps_per_candidate, double* best_ms)
   BCK(b, cudaEventCreate(&e0));
   BCK(b, cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_v = b->variant, best_f = b->seg_factor;
+  int best_v = b->variant, best_b = b->band;
   for (int v = 0; v < 2; v++)
-    for (int fi = 0; fi < 2; fi++) {
+    for (int bi = 0; bi < 4; bi++) {
       b->variant = v;
-      b->seg_factor = kSegFactors[fi];
+      b->band = bi;
       int rc = rebuild_worklist(b);
       if (rc) return rc;
       rc = launch_one(b, v);  // warm-up: one real step
@@ -695,13 +703,13 @@ int lbmh_batch_autotune(lbmh_batch* b, int steps_per_candidate, double* best_ms)
       if (ms < best) {
         best = ms;
         best_v = v;
-        best_f = kSegFactors[fi];
+        best_b = bi;
       }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->variant = best_v;
-  b->seg_factor = best_f;
+  b->band = best_b;
   b->tuned = true;
   if (best_ms) *best_ms = best;
   return rebuild_worklist(b);
@@ -757,7 +765,7 @@ int lbmh_batch_info(lbmh_batch* b, int64_t* used_bytes, int64_t* capacity_bytes,
   if (capacity_bytes) *capacity_bytes = (int64_t)b->capacity;
   if (active) *active = n;
   if (grid) *grid = b->grid[b->variant];
-  if (variant) *variant = kPrefVariants[b->variant] * 10 + b->seg_factor;
+  if (variant) *variant = kPrefVariants[b->variant] * 1000 + kBands[b->band];
   return LBMH_OK;
 }
 

@@ -79,6 +79,10 @@ struct DevParams {
   // lattice.
   int ywin0, ywin1;
   int row0;
+  // polls of each CTA's first row-load wait in the 2D row pipeline (1 << 22;
+  // LBMH_TEST_FIRST_WAIT_POLLS at handle creation sets it, so that a test can
+  // make a wait run out without disturbing the GPU)
+  int first_wait_polls;
   PhysConstF pf;
 };
 
@@ -102,8 +106,27 @@ struct Ctl {
 
 // status bits: NONPHYSICAL (NaN/inf, rho <= 0 or p <= 0) fails lbmh_moments;
 // NEGATIVE_DEPTH (shallow water h < -1e-12, which the scheme produces at
-// wet-dry fronts: it is not positivity preserving) is reported only.
-enum : unsigned int { ST_NONPHYSICAL = 1u, ST_NOROOT = 2u, ST_TIMEOUT = 4u, ST_NEGATIVE_DEPTH = 8u };
+// wet-dry fronts: it is not positivity preserving) is reported only; BOUNDS
+// (bounds-checked builds only) marks an index that left its array.
+enum : unsigned int { ST_NONPHYSICAL = 1u, ST_NOROOT = 2u, ST_TIMEOUT = 4u, ST_NEGATIVE_DEPTH = 8u, ST_BOUNDS = 16u };
+
+// Index guard of the bounds-checked build (compiled with LBMH_CHECK_BOUNDS):
+// an index outside [0, n) sets ST_BOUNDS in *st and is clamped into range, so
+// a wrong index shows up as a status bit (and wrong values), never as a
+// memory fault.  In other builds it is the identity and costs nothing.
+template <class I>
+__device__ __forceinline__ I chk(I i, long long n, unsigned int* st) {
+#ifdef LBMH_CHECK_BOUNDS
+  if ((long long)i < 0 || (long long)i >= n) {
+    if (st) atomicOr(st, ST_BOUNDS);
+    return (long long)i < 0 ? I(0) : I(n - 1);
+  }
+#else
+  (void)n;
+  (void)st;
+#endif
+  return i;
+}
 
 // Coefficients of one step, computed identically by every thread from the
 // control slot: dt (2.21), lambda = dx/dt, alpha_j = abar_j + eps, and the

@@ -96,9 +96,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait: gives up after ~2^22 polls (each try_wait may itself sleep)
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  for (int i = 0; i < (1 << 22); i++)
+// bounded wait: gives up after `polls` polls (each try_wait may itself sleep;
+// the default 2^22 polls last at least a few tenths of a second, thousands of
+// times the latency of a row load)
+constexpr int kWaitPolls = 1 << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int polls = kWaitPolls) {
+  for (int i = 0; i < polls; i++)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -318,7 +321,8 @@ struct Pipe2D {
 template <int SYS, class R, int PREF, int CPT>
 __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml, const CUtensorMap* tms, R* fout,
                                               const DevParams& P, const Phys<R>& K, const Coef2D<R>& cc, int strip,
-                                              int yb, int ye, int nxs, R& sp0, R& sp1, Acc<R>* acc, unsigned& st) {
+                                              int yb, int ye, int nxs, R& sp0, R& sp1, Acc<R>* acc, unsigned& st,
+                                              unsigned int* stc) {
   constexpr int M = Fields<SYS, 2>::M, Q = 5, QM = Q * M;
   constexpr bool SRC = HasSource<SYS>::value;
   using L = Smem2D<M, R, PREF, CPT>;
@@ -436,7 +440,10 @@ __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml
           tma_load_row(tml, smem_u32(fring + (size_t)(s % S) * QM * NC), smem_u32(&bars[s % S]), x0 - 4 + XPAD, my, row_bytes);
           issued_end = s + 1;
         }
-        if (!mbar_wait_bounded(smem_u32(&bars[sidx % S]), (sidx / S) & 1u)) *s_abort = 1;
+        // the CTA's first row wait takes its limit from the problem (a test can
+        // make it give up at once); every other wait polls kWaitPolls times
+        if (!mbar_wait_bounded(smem_u32(&bars[sidx % S]), (sidx / S) & 1u, sidx == 0 ? P.first_wait_polls : kWaitPolls))
+          *s_abort = 1;
         R* frow_w = fring + (size_t)(sidx % S) * QM * NC;
         if (P.has_special_bc) {  // ghost nodes across reflecting / inflow sides (own columns only)
           const int rs = ghost_side(r, P.ny, P.bc[2], P.bc[3]);
@@ -606,11 +613,12 @@ __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml
           }
           if (outc[j] && row_out) {
             if (gx[j] >= nxs) {  // tail columns outside the bulk store
-              R* base = fout + (long long)y * P.pitch + XPAD + gx[j];
+              const long long o = (long long)y * P.pitch + XPAD + gx[j];
   #pragma unroll
               for (int k = 0; k < Q; k++)
   #pragma unroll
-                for (int c = 0; c < M; c++) base[(long long)(k * M + c) * P.plane] = Fk[k][c];
+                for (int c = 0; c < M; c++)
+                  fout[chk(o + (long long)(k * M + c) * P.plane, (long long)QM * P.plane, stc)] = Fk[k][c];
             }
             sp0 = rmax(sp0, max_speed<SYS, 2, R>(K, wn, 0));
             sp1 = rmax(sp1, max_speed<SYS, 2, R>(K, wn, 1));
@@ -639,10 +647,10 @@ __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml
         __syncthreads();
         if (t == 0 && row_out && x0 < nxs) tma_store_row(tms, smem_u32(stage), x0, y);
         if (row_out && has_pads) {
-          R* base = fout + (long long)y * P.pitch + XPAD;
+          const long long o = (long long)y * P.pitch + XPAD;
   #pragma unroll
           for (int i = 0; i < NPAD; i++)
-            if (pad_sidx[i] >= 0) base[pad_goff[i]] = stage[pad_sidx[i]];
+            if (pad_sidx[i] >= 0) fout[chk(o + pad_goff[i], (long long)QM * P.plane, stc)] = stage[pad_sidx[i]];
         }
       }
 }
@@ -664,7 +672,11 @@ __device__ __forceinline__ void pipe2d_init(Pipe2D& pp, unsigned char* smem_raw,
 }
 
 // Before the CTA exits: let every row load it issued land (after an abort) and
-// every bulk store finish.
+// every bulk store finish.  After an abort the loads still in flight are those
+// from the one being consumed up to the last issued (at most 1 + PREF); each is
+// waited for with the full kWaitPolls limit.  A row load that has not landed
+// after that many polls means the memory system itself has stopped: the CTA
+// then exits with ST_TIMEOUT set, the one action left to it.
 template <int SYS, class R, int PREF, int CPT>
 __device__ __forceinline__ void pipe2d_drain(Pipe2D& pp) {
   using L = Smem2D<Fields<SYS, 2>::M, R, PREF, CPT>;
@@ -725,7 +737,7 @@ __global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensor
     const int yb = P.ywin0 + b * band + (int)(local % rb);
     const int ye = (int)min((long long)(P.ywin0 + b * band + rb), (long long)yb + (we - w));
     w += ye - yb;
-    run_segment2d<SYS, R, PREF, CPT>(pp, tml, tms, fout, P, K, cc, strip, yb, ye, nxs, sp0, sp1, acc, st);
+    run_segment2d<SYS, R, PREF, CPT>(pp, tml, tms, fout, P, K, cc, strip, yb, ye, nxs, sp0, sp1, acc, st, &ctl->status);
   }
   pipe2d_drain<SYS, R, PREF, CPT>(pp);
   if (pp.aborted) st |= ST_TIMEOUT;
@@ -796,7 +808,7 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
 #pragma unroll
     for (int c = 0; c < M; c++)
 #pragma unroll
-      for (int k = 0; k < Q; k++) f[k][c] = fin[(long long)(k * M + c) * P.plane + mx + XPAD];
+      for (int k = 0; k < Q; k++) f[k][c] = fin[chk((long long)(k * M + c) * P.plane + mx + XPAD, (long long)Q * M * P.plane, &ctl->status)];
     if (P.has_special_bc) {
       const int cs = ghost_side(gx, P.nx, P.bc[0], P.bc[1]);
       if (cs >= BC_REFLECT) ghost_fixup<SYS, 1, R>(&f[0][0], 1, cs, -1, K, inflow_state<R>(P), a0, al0, al0, inv2l);
@@ -866,7 +878,7 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
         for (int c = 0; c < M; c++) {
           R v = Fk[k][c];
           if constexpr (SRC) v += hdt * ak[k] * Sn[c];
-          fout[(long long)(k * M + c) * P.plane + gx + XPAD] = v;
+          fout[chk((long long)(k * M + c) * P.plane + gx + XPAD, (long long)Q * M * P.plane, &ctl->status)] = v;
           Uo[c] += v;
         }
       Prim<R> wn = primitives<SYS, 1, R>(K, Uo);

@@ -4,6 +4,7 @@
 #include <math.h>
 
 #include <cmath>
+#include <stdlib.h>
 #include <string.h>
 
 #include <string>
@@ -101,6 +102,7 @@ inline DevParams make_devparams(const lbmh_problem* p, int pitch) {
   P.ywin0 = 0;
   P.ywin1 = P.ny;
   P.row0 = 0;
+  P.first_wait_polls = 1 << 22;
   for (int s = 0; s < 4; s++) P.bc[s] = p->bc[s];
   if (p->dim == 1) P.bc[2] = P.bc[3] = LBMH_BC_PERIODIC;
   P.bc_z[0] = p->dim == 3 ? p->bc_z[0] : LBMH_BC_PERIODIC;
@@ -158,6 +160,13 @@ inline DevParams make_devparams(const lbmh_problem* p, int pitch) {
   f.sponge_dx_over_w = (float)P.sponge_dx_over_w;
   for (int c = 0; c < 8; c++) f.u_in[c] = (float)P.u_in[c];
   return P;
+}
+
+// test hook: LBMH_TEST_FIRST_WAIT_POLLS sets the polls of each CTA's first
+// row-load wait (0: the wait gives up at once and the step reports a timeout)
+inline void apply_wait_hook(DevParams& P) {
+  const char* e = getenv("LBMH_TEST_FIRST_WAIT_POLLS");
+  if (e && e[0]) P.first_wait_polls = atoi(e);
 }
 
 // elements per row of a padded distribution plane (rows start on 128 bytes)

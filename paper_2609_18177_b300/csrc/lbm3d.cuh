@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(kBlock) k3_init_eq(DevParams P, const double* 
   const double al[3] = {ab[0] + P.eps, ab[1] + P.eps, ab[2] + P.eps};
   const R a0 = R(1.0 - (al[0] + al[1] + al[2]) / lam), inv2l = R(1.0 / (2.0 * lam));
   const Phys<R> K = make_phys<R>(P);
+  const long long nf = 7ll * M * P.plane;  // elements of the distributions (index guards)
   double s[3] = {0.0, 0.0, 0.0};
   for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < nn;
        node += (long long)gridDim.x * blockDim.x) {
@@ -269,15 +270,15 @@ __global__ void __launch_bounds__(kBlock) k3_init_eq(DevParams P, const double* 
     for (int c = 0; c < M; c++) U[c] = R(U0[c * nn + node]);
     const Prim3<R> w = prim3<SYS, R>(K, U);
 #pragma unroll
-    for (int c = 0; c < M; c++) f[(long long)c * P.plane + off] = a0 * U[c];
+    for (int c = 0; c < M; c++) f[chk((long long)c * P.plane + off, nf, &ctl->status)] = a0 * U[c];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       R F[M];
       flux3<SYS, R>(K, P, U, w, d, F);
 #pragma unroll
       for (int c = 0; c < M; c++) {
-        f[(long long)((1 + d) * M + c) * P.plane + off] = (R(al[d]) * U[c] + F[c]) * inv2l;
-        f[(long long)((4 + d) * M + c) * P.plane + off] = (R(al[d]) * U[c] - F[c]) * inv2l;
+        f[chk((long long)((1 + d) * M + c) * P.plane + off, nf, &ctl->status)] = (R(al[d]) * U[c] + F[c]) * inv2l;
+        f[chk((long long)((4 + d) * M + c) * P.plane + off, nf, &ctl->status)] = (R(al[d]) * U[c] - F[c]) * inv2l;
       }
     }
     // moments of the stored distributions, summed k = 0..6 as a step does
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(kBlock) k3_init_eq(DevParams P, const double* 
     for (int c = 0; c < M; c++) {
       R sum = R(0);
 #pragma unroll
-      for (int k = 0; k < 7; k++) sum += f[(long long)(k * M + c) * P.plane + off];
+      for (int k = 0; k < 7; k++) sum += f[chk((long long)(k * M + c) * P.plane + off, nf, &ctl->status)];
       Us[c] = sum;
     }
     const Prim3<R> ws = prim3<SYS, R>(K, Us);
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(kBlock) k3_speed_of_f(DevParams P, R* const* b
     for (int c = 0; c < M; c++) {
       R sum = R(0);
 #pragma unroll
-      for (int k = 0; k < 7; k++) sum += f[(long long)(k * M + c) * P.plane + off];
+      for (int k = 0; k < 7; k++) sum += f[chk((long long)(k * M + c) * P.plane + off, 7ll * M * P.plane, &ctl->status)];
       U[c] = sum;
     }
     const Prim3<R> w = prim3<SYS, R>(K, U);
@@ -355,14 +356,15 @@ __global__ void k3_moments_ext(DevParams P, R* const* buf, const Ctl* ctl, int s
   const int par = ctl->parity[slot];
   const R* f = buf[par];
   R* Ue = ue_copy<M>(Ue2, G, par);
+  unsigned int* const stc = (unsigned int*)&ctl->status;  // index guards (bounds-checked builds)
   const long long off = cell3(P, map_index(ei - GH, P.nx, P.bc[0], P.bc[1]), map_index(ej - GH, P.ny3, P.bc[2], P.bc[3]),
                               map_index(ek - GH, P.nz3, P.bc_z[0], P.bc_z[1]));
 #pragma unroll
   for (int c = 0; c < M; c++) {
     R sum = R(0);
 #pragma unroll
-    for (int q = 0; q < 7; q++) sum += f[(long long)(q * M + c) * P.plane + off];
-    Ue[(long long)c * n + e] = sum;
+    for (int q = 0; q < 7; q++) sum += f[chk((long long)(q * M + c) * P.plane + off, 7ll * M * P.plane, stc)];
+    Ue[chk((long long)c * n + e, (long long)M * n, stc)] = sum;
   }
 }
 
@@ -403,7 +405,9 @@ __global__ void k3_ghost_fill(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G,
   R* Ue = ue_copy<M>(Ue2, G, ctl->parity[slot]);
   const long long e = G.idx(ek, ej, ei), src = G.idx(mk + GH, mj + GH, mi + GH);
 #pragma unroll
-  for (int c = 0; c < M; c++) Ue[(long long)c * n + e] = Ue[(long long)c * n + src];
+  for (int c = 0; c < M; c++)
+    Ue[chk((long long)c * n + e, (long long)M * n, (unsigned int*)&ctl->status)] =
+        Ue[chk((long long)c * n + src, (long long)M * n, (unsigned int*)&ctl->status)];
 }
 
 // threads per block of the extended-grid kernels; planes a thread of the
@@ -424,21 +428,22 @@ __global__ void k3_indicator(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, 
   if (ei < 1 || ei >= G.ex - 1 || ej < 1 || ej >= G.ey - 1 || ek < 1 || ek >= G.ez - 1) return;
   const Phys<R> K = make_phys<R>(P);
   const long long stride[3] = {1, G.ex, (long long)G.ex * G.ey};
+  unsigned int* const stc = (unsigned int*)&ctl->status;  // index guards (bounds-checked builds)
   R U0[M], dm[M], dp[M];
 #pragma unroll
-  for (int c = 0; c < M; c++) U0[c] = Ue[(long long)c * n + e];
+  for (int c = 0; c < M; c++) U0[c] = Ue[chk((long long)c * n + e, (long long)M * n, stc)];
   const Prim3<R> w = prim3<SYS, R>(K, U0);
   R sum = R(0);
 #pragma unroll
   for (int d = 0; d < 3; d++) {
 #pragma unroll
     for (int c = 0; c < M; c++) {
-      dm[c] = U0[c] - Ue[(long long)c * n + e - stride[d]];
-      dp[c] = Ue[(long long)c * n + e + stride[d]] - U0[c];
+      dm[c] = U0[c] - Ue[chk((long long)c * n + e - stride[d], (long long)M * n, stc)];
+      dp[c] = Ue[chk((long long)c * n + e + stride[d], (long long)M * n, stc)] - U0[c];
     }
     sum += theta3<SYS, R>(K, w, d, dm, dp);
   }
-  nu[e] = sum;
+  nu[chk(e, n, stc)] = sum;
 }
 
 // K2: omega = 1 + 1/(1 + nu~), nu~ the sum over the 3^3 box (Eq. 2.15, 2.16).
@@ -452,13 +457,15 @@ __global__ void k3_omega(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, cons
   if (ei < 2 || ei >= G.ex - 2 || ej < 2 || ej >= G.ey - 2) return;
   if (P.T > 0.0 && ctl->t[slot] >= P.T) return;
   const int k0 = max(2, (int)blockIdx.z * kZ3), k1 = min(G.ez - 2, (int)blockIdx.z * kZ3 + kZ3);
+  const long long n = (long long)G.ex * G.ey * G.ez;
+  unsigned int* const stc = (unsigned int*)&ctl->status;  // index guards (bounds-checked builds)
   if (P.omega_mode == 1) {
     R wf;
     if constexpr (sizeof(R) == 4)
       wf = P.pf.omega_fixed;
     else
       wf = P.omega_fixed;
-    for (int ek = k0; ek < k1; ek++) om[G.idx(ek, ej, ei)] = wf;
+    for (int ek = k0; ek < k1; ek++) om[chk(G.idx(ek, ej, ei), n, stc)] = wf;
     return;
   }
   R win[3][9];  // nu of planes ek - 1, ek, ek + 1 around (ei, ej)
@@ -467,7 +474,7 @@ __global__ void k3_omega(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, cons
 #pragma unroll
     for (int bj = -1; bj <= 1; bj++)
 #pragma unroll
-      for (int bi = -1; bi <= 1; bi++) o[(bj + 1) * 3 + bi + 1] = nu[b + (long long)bj * G.ex + bi];
+      for (int bi = -1; bi <= 1; bi++) o[(bj + 1) * 3 + bi + 1] = nu[chk(b + (long long)bj * G.ex + bi, n, stc)];
   };
   if (k0 < k1) {
     load_plane(k0 - 1, win[0]);
@@ -481,7 +488,7 @@ __global__ void k3_omega(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, cons
     for (int pz = 0; pz < 3; pz++)
 #pragma unroll
       for (int q = 0; q < 9; q++) s += win[pz][q];
-    om[G.idx(ek, ej, ei)] = R(1) + fdiv(R(1), R(1) + s);
+    om[chk(G.idx(ek, ej, ei), n, stc)] = R(1) + fdiv(R(1), R(1) + s);
 #pragma unroll
     for (int q = 0; q < 9; q++) {
       win[0][q] = win[1][q];
@@ -700,6 +707,8 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks))
   R* Uo_ext = ue_copy<M>(Ue2, G, par ^ 1);  // U^{n+1} of the interior, for the next step
   // offsets in IX: int where every offset of the lattice fits (chosen at launch), else long long
   const IX n = (IX)G.ex * G.ey * G.ez, pl = (IX)P.plane;
+  const long long nf = 7ll * M * P.plane;  // elements of the distributions (index guards)
+  unsigned int* const stc = &ctl->status;
   auto eidx = [&](int ek, int ej, int ei) -> IX { return ((IX)ek * G.ey + ej) * G.ex + ei; };
   auto fidx = [&](int ci, int cj, int ck) -> IX { return ((IX)ck * P.ny3 + cj) * P.pitch + ci + XPAD; };
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -725,13 +734,13 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks))
     const IX e = eidx(k + GH, r + GH, i + GH);
     const IX off = fidx(mi, map_index(r, P.ny3, P.bc[2], P.bc[3]), k);
 #pragma unroll
-    for (int c = 0; c < M; c++) oU[c] = halo_or_out ? Ue[(IX)c * n + e] : R(1);
-    ow = halo_or_out ? om[e] : R(1);
+    for (int c = 0; c < M; c++) oU[c] = halo_or_out ? Ue[chk((IX)c * n + e, (long long)M * n, stc)] : R(1);
+    ow = halo_or_out ? om[chk(e, n, stc)] : R(1);
 #pragma unroll
     for (int q = 0; q < 5; q++) {
       const int qq = q == 0 ? 0 : (q == 1 ? 1 : (q == 2 ? 4 : (q == 3 ? 2 : 5)));  // 0, +x, -x, +y, -y
 #pragma unroll
-      for (int c = 0; c < M; c++) of[q][c] = halo_or_out ? f[(IX)(qq * M + c) * pl + off] : R(0);
+      for (int c = 0; c < M; c++) of[q][c] = halo_or_out ? f[chk((IX)(qq * M + c) * pl + off, nf, stc)] : R(0);
     }
   };
   // operands of the +-z posts of an output row: U, omega and f_{+z} at plane
@@ -746,10 +755,10 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks))
       const IX offz = fidx(mi, my, s2 == 0 ? mkm : mkp);
 #pragma unroll
       for (int c = 0; c < M; c++) {
-        zU[s2][c] = Ue[(IX)c * n + ez];
-        zf[s2][c] = f[(IX)(qq * M + c) * pl + offz];
+        zU[s2][c] = Ue[chk((IX)c * n + ez, (long long)M * n, stc)];
+        zf[s2][c] = f[chk((IX)(qq * M + c) * pl + offz, nf, stc)];
       }
-      zw[s2] = om[ez];
+      zw[s2] = om[chk(ez, n, stc)];
     }
   };
   // lane registers: post_0, post_{+y} and the received F_{+x}, F_{-x} of row
@@ -840,13 +849,13 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks))
         for (int c = 0; c < M; c++) {
           R v = Fk[q][c];
           if constexpr (SRC) v += hdt * akq * Sn[c];
-          fo[(IX)(q * M + c) * pl + oo] = v;
+          fo[chk((IX)(q * M + c) * pl + oo, nf, stc)] = v;
           Uo[c] += v;
         }
       }
       const IX eo = eidx(k + GH, y + GH, i + GH);
 #pragma unroll
-      for (int c = 0; c < M; c++) Uo_ext[(IX)c * n + eo] = Uo[c];
+      for (int c = 0; c < M; c++) Uo_ext[chk((IX)c * n + eo, (long long)M * n, stc)] = Uo[c];
       const Prim3<R> wn = prim3<SYS, R>(K, Uo);
       sp0 = rmax(sp0, speed3<SYS, R>(K, P, wn, 0));
       sp1 = rmax(sp1, speed3<SYS, R>(K, P, wn, 1));

@@ -113,7 +113,7 @@ struct Impl {
 
   static void fill_pads(lbmh_handle* h, R* f) {
     long long n = (long long)h->P.ny * Q * M * 2 * NGHOST;
-    k_fill_pads<R><<<blocks_for(n), kBlock, 0, h->stream>>>(h->P, Q * M, f);
+    k_fill_pads<R><<<blocks_for(n), kBlock, 0, h->stream>>>(h->P, Q * M, f, h->ctl);
   }
 
   static int unfused_front(lbmh_handle* h, int slot, const DevParams& P) {
@@ -182,7 +182,7 @@ struct Impl {
 
   static int set_f(lbmh_handle* h, const double* dev) {
     long long n = (long long)h->P.nx * h->P.ny * Q * M;
-    k_set_f<R><<<blocks_for(n), kBlock, 0, h->stream>>>(h->P, Q * M, (R*)h->fbuf[0], dev);
+    k_set_f<R><<<blocks_for(n), kBlock, 0, h->stream>>>(h->P, Q * M, (R*)h->fbuf[0], dev, h->ctl);
     fill_pads(h, (R*)h->fbuf[0]);
     k_speed_of_f<SYS, D, R><<<reduce_blocks_for((long long)h->P.nx * h->P.ny), kBlock, 0, h->stream>>>(
         h->P, (R* const*)h->dbuf, h->ctl);
@@ -277,7 +277,7 @@ struct Impl3 {
 
   static int set_f(lbmh_handle* h, const double* dev) {
     const long long n = (long long)h->P.nx * h->P.ny * Q * M;
-    k_set_f<R><<<blocks_for(n), kBlock, 0, h->stream>>>(h->P, Q * M, (R*)h->fbuf[0], dev);
+    k_set_f<R><<<blocks_for(n), kBlock, 0, h->stream>>>(h->P, Q * M, (R*)h->fbuf[0], dev, h->ctl);
     k3_speed_of_f<SYS, R><<<reduce_blocks_for((long long)h->P.nx * h->P.ny), kBlock, 0, h->stream>>>(
         h->P, (R* const*)h->dbuf, h->ctl);
     cudaError_t e = cudaGetLastError();
@@ -462,7 +462,11 @@ int read_ctl(lbmh_handle* h, Ctl* out) {
 
 extern "C" {
 
-const char* lbmh_version(void) { return "lbmh 0.1 sm_103a"; }
+#ifdef LBMH_CHECK_BOUNDS
+const char* lbmh_version(void) { return "lbmh 0.2 sm_103a bounds-checked"; }
+#else
+const char* lbmh_version(void) { return "lbmh 0.2 sm_103a"; }
+#endif
 
 const char* lbmh_last_error(const lbmh_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
@@ -507,6 +511,7 @@ int create_impl(const lbmh_problem* p, const SlabGeom* sg, lbmh_handle** out) {
   h->P = make_devparams(p, padded_pitch(p->nx, h->elem));
   DevParams& P = h->P;
   h->plane = P.plane;
+  apply_wait_hook(P);
   h->halo_lo = sg ? sg->halo_lo : 0;
   h->halo_hi = sg ? sg->halo_hi : 0;
   if (sg) {
@@ -698,6 +703,7 @@ int lbmh_moments(lbmh_handle* h, double* U_out, int on_device, double* t, int64_
   if (rc) return rc;
   if (t) *t = c.t[slot];
   if (steps) *steps = c.nsteps[slot];
+  if (c.status & ST_BOUNDS) return fail(h, LBMH_ERR_BOUNDS, "an index left its array (bounds-checked build)");
   if (c.status & ST_TIMEOUT) return fail(h, LBMH_ERR_TIMEOUT, "a bounded device-side wait gave up");
   if (c.status & ST_NONPHYSICAL) return fail(h, LBMH_ERR_NONPHYSICAL, "a step produced a non-physical state");
   return LBMH_OK;
@@ -1109,6 +1115,7 @@ extern "C" int lbmh_step_static(const lbmh_problem* p, const double* f_in, doubl
     if (e != cudaSuccess) return fail(nullptr, LBMH_ERR_CUDA, std::string("static step readback: ") + cudaGetErrorString(e));
     if (dt_out) *dt_out = c.last_dt;
     if (status_out) *status_out = c.status;
+    if (c.status & ST_BOUNDS) return fail(nullptr, LBMH_ERR_BOUNDS, "an index left its array (bounds-checked build)");
     if (c.status & ST_NONPHYSICAL) return fail(nullptr, LBMH_ERR_NONPHYSICAL, "the step produced a non-physical state");
   }
   (void)Q;

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(DevParams P, const double* U
       }
 #pragma unroll
       for (int c = 0; c < M; c++) {
-        f[(long long)(k * M + c) * P.plane + off] = feq[c];
+        f[chk((long long)(k * M + c) * P.plane + off, (long long)Q * M * P.plane, &ctl->status)] = feq[c];
         Us[c] += feq[c];
       }
     }
@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(DevParams P, const double* U
 // U = sum_k f_k into FP64 [m][ny][nx]
 template <int M, int Q, class R>
 __global__ void k_moments(DevParams P, R* const* buf, const Ctl* ctl, int slot, double* U) {
+  unsigned int* st = (unsigned int*)&ctl->status;
   long long nn = (long long)P.nx * P.ny;
   long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (node >= nn) return;
@@ -136,7 +137,7 @@ __global__ void k_moments(DevParams P, R* const* buf, const Ctl* ctl, int slot, 
   for (int c = 0; c < M; c++) {
     R s = R(0);
 #pragma unroll
-    for (int k = 0; k < Q; k++) s += f[(long long)(k * M + c) * P.plane + off];
+    for (int k = 0; k < Q; k++) s += f[chk((long long)(k * M + c) * P.plane + off, (long long)Q * M * P.plane, st)];
     U[c * nn + node] = (double)s;
   }
 }
@@ -150,17 +151,17 @@ __global__ void k_get_f(DevParams P, int QM, R* const* buf, const Ctl* ctl, int 
   const R* f = buf[ctl->parity[slot]];
   long long q = idx / nn, node = idx % nn;
   int j = (int)(node / P.nx), i = (int)(node % P.nx);
-  out[idx] = (double)f[q * P.plane + cell(P, i, j)];
+  out[idx] = (double)f[chk(q * P.plane + cell(P, i, j), (long long)QM * P.plane, (unsigned int*)&ctl->status)];
 }
 
 template <class R>
-__global__ void k_set_f(DevParams P, int QM, R* f, const double* in) {
+__global__ void k_set_f(DevParams P, int QM, R* f, const double* in, Ctl* ctl) {
   long long nn = (long long)P.nx * P.ny;
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= nn * QM) return;
   long long q = idx / nn, node = idx % nn;
   int j = (int)(node / P.nx), i = (int)(node % P.nx);
-  f[q * P.plane + cell(P, i, j)] = R(in[idx]);
+  f[chk(q * P.plane + cell(P, i, j), (long long)QM * P.plane, &ctl->status)] = R(in[idx]);
 }
 
 // speed bound of the stored distributions -> slot 0 (after lbmh_set_f)
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(kBlock) k_speed_of_f(DevParams P, R* const* bu
     for (int c = 0; c < M; c++) {
       R s = R(0);
 #pragma unroll
-      for (int k = 0; k < Q; k++) s += f[(long long)(k * M + c) * P.plane + off];
+      for (int k = 0; k < Q; k++) s += f[chk((long long)(k * M + c) * P.plane + off, (long long)Q * M * P.plane, &ctl->status)];
       U[c] = s;
     }
     Prim<R> w = primitives<SYS, D, R>(K, U);
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(kBlock) k_speed_of_f(DevParams P, R* const* bu
 // ghost columns of every row := the wrapped / clamped node (after the
 // distributions were written by something other than a fused 2D step)
 template <class R>
-__global__ void k_fill_pads(DevParams P, int QM, R* f) {
+__global__ void k_fill_pads(DevParams P, int QM, R* f, Ctl* ctl) {
   long long rows = (long long)P.ny * QM;
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= rows * 2 * NGHOST) return;
@@ -202,8 +203,8 @@ __global__ void k_fill_pads(DevParams P, int QM, R* f) {
   int x = p < NGHOST ? p - NGHOST : P.nx + (p - NGHOST);
   int src = map_index(x, P.nx, P.bc[0], P.bc[1]);
   long long q = row / P.ny, j = row % P.ny;
-  R* base = f + q * P.plane + j * P.pitch + XPAD;
-  base[x] = base[src];
+  const long long base = q * P.plane + j * P.pitch + XPAD, nf = (long long)QM * P.plane;
+  f[chk(base + x, nf, &ctl->status)] = f[chk(base + src, nf, &ctl->status)];
 }
 
 template <class R>
@@ -226,7 +227,7 @@ __global__ void k_halo_rows(DevParams P, int QM, R* const* buf, const Ctl* ctl, 
   if (idx >= per * QM) return;
   R* f = buf[ctl->parity[slot]];
   const long long q = idx / per, r = idx % per;
-  R* a = f + q * P.plane + (long long)row * P.pitch + r;
+  R* a = f + chk(q * P.plane + (long long)row * P.pitch + r, (long long)QM * P.plane, (unsigned int*)&ctl->status);
   if (to_rows)
     rows[idx] = *a;
   else

@@ -25,6 +25,7 @@ __device__ __forceinline__ const R* state_in(R* const* buf, const Ctl* ctl, int 
 // at the wrapped / clamped index.
 template <int SYS, int D, class R>
 __global__ void k_moments_ext(DevParams P, R* const* buf, const Ctl* ctl, int slot, ExtGeom G, R* Ue) {
+  unsigned int* const stc = (unsigned int*)&ctl->status;  // index guards (bounds-checked builds)
   constexpr int M = Fields<SYS, D>::M, Q = Fields<SYS, D>::Q;
   long long n = (long long)G.ex * G.ey;
   long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -40,7 +41,7 @@ __global__ void k_moments_ext(DevParams P, R* const* buf, const Ctl* ctl, int sl
   for (int c = 0; c < M; c++) {
     R s = R(0);
 #pragma unroll
-    for (int k = 0; k < Q; k++) s += f[(long long)(k * M + c) * P.plane + off];
+    for (int k = 0; k < Q; k++) s += f[chk((long long)(k * M + c) * P.plane + off, (long long)Q * M * P.plane, stc)];
     U[c] = s;
   }
   if (P.has_special_bc) {
@@ -59,12 +60,13 @@ __global__ void k_moments_ext(DevParams P, R* const* buf, const Ctl* ctl, int sl
     }
   }
 #pragma unroll
-  for (int c = 0; c < M; c++) Ue[(long long)c * n + e] = U[c];
+  for (int c = 0; c < M; c++) Ue[chk((long long)c * n + e, (long long)M * n, stc)] = U[c];
 }
 
 // K1: nu = sum_j sum_r theta^{(r,j)} (Eq. 2.10/2.14) one layer inside the extension
 template <int SYS, int D, class R>
 __global__ void k_indicator(DevParams P, const Ctl* ctl, int slot, ExtGeom G, const R* Ue, R* nu) {
+  unsigned int* const stc = (unsigned int*)&ctl->status;  // index guards (bounds-checked builds)
   constexpr int M = Fields<SYS, D>::M;
   long long n = (long long)G.ex * G.ey;
   long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -76,7 +78,7 @@ __global__ void k_indicator(DevParams P, const Ctl* ctl, int slot, ExtGeom G, co
   const Phys<R> K = make_phys<R>(P);
   R U0[M], dm[M], dp[M];
 #pragma unroll
-  for (int c = 0; c < M; c++) U0[c] = Ue[(long long)c * n + e];
+  for (int c = 0; c < M; c++) U0[c] = Ue[chk((long long)c * n + e, (long long)M * n, stc)];
   Prim<R> w = primitives<SYS, D, R>(K, U0);
   R s = R(0);
 #pragma unroll
@@ -84,17 +86,18 @@ __global__ void k_indicator(DevParams P, const Ctl* ctl, int slot, ExtGeom G, co
     long long step = dir == 0 ? 1 : G.ex;
 #pragma unroll
     for (int c = 0; c < M; c++) {
-      dm[c] = U0[c] - Ue[(long long)c * n + e - step];
-      dp[c] = Ue[(long long)c * n + e + step] - U0[c];
+      dm[c] = U0[c] - Ue[chk((long long)c * n + e - step, (long long)M * n, stc)];
+      dp[c] = Ue[chk((long long)c * n + e + step, (long long)M * n, stc)] - U0[c];
     }
     s += theta_sum<SYS, D, R>(K, w, dir, dm, dp);
   }
-  nu[e] = s;
+  nu[chk(e, n, stc)] = s;
 }
 
 // K2: omega = 1 + 1/(1 + nu~), nu~ the sum over the 3^d box (Eq. 2.11/2.15, 2.12/2.16)
 template <int D, class R>
 __global__ void k_omega(DevParams P, const Ctl* ctl, int slot, ExtGeom G, const R* nu, R* om) {
+  unsigned int* const stc = (unsigned int*)&ctl->status;  // index guards (bounds-checked builds)
   long long n = (long long)G.ex * G.ey;
   long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= n) return;
@@ -108,7 +111,7 @@ __global__ void k_omega(DevParams P, const Ctl* ctl, int slot, ExtGeom G, const 
   } else {
     R s = R(0);
     for (int bj = (D == 2 ? -1 : 0); bj <= (D == 2 ? 1 : 0); bj++)
-      for (int bi = -1; bi <= 1; bi++) s += nu[e + (long long)bj * G.ex + bi];
+      for (int bi = -1; bi <= 1; bi++) s += nu[chk(e + (long long)bj * G.ex + bi, n, stc)];
     w = R(1) + fdiv(R(1), R(1) + s);
   }
   if (P.sponge_width > 0.0) {  // blended toward 1 over the sponge (x-lo)
@@ -117,7 +120,7 @@ __global__ void k_omega(DevParams P, const Ctl* ctl, int slot, ExtGeom G, const 
     const double keep = x <= 0.0 ? 0.0 : (x >= 1.0 ? 1.0 : 1.0 - 0.5 * (1.0 + cos(3.14159265358979323846 * x)));
     w = R(1) + (w - R(1)) * R(keep);
   }
-  om[e] = w;
+  om[chk(e, n, stc)] = w;
 }
 
 // velocity e_k of the DdQ(2d+1) lattice: e_0 = 0, e_j = unit j, e_{j+d} = -e_j
@@ -194,6 +197,7 @@ template <int SYS, int D, class R>
 __global__ void k_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot, ExtGeom G, const R* Ue,
                                  const R* om, double* partials) {
   constexpr int M = Fields<SYS, D>::M, Q = Fields<SYS, D>::Q;
+  unsigned int* const stc = &ctl->status;  // index guards (bounds-checked builds)
   const StepCoef cf = step_coef<D>(P, ctl, slot);
   if (!cf.active) {
     if (blockIdx.x == 0 && threadIdx.x == 0) advance_ctl<D>(ctl, slot, cf);
@@ -223,7 +227,7 @@ __global__ void k_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
       long long e = G.idx(ej, ei);
       R U[M], S[M];
 #pragma unroll
-      for (int c = 0; c < M; c++) U[c] = Ue[(long long)c * next + e];
+      for (int c = 0; c < M; c++) U[c] = Ue[chk((long long)c * next + e, (long long)M * next, stc)];
       int si = map_index(ei - GH, P.nx, P.bc[0], P.bc[1]);
       int sj = D == 2 ? map_index(ej - G.gy, P.ny, P.bc[2], P.bc[3]) : 0;
       Prim<R> w = primitives<SYS, D, R>(K, U);
@@ -240,12 +244,12 @@ __global__ void k_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
         for (int c = 0; c < M; c++) feq[c] = (al[jd] * U[c] + sg * F[c]) * inv2l;
       }
       source<SYS, D, R>(K, U, K.xb + R(si) * K.dx, K.yb + R(sj) * K.dx, S);
-      R wk = om[e];
+      R wk = om[chk(e, next, stc)];
       R akk = k == 0 ? ak[0] : ak[1 + (k - 1) % D];
       long long off = cell(P, si, sj);
 #pragma unroll
       for (int c = 0; c < M; c++) {
-        R fk = f[(long long)(k * M + c) * P.plane + off];
+        R fk = f[chk((long long)(k * M + c) * P.plane + off, (long long)Q * M * P.plane, stc)];
         Fk[k][c] = fk - wk * (fk - feq[c]) + hdt * akk * S[c];
       }
     }
@@ -270,7 +274,7 @@ __global__ void k_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
 #pragma unroll
       for (int c = 0; c < M; c++) {
         R v = Fk[k][c] + hdt * akk * S[c];
-        fo[(long long)(k * M + c) * P.plane + off] = v;
+        fo[chk((long long)(k * M + c) * P.plane + off, (long long)Q * M * P.plane, stc)] = v;
         Us[c] += v;  // the moments the next step will see (Eq. 2.3, k = 0..Q-1)
       }
     }

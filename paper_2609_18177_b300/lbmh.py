@@ -14,9 +14,11 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_lbmh.so")
+# LBMH_LIBRARY=checked selects the bounds-checked build (debug runs of the tests)
+LIB_PATH = os.path.join(HERE, "_lbmh_checked.so" if os.environ.get("LBMH_LIBRARY") == "checked" else "_lbmh.so")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+ERR_BOUNDS = -7  # bounds-checked build only: an index left its array
 KERNEL_AUTO, KERNEL_FUSED, KERNEL_UNFUSED = 0, 1, 2
 FP64, FP32 = 0, 1
 

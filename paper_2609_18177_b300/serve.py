@@ -63,6 +63,49 @@ def poisson_trace(nreq, rate, seed=0, n_range=(128, 2048), steps_range=(200, 500
     return out
 
 
+class InputPrefetcher:
+    """Builds the requests' (problem, U0) on host threads ahead of their
+    arrival order, so that the serving loop does not stop to build inputs
+    (numpy releases the GIL in its array loops).  At most `lookahead` inputs are
+    held at a time; an input is dropped once the server has taken it.  Usable
+    as the server's `inputs` mapping."""
+
+    def __init__(self, trace, make=None, workers=4, lookahead=24):
+        from concurrent.futures import ThreadPoolExecutor
+        self.order = [r for r in sorted(trace, key=lambda r: r.arrival)]
+        self.make = make or make_problem
+        self.pool = ThreadPoolExecutor(max_workers=workers)
+        self.lookahead = lookahead
+        self.futures = {}
+        self.next = 0
+        self._fill()
+
+    def _fill(self):
+        while self.next < len(self.order) and len(self.futures) < self.lookahead:
+            req = self.order[self.next]
+            self.futures[req.rid] = self.pool.submit(self.make, req)
+            self.next += 1
+
+    def __bool__(self):
+        return True
+
+    def __contains__(self, rid):
+        return True
+
+    def __getitem__(self, rid):
+        fut = self.futures.pop(rid, None)
+        if fut is None:  # taken out of arrival order, or beyond the window
+            req = next(r for r in self.order if r.rid == rid)
+            out = self.make(req)
+        else:
+            out = fut.result()
+        self._fill()
+        return out
+
+    def close(self):
+        self.pool.shutdown(wait=False, cancel_futures=True)
+
+
 @dataclass
 class Result:
     rid: int
@@ -86,7 +129,9 @@ class Server:
 
     def __init__(self, capacity_bytes=8 << 30, max_instances=256, chunk=32, autotune=False, keep_results=False,
                  batches=None, new_event=None):
-        """`batches` (one object per system with the lbmh.Batch methods add,
+        """keep_results: True keeps every result's moments, a set keeps those of
+        the request ids in it, False none.
+        `batches` (one object per system with the lbmh.Batch methods add,
         step, poll, moments, remove, autotune) and `new_event` (a factory of
         objects with record(stream) and query()) replace the CUDA batches and
         events, e.g. to exercise the scheduling on a host without a GPU."""
@@ -162,8 +207,9 @@ class Server:
                             fin = time.perf_counter() - t0
                             self.batches[k].remove(slot)
                             node_steps += req.n * req.n * int(steps[slot])
+                            keep = self.keep_results is True or (self.keep_results and req.rid in self.keep_results)
                             results.append(Result(req.rid, k, req.n, int(steps[slot]), req.arrival, adm, fin,
-                                                  U if self.keep_results else None, bool(done[slot] != 1)))
+                                                  U if keep else None, bool(done[slot] != 1)))
                 # the batch is idle: admit (first fit by footprint, in arrival order)
                 kept = []
                 for req in queue[k]:

@@ -147,3 +147,27 @@ def test_withdrawn_requests_leave_queue_and_batch():
     assert by[2].cancelled and 0 < by[2].steps < 3200 and by[2].steps % 32 == 0 and by[2].U is None
     assert by[2].finished >= 0.2
     assert all(not b.live for b in batches.values())
+
+
+def test_input_prefetcher_builds_inputs_ahead_in_arrival_order():
+    """The prefetcher hands the server each request's input once, built on
+    host threads in arrival order, holding at most `lookahead` at a time."""
+    import threading
+    from paper_2609_18177_b300 import serve as S
+    trace = S.poisson_trace(12, rate=50.0, seed=3)
+    built = []
+    lock = threading.Lock()
+
+    def make(req):
+        with lock:
+            built.append(req.rid)
+        return ("pb", req.rid)
+
+    feed = S.InputPrefetcher(trace, make=make, workers=2, lookahead=4)
+    assert len(feed.futures) <= 4
+    for req in sorted(trace, key=lambda r: r.arrival):
+        assert req.rid in feed
+        assert feed[req.rid] == ("pb", req.rid)
+        assert len(feed.futures) <= 4
+    feed.close()
+    assert sorted(built) == sorted(r.rid for r in trace) and len(built) == len(trace)
