@@ -48,7 +48,6 @@ inline int validate(const lbmh_problem* p, std::string& why) {
     double dx = (p->x1 - p->x0) / p->nx, dz = (p->z1 - p->z0) / p->nz;
     if (!(fabs(dx - dz) <= 1e-12 * dx)) { why = "3D mesh must satisfy dx == dy == dz"; return LBMH_ERR_INVALID_ARG; }
     if (p->sponge_width != 0.0) { why = "no sponge on 3D lattices"; return LBMH_ERR_UNSUPPORTED; }
-    if (p->kernel == LBMH_KERNEL_FUSED) { why = "3D lattices run on the four-kernel path"; return LBMH_ERR_UNSUPPORTED; }
   }
   if (!(p->x1 > p->x0)) { why = "x1 must exceed x0"; return LBMH_ERR_INVALID_ARG; }
   for (int s = 0; s < 2 * p->dim; s++)

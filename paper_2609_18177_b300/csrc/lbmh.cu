@@ -18,6 +18,7 @@
 #include "physics.cuh"
 #include "state.cuh"
 #include "lbm3d.cuh"
+#include "lbm3d_fused.cuh"
 #include "unfused.cuh"
 
 using namespace lbmh;
@@ -229,6 +230,16 @@ struct Impl3 {
     } else {
       k3_moments_ext<SYS, R><<<ge, kBlock3, 0, h->stream>>>(P, buf, h->ctl, slot, G, (R*)h->Ue);
     }
+    if (h->kernel == LBMH_KERNEL_FUSED) {  // indicator, omega, collision and streaming in one pass
+      const int zc = h->fp.band;
+      const dim3 gf = grid3_fused(P.nx, P.ny3, P.nz3, zc);
+      k3_fused<SYS, R><<<gf, kThreads3F, h->fp.smem, h->stream>>>(P, buf, h->ctl, slot, G, (R*)h->Ue, h->partials, zc);
+      h->u3_valid = true;
+      h->nblocks = (int)(gf.x * gf.y * gf.z) * (kThreads3F / 32);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(h, e, "3D fused step launch");
+      return LBMH_OK;
+    }
     k3_indicator<SYS, R><<<ge, kBlock3, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->Ue, (R*)h->nue);
     k3_omega<R><<<grid3_omega(G.ex, G.ey, G.ez), kBlock3, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->nue,
                                                                           (R*)h->ome);
@@ -289,11 +300,29 @@ struct Impl3 {
     return fail(h, LBMH_ERR_UNSUPPORTED, "the omega diagnostic is not provided for 3D lattices");
   }
 
-  static int setup_fused(lbmh_handle*) { return -1; }
+  // the fused step's shared memory, z chunk (planes a block marches; at least
+  // 8; LBMH_3D_ZCHUNK overrides it for tuning runs) and partial-sum slots
+  static int setup_fused(lbmh_handle* h) {
+    using L = Smem3F<M, R>;
+    auto kern = k3_fused<SYS, R>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::total) != cudaSuccess)
+      return -1;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads3F, L::total) != cudaSuccess || per_sm < 1)
+      return -1;
+    int zc = 32;
+    const char* e = getenv("LBMH_3D_ZCHUNK");
+    if (e && atoi(e) >= 8) zc = atoi(e);
+    h->fp.smem = (int)L::total;
+    h->fp.band = zc;
+    const dim3 g = grid3_fused(h->P.nx, h->P.ny3, h->P.nz3, zc);
+    h->fp.blocks = (int)(g.x * g.y * g.z) * (kThreads3F / 32);
+    return 0;
+  }
 
   static const Ops* ops() {
     static const Ops o = {launch_step, launch_unfused_diag, init, moments, get_f, set_f, omega_extract, setup_fused,
-                          false};
+                          true};
     return &o;
   }
 };
@@ -363,8 +392,11 @@ int ensure_scratch(lbmh_handle* h) {
   if (h->Ue) return LBMH_OK;
   long long next = (long long)h->G.ex * h->G.ey * h->G.ez;
   size_t b1 = (size_t)next * h->m * h->elem * (h->dim == 3 ? 2 : 1), b2 = (size_t)next * h->elem;
-  if (cudaMalloc(&h->Ue, b1) != cudaSuccess || cudaMalloc(&h->nue, b2) != cudaSuccess ||
-      cudaMalloc(&h->ome, b2) != cudaSuccess) {
+  // the fused 3D step keeps nu and omega on chip: only the two U copies
+  const bool u_only = h->dim == 3 && h->kernel == LBMH_KERNEL_FUSED;
+  if (u_only) b2 = 0;
+  if (cudaMalloc(&h->Ue, b1) != cudaSuccess || (!u_only && cudaMalloc(&h->nue, b2) != cudaSuccess) ||
+      (!u_only && cudaMalloc(&h->ome, b2) != cudaSuccess)) {
     cudaGetLastError();
     cudaFree(h->Ue);
     cudaFree(h->nue);
@@ -520,7 +552,9 @@ int create_impl(const lbmh_problem* p, const SlabGeom* sg, lbmh_handle** out) {
     P.row0 = sg->row0;
   }
 
-  bool want_fused = p->kernel != LBMH_KERNEL_UNFUSED;
+  // 3D: the fused z-marching kernel only when asked for (measured slower than
+  // the four-kernel path at 256^3: 1.80 against 1.64 ms per step)
+  bool want_fused = p->dim == 3 ? p->kernel == LBMH_KERNEL_FUSED : p->kernel != LBMH_KERNEL_UNFUSED;
   if (p->kernel == LBMH_KERNEL_FUSED && !h->ops->has_fused) {
     delete h;
     return fail(nullptr, LBMH_ERR_UNSUPPORTED, "no fused kernel for this system/dimension/precision");
@@ -568,7 +602,7 @@ int create_impl(const lbmh_problem* p, const SlabGeom* sg, lbmh_handle** out) {
   ok = ok && alloc((void**)&h->dbuf, 2 * sizeof(void*)) &&
        alloc((void**)&h->partials, (size_t)h->max_blocks * h->m * sizeof(double)) &&
        alloc((void**)&h->ctl, sizeof(Ctl));
-  if (ok && h->kernel == LBMH_KERNEL_UNFUSED && ensure_scratch(h) != LBMH_OK) ok = false;
+  if (ok && (h->kernel == LBMH_KERNEL_UNFUSED || h->dim == 3) && ensure_scratch(h) != LBMH_OK) ok = false;
   if (!ok) {
     free_handle(h);
     return fail(nullptr, LBMH_ERR_OOM, "device allocation failed");

@@ -63,12 +63,20 @@ def poisson_trace(nreq, rate, seed=0, n_range=(128, 2048), steps_range=(200, 500
     return out
 
 
+def request_footprint(req: Request) -> int:
+    """Device bytes the request's lattice takes in its system's batch arena
+    (from the problem's geometry alone: no input is built)."""
+    pb = W.Problem(system=KIND_SYSTEM[req.kind], dim=2, nx=req.n, ny=req.n)
+    return lbmh.Batch.footprint(pb, lbmh.FP32)
+
+
 class InputPrefetcher:
     """Builds the requests' (problem, U0) on host threads ahead of their
     arrival order, so that the serving loop does not stop to build inputs
     (numpy releases the GIL in its array loops).  At most `lookahead` inputs are
-    held at a time; an input is dropped once the server has taken it.  Usable
-    as the server's `inputs` mapping."""
+    held at a time; an input is kept until the server releases it after the
+    admission (a request that waits for room is not built twice).  Usable as
+    the server's `inputs` mapping."""
 
     def __init__(self, trace, make=None, workers=4, lookahead=24):
         from concurrent.futures import ThreadPoolExecutor
@@ -93,14 +101,19 @@ class InputPrefetcher:
         return True
 
     def __getitem__(self, rid):
-        fut = self.futures.pop(rid, None)
-        if fut is None:  # taken out of arrival order, or beyond the window
+        fut = self.futures.get(rid)
+        if fut is None:  # beyond the window: built now, and kept until released
+            from concurrent.futures import Future
             req = next(r for r in self.order if r.rid == rid)
-            out = self.make(req)
-        else:
-            out = fut.result()
+            fut = Future()
+            fut.set_result(self.make(req))
+            self.futures[rid] = fut
+        return fut.result()
+
+    def release(self, rid):
+        """The server has admitted the request: drop its input, build the next."""
+        self.futures.pop(rid, None)
         self._fill()
-        return out
 
     def close(self):
         self.pool.shutdown(wait=False, cancel_futures=True)
@@ -155,6 +168,14 @@ class Server:
         for b in self.batches.values():
             b.close()
 
+    def _free_bytes(self, k):
+        """Free arena bytes of system k's batch (None for batches without an arena)."""
+        info = getattr(self.batches[k], "info", None)
+        if info is None:
+            return None
+        d = info()
+        return d["capacity_bytes"] - d["used_bytes"]
+
     def run(self, trace: List[Request], inputs: Optional[Dict[int, tuple]] = None, max_seconds=1e9):
         """Serve `trace` in real time; `inputs` may hold pre-built (problem, U0)
         per request id.  Returns the list of results and summary statistics.
@@ -170,6 +191,7 @@ class Server:
         live: Dict[str, Dict[int, tuple]] = {k: {} for k in KINDS}  # slot -> (request, admitted time)
         inflight: Dict[str, Optional[object]] = {k: None for k in KINDS}  # event of the launched chunk
         results: List[Result] = []
+        footprints: Dict[int, int] = {}
         node_steps = 0
         deferred = set()  # requests refused admission at least once (arena full)
         t0 = time.perf_counter()
@@ -210,9 +232,18 @@ class Server:
                             keep = self.keep_results is True or (self.keep_results and req.rid in self.keep_results)
                             results.append(Result(req.rid, k, req.n, int(steps[slot]), req.arrival, adm, fin,
                                                   U if keep else None, bool(done[slot] != 1)))
-                # the batch is idle: admit (first fit by footprint, in arrival order)
+                # the batch is idle: admit (first fit by footprint, in arrival order);
+                # a request whose lattice cannot fit in the free space is passed
+                # over before its input is built
                 kept = []
+                free = self._free_bytes(k)
                 for req in queue[k]:
+                    if free is not None:
+                        need = footprints.setdefault(req.rid, request_footprint(req))
+                        if need > free:
+                            kept.append(req)
+                            deferred.add(req.rid)
+                            continue
                     pb, U0 = inputs[req.rid] if inputs and req.rid in inputs else make_problem(req)
                     slot = self.batches[k].add(pb, U0, max_steps=req.steps)
                     if slot is None:
@@ -221,6 +252,10 @@ class Server:
                     else:
                         live[k][slot] = (req, time.perf_counter() - t0)
                         progressed = True
+                        if free is not None:
+                            free -= footprints[req.rid]
+                        if hasattr(inputs, "release"):
+                            inputs.release(req.rid)
                 queue[k] = kept
                 if live[k]:
                     if self.autotune and k not in self.tuned and len(live[k]) >= 2:

@@ -102,12 +102,6 @@ def test_create_rejects_invalid_problems_before_touching_the_device(lib, bad, co
     assert rc == code and not h.value and msg
 
 
-def test_3d_lattices_have_no_fused_kernel(lib):
-    pb = W.Problem(system=W.EULER, dim=3, nx=8, ny=8, nz=8)
-    rc, h, msg = _create(lib, pb, kernel=lbmh.KERNEL_FUSED)
-    assert rc == lbmh.ERR_UNSUPPORTED and not h.value and msg
-
-
 def test_null_arguments(lib):
     assert lib.lbmh_create(None, None) == lbmh.ERR_INVALID_ARG
     assert lib.lbmh_step(None, 1) == lbmh.ERR_INVALID_ARG

@@ -48,13 +48,18 @@ CASES = [(s, bc) for s in (W.ADVECTION, W.EULER, W.REACTIVE) for bc in (W.PERIOD
 IDS = [f"{W.SYSTEM_NAMES[s]}-{'per' if bc == 0 else 'out'}" for s, bc in CASES]
 
 
+KERNELS = [(lbmh.KERNEL_FUSED, "fused"), (lbmh.KERNEL_AUTO, "four-kernel")]
+
+
+@pytest.mark.parametrize("kernel", [k for k, _ in KERNELS], ids=[n for _, n in KERNELS])
 @pytest.mark.parametrize("precision", [lbmh.FP64, lbmh.FP32], ids=["fp64", "fp32"])
 @pytest.mark.parametrize("system,bc", CASES, ids=IDS)
-def test_3d_matches_oracle(system, bc, precision):
+def test_3d_matches_oracle(system, bc, precision, kernel):
     pb, U0 = case(system, bc)
     pb = pb.with_(precision=precision)
     r = oracle.Run(pb, U0)
-    s = lbmh.Solver(pb, precision=precision).set_state(U0)
+    s = lbmh.Solver(pb, precision=precision, kernel=kernel).set_state(U0)
+    assert s.info()["kernel"] == (lbmh.KERNEL_FUSED if kernel == lbmh.KERNEL_FUSED else lbmh.KERNEL_UNFUSED)
     for n in range(4):
         r.step(5)
         s.step(5)
@@ -101,16 +106,17 @@ def test_3d_unsupported_combinations():
     s.close()
 
 
+@pytest.mark.parametrize("kernel", [k for k, _ in KERNELS], ids=[n for _, n in KERNELS])
 @pytest.mark.parametrize("precision", [lbmh.FP64, lbmh.FP32], ids=["fp64", "fp32"])
-def test_3d_graph_replay_and_set_f_keep_moments_consistent(precision):
+def test_3d_graph_replay_and_set_f_keep_moments_consistent(precision, kernel):
     """A step normally reuses the moments U^{n+1} that the previous collision
     wrote and refills only the ghost layers; the distributions set from
     outside (set_f) and the first step of every graph replay take the full
     moments pass.  Graph replays, single steps and the oracle must agree."""
     pb, U0 = case(W.REACTIVE, W.OUTFLOW)
     pb = pb.with_(precision=precision)
-    a = lbmh.Solver(pb, precision=precision).set_state(U0).step(60)  # 0 single, 2 graph replays, 12 single
-    b = lbmh.Solver(pb, precision=precision).set_state(U0)
+    a = lbmh.Solver(pb, precision=precision, kernel=kernel).set_state(U0).step(60)  # 0 single, 2 graph replays, 12 single
+    b = lbmh.Solver(pb, precision=precision, kernel=kernel).set_state(U0)
     for _ in range(60):
         b.step(1)
     assert np.array_equal(a.get_f(), b.get_f())
@@ -121,7 +127,7 @@ def test_3d_graph_replay_and_set_f_keep_moments_consistent(precision):
     f_other = lbmh.Solver(pb, precision=precision).set_state(W.random_state(pb, seed=7)).step(3).get_f()
     a.set_f(f_other, 0.0, 0)
     a.step(50)
-    c = lbmh.Solver(pb, precision=precision).set_f(f_other, 0.0, 0)
+    c = lbmh.Solver(pb, precision=precision, kernel=kernel).set_f(f_other, 0.0, 0)
     for _ in range(50):
         c.step(1)
     assert np.array_equal(a.get_f(), c.get_f())
@@ -130,16 +136,16 @@ def test_3d_graph_replay_and_set_f_keep_moments_consistent(precision):
 
 
 def test_3d_int_and_64bit_offsets_give_the_same_bits(monkeypatch):
-    """The collision kernel indexes with int offsets where every offset of the
-    lattice fits (up to ~390^3) and with 64-bit offsets beyond; the two
-    instances do the same arithmetic.  LBMH_3D_INDEX64=1 forces the 64-bit
-    one on a small lattice."""
+    """The four-kernel path's collision kernel indexes with int offsets where
+    every offset of the lattice fits (up to ~390^3) and with 64-bit offsets
+    beyond; the two instances do the same arithmetic.  LBMH_3D_INDEX64=1
+    forces the 64-bit one on a small lattice."""
     pb, U0 = case(W.REACTIVE, W.OUTFLOW)
     for prec in (lbmh.FP64, lbmh.FP32):
         monkeypatch.delenv("LBMH_3D_INDEX64", raising=False)
-        a = lbmh.Solver(pb, precision=prec).set_state(U0).step(12)
+        a = lbmh.Solver(pb, precision=prec, kernel=lbmh.KERNEL_UNFUSED).set_state(U0).step(12)
         monkeypatch.setenv("LBMH_3D_INDEX64", "1")
-        b = lbmh.Solver(pb, precision=prec).set_state(U0).step(12)
+        b = lbmh.Solver(pb, precision=prec, kernel=lbmh.KERNEL_UNFUSED).set_state(U0).step(12)
         assert np.array_equal(a.get_f(), b.get_f())
         a.close()
         b.close()
@@ -162,4 +168,31 @@ def test_3d_speed_bounds_reported(precision):
     got = [inf["abar"][0], inf["abar"][1], inf["abar_z"]]
     tol = 1e-12 if precision == lbmh.FP64 else 1e-5
     assert np.allclose(got, want, rtol=tol, atol=0.0), (got, want)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [lbmh.FP64, lbmh.FP32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("bc", [W.PERIODIC, W.OUTFLOW], ids=["per", "out"])
+def test_3d_fused_over_several_tiles_and_chunks(bc, precision, monkeypatch):
+    """A lattice of several 32 x 8 tiles with ragged edges in x and y, and z
+    chunks of 8 planes with a ragged last chunk (the fused kernel marches each
+    chunk with a fill of its own), against the oracle."""
+    monkeypatch.setenv("LBMH_3D_ZCHUNK", "8")
+    pb, U0 = case(W.EULER, bc, nx=70, ny=19, nz=29, seed=5)
+    pb = pb.with_(precision=precision)
+    s = lbmh.Solver(pb, precision=precision, kernel=lbmh.KERNEL_FUSED).set_state(U0)
+    monkeypatch.delenv("LBMH_3D_ZCHUNK")
+    r = oracle.Run(pb, U0).step(6)
+    s.step(6)
+    Ug, Uo = s.moments(), r.moments()
+    if precision == lbmh.FP64:
+        assert np.all(rel_max(Ug, Uo) <= 1e-12), rel_max(Ug, Uo)
+    else:
+        assert np.all(rel_l1(Ug, Uo) <= 2e-5), rel_l1(Ug, Uo)
+        assert np.all(rel_max(Ug, Uo) <= 5e-4), rel_max(Ug, Uo)
+    info = s.info()
+    # the FP64 sums over the warps' partial slots: conservation under periodic sides
+    if bc == W.PERIODIC:
+        tot0 = U0.reshape(pb.nfields, -1).sum(axis=1)
+        assert np.allclose(info["sum_U"], tot0, rtol=1e-10 if precision == lbmh.FP64 else 1e-5)
     s.close()

@@ -168,6 +168,8 @@ def test_input_prefetcher_builds_inputs_ahead_in_arrival_order():
     for req in sorted(trace, key=lambda r: r.arrival):
         assert req.rid in feed
         assert feed[req.rid] == ("pb", req.rid)
+        assert feed[req.rid] == ("pb", req.rid)  # asked again while it waits for room: not rebuilt
+        feed.release(req.rid)
         assert len(feed.futures) <= 4
     feed.close()
     assert sorted(built) == sorted(r.rid for r in trace) and len(built) == len(trace)
