@@ -122,3 +122,16 @@ def test_contract_norm_torch_matches_numpy():
     b = A.contract_l1_torch(torch.from_numpy(got), torch.from_numpy(ref), A.EULER, 2)
     for k in a:
         assert b[k] == pytest.approx(a[k], rel=1e-12)
+
+
+def test_contract_norm_measures_unburnt_gas_against_the_density():
+    """rho*Y of a burnt-out state is ~0: its error is taken relative to the
+    density, not to its own vanishing sum."""
+    from paper_2609_18177_b300 import accuracy as A
+    ref = np.ones((5, 4, 4))
+    ref[4] = 1e-300              # burnt: rho*Y decayed towards zero
+    got = ref.copy()
+    got[4] = 1e-38               # an FP32 run stops at its smallest normal numbers
+    e = A.contract_l1(got, ref, A.REACTIVE, 2)
+    assert e["rhoY"] == pytest.approx(1e-38)
+    assert e["max"] == pytest.approx(1e-38)
