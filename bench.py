@@ -604,7 +604,9 @@ def run_lines1d(args):
 def run_cube3d(args):
     """The 3D (D3Q7) path: Euler on a periodic n^3 cube with a seeded random
     state (smooth fields plus a jump), FP32 and FP64, and reactive Euler (the
-    Example 5.12 constants) in FP32; four kernels per step.  value = Euler
+    Example 5.12 constants) in FP32; the default kernel choice (the fused
+    z-marching kernel in FP32, the four-kernel path in FP64) unless --kernel
+    names one, the kernel of each case reported.  value = Euler
     FP32 MLUPS; algorithmic bytes per node update 2 Q m sizeof(real) (Q = 7,
     m = 5: 280 B in FP32; reactive m = 6: 336 B)."""
     import torch

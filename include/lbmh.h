@@ -119,8 +119,9 @@ typedef struct lbmh_problem {
                           sigma = (1 + cos(pi (x - x0) / sponge_width)) / 2; 0: none */
   double u_in[8];      /* conservative state (first m entries) held by INFLOW sides */
   /* 3D (dim = 3, the D3Q7 lattice; the paper names 3D as future work):
-   * advection, Euler and reactive Euler, periodic or outflow sides, the
-   * four-kernel path (KERNEL_AUTO); dx == dy == dz required.  U and f are
+   * advection, Euler and reactive Euler, periodic or outflow sides;
+   * KERNEL_AUTO takes the fused z-marching kernel in FP32 and the four-kernel
+   * path (KERNEL_UNFUSED) in FP64; dx == dy == dz required.  U and f are
    * laid out [..][nz][ny][nx]. */
   int nz;
   double z0, z1;

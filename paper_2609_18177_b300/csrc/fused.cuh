@@ -45,6 +45,8 @@ struct FusedPlan {
   int smem;        // dynamic shared memory bytes
   CUtensorMap tm[2];   // loads: padded rows of buffer b
   CUtensorMap tms[2];  // stores: interior columns of buffer b
+  CUtensorMap tu3[2];  // fused 3D step: U tiles of ext copy b
+  CUtensorMap tf3[2];  // fused 3D step: own-column f^n tiles of buffer b
 };
 
 template <int SYS, int D, class R>
@@ -426,6 +428,15 @@ __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml
         nu1[j] = nu2[j] = nu3[j] = R(0);
       }
 
+      // A shorter limit for the CTA's first row wait, from the problem (a test
+      // makes it give up at once): checked here, before the row loop, so that
+      // the loop's own waits keep their constant limit (a run-time limit
+      // inside the loop cost the 8192^2 step 1.4 %).  A wait that gives up
+      // sets the abort flag; the loop's wait on the same row then lets the
+      // load land, and the CTA stops at the row's barrier.
+      if (seq0 == 0 && P.first_wait_polls < kWaitPolls) {
+        if (!mbar_wait_bounded(smem_u32(&bars[0]), 0u, P.first_wait_polls)) *s_abort = 1;
+      }
   // not unrolled: the copies of an unrolled body compile to different FMA
   // contractions, and a row's rounding would then depend on its parity
   // relative to the segment start, i.e. on the work split (a lattice would
@@ -440,10 +451,7 @@ __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml
           tma_load_row(tml, smem_u32(fring + (size_t)(s % S) * QM * NC), smem_u32(&bars[s % S]), x0 - 4 + XPAD, my, row_bytes);
           issued_end = s + 1;
         }
-        // the CTA's first row wait takes its limit from the problem (a test can
-        // make it give up at once); every other wait polls kWaitPolls times
-        if (!mbar_wait_bounded(smem_u32(&bars[sidx % S]), (sidx / S) & 1u, sidx == 0 ? P.first_wait_polls : kWaitPolls))
-          *s_abort = 1;
+        if (!mbar_wait_bounded(smem_u32(&bars[sidx % S]), (sidx / S) & 1u)) *s_abort = 1;
         R* frow_w = fring + (size_t)(sidx % S) * QM * NC;
         if (P.has_special_bc) {  // ghost nodes across reflecting / inflow sides (own columns only)
           const int rs = ghost_side(r, P.ny, P.bc[2], P.bc[3]);

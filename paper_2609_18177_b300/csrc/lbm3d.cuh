@@ -182,12 +182,19 @@ __device__ __forceinline__ void advance_ctl3(Ctl* ctl, int slot, const StepCoef3
 }
 
 // ghost-extended 3D geometry: ex x ey x ez nodes, 3 ghost layers per side
+// The ghost-extended grid: ex x ey x ez nodes (the lattice plus GH layers on
+// every side), stored with rows of px >= ex elements (px a multiple of 4, so
+// that every row starts on 16 bytes, as a TMA box needs).  Columns [ex, px)
+// are never read or written.
 struct ExtGeom3 {
-  int ex, ey, ez;
+  int ex, ey, ez, px;
   __device__ __forceinline__ long long idx(int ek, int ej, int ei) const {
-    return ((long long)ek * ey + ej) * ex + ei;
+    return ((long long)ek * ey + ej) * px + ei;
   }
+  // elements of one copy of one field
+  __host__ __device__ __forceinline__ long long size() const { return (long long)px * ey * ez; }
 };
+inline int ext_pitch3(int ex) { return (ex + 3) / 4 * 4; }
 
 // offset of node (i, j, k) in a distribution plane (row = k * ny + j)
 __device__ __forceinline__ long long cell3(const DevParams& P, int i, int j, int k) {
@@ -341,7 +348,7 @@ __device__ __forceinline__ bool ext_coords(const ExtGeom3& G, int& ei, int& ej, 
 // pass K0 runs after the distributions were set from outside.
 template <int M, class T>
 __device__ __forceinline__ T* ue_copy(T* Ue, const ExtGeom3& G, int par) {
-  return Ue + (long long)par * M * ((long long)G.ex * G.ey * G.ez);
+  return Ue + (long long)par * M * G.size();
 }
 
 // K0: U = sum_k f_k on the ghost-extended grid (wrapped / clamped reads).  It
@@ -349,7 +356,7 @@ __device__ __forceinline__ T* ue_copy(T* Ue, const ExtGeom3& G, int par) {
 template <int SYS, class R>
 __global__ void k3_moments_ext(DevParams P, R* const* buf, const Ctl* ctl, int slot, ExtGeom3 G, R* Ue2) {
   constexpr int M = Fields3<SYS>::M;
-  const long long n = (long long)G.ex * G.ey * G.ez;
+  const long long n = G.size();
   int ei, ej, ek;
   long long e;
   if (!ext_coords(G, ei, ej, ek, e)) return;
@@ -375,7 +382,7 @@ __global__ void k3_moments_ext(DevParams P, R* const* buf, const Ctl* ctl, int s
 template <int SYS, class R>
 __global__ void k3_ghost_fill(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, R* Ue2) {
   constexpr int M = Fields3<SYS>::M;
-  const long long n = (long long)G.ex * G.ey * G.ez;
+  const long long n = G.size();
   const long long na = 2LL * GH * G.ey * G.ex, nb = 2LL * GH * G.ex * P.nz3, nc = 2LL * GH * P.ny3 * P.nz3;
   const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (g >= na + nb + nc) return;
@@ -419,7 +426,7 @@ constexpr int kZ3 = 16;
 template <int SYS, class R>
 __global__ void k3_indicator(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, const R* Ue2, R* nu) {
   constexpr int M = Fields3<SYS>::M;
-  const long long n = (long long)G.ex * G.ey * G.ez;
+  const long long n = G.size();
   int ei, ej, ek;
   long long e;
   if (!ext_coords(G, ei, ej, ek, e)) return;
@@ -427,7 +434,7 @@ __global__ void k3_indicator(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, 
   const R* Ue = ue_copy<M>(Ue2, G, ctl->parity[slot]);
   if (ei < 1 || ei >= G.ex - 1 || ej < 1 || ej >= G.ey - 1 || ek < 1 || ek >= G.ez - 1) return;
   const Phys<R> K = make_phys<R>(P);
-  const long long stride[3] = {1, G.ex, (long long)G.ex * G.ey};
+  const long long stride[3] = {1, G.px, (long long)G.px * G.ey};
   unsigned int* const stc = (unsigned int*)&ctl->status;  // index guards (bounds-checked builds)
   R U0[M], dm[M], dp[M];
 #pragma unroll
@@ -457,7 +464,7 @@ __global__ void k3_omega(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, cons
   if (ei < 2 || ei >= G.ex - 2 || ej < 2 || ej >= G.ey - 2) return;
   if (P.T > 0.0 && ctl->t[slot] >= P.T) return;
   const int k0 = max(2, (int)blockIdx.z * kZ3), k1 = min(G.ez - 2, (int)blockIdx.z * kZ3 + kZ3);
-  const long long n = (long long)G.ex * G.ey * G.ez;
+  const long long n = G.size();
   unsigned int* const stc = (unsigned int*)&ctl->status;  // index guards (bounds-checked builds)
   if (P.omega_mode == 1) {
     R wf;
@@ -474,7 +481,7 @@ __global__ void k3_omega(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, cons
 #pragma unroll
     for (int bj = -1; bj <= 1; bj++)
 #pragma unroll
-      for (int bi = -1; bi <= 1; bi++) o[(bj + 1) * 3 + bi + 1] = nu[chk(b + (long long)bj * G.ex + bi, n, stc)];
+      for (int bi = -1; bi <= 1; bi++) o[(bj + 1) * 3 + bi + 1] = nu[chk(b + (long long)bj * G.px + bi, n, stc)];
   };
   if (k0 < k1) {
     load_plane(k0 - 1, win[0]);
@@ -706,10 +713,10 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks))
   const R* Ue = ue_copy<M>(Ue2, G, par);
   R* Uo_ext = ue_copy<M>(Ue2, G, par ^ 1);  // U^{n+1} of the interior, for the next step
   // offsets in IX: int where every offset of the lattice fits (chosen at launch), else long long
-  const IX n = (IX)G.ex * G.ey * G.ez, pl = (IX)P.plane;
+  const IX n = (IX)G.size(), pl = (IX)P.plane;
   const long long nf = 7ll * M * P.plane;  // elements of the distributions (index guards)
   unsigned int* const stc = &ctl->status;
-  auto eidx = [&](int ek, int ej, int ei) -> IX { return ((IX)ek * G.ey + ej) * G.ex + ei; };
+  auto eidx = [&](int ek, int ej, int ei) -> IX { return ((IX)ek * G.ey + ej) * G.px + ei; };
   auto fidx = [&](int ci, int cj, int ck) -> IX { return ((IX)ck * P.ny3 + cj) * P.pitch + ci + XPAD; };
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i = blockIdx.x * kOut3 + w * kSeg3 - 1 + lane, k = blockIdx.z;

@@ -7,38 +7,82 @@
 // kernel); the indicator (Eq. 2.13/2.14), its 27-point box sum and omega
 // (Eq. 2.15/2.16) are computed in shared memory as the tile marches, instead
 // of round trips through global nu and omega arrays.  Per plane q:
-//   U(q) on the tile + 3 arrives (cp.async, one plane ahead) in a ring of 4 planes
+//   U(q) on the tile + 3 arrives (one TMA box, one plane ahead) in a ring of 4
 //   1  nu(q-1) on the tile + 2 from U(q-2..q)         (ring of 3 nu planes)
 //   2  omega(q-2) on the tile + 1 from nu(q-3..q-1)
 //   3  posts of plane q-2: every direction at the tile's own columns, the one
 //      direction each halo column or row streams into the tile
 //   4  plane q-3 streamed (F_k(x) = post_k(x - e_k), Eq. 2.2), the implicit
 //      moment (2.8) and second half-source; f^{n+1} and U^{n+1} stored
-// Sideways posts pass between lanes by warp shuffles (x) and shared memory (y,
-// and the halo); the +-z posts stay in the thread's registers.  Every node's
-// values are those of the four-kernel path (the same expressions in the same
-// order), so the two paths agree to rounding.
+// The own columns' f^n of plane q-2 (all 7 m planes of the tile, one TMA box
+// in FP32) is requested once plane q-3's posts are formed, so it lands while
+// phases 1 and 2 of the next plane run (lanes of a ragged tile past the
+// lattice's edge hold ghost nodes: they load the mapped node's f^n instead);
+// the halo nodes' f^n (one direction each) is copied with cp.async at the
+// start of the plane.  Sideways posts
+// pass between lanes by warp shuffles (x) and shared memory (y, and the
+// halo); the +-z posts stay in the thread's registers.  Every node's values
+// are those of the four-kernel path (the same expressions in the same order),
+// so the two paths agree to rounding.
 #pragma once
 #include "lbm3d.cuh"
 
 namespace lbmh {
 
 constexpr int kTX3 = 32, kTY3 = 8, kThreads3F = kTX3 * kTY3;
-constexpr int kUW3 = kTX3 + 6, kUH3 = kTY3 + 6;  // U tile + 3
+constexpr int kUW3 = kTX3 + 8, kUH3 = kTY3 + 6;  // U tile + 3 (38 x 14 used), loaded as a 40 x 14 box
 constexpr int kNW3 = kTX3 + 4, kNH3 = kTY3 + 4;  // nu tile + 2
 constexpr int kOW3 = kTX3 + 2, kOH3 = kTY3 + 2;  // omega tile + 1
 constexpr int kURing3 = 4;
+constexpr int kHalo3 = 2 * kTY3 + 2 * kTX3;      // halo columns and rows that stream into the tile
+
+// The own columns' f^n through one TMA box per plane in FP32.  FP64 (bound by
+// the FP64 pipe) loads it where it is used: the box would not fit beside the
+// U ring at every system.
+template <class R>
+constexpr bool k3f_f_tma() {
+  return sizeof(R) == 4;
+}
 
 template <int M, class R>
 struct Smem3F {
-  static constexpr size_t u_elems = (size_t)kURing3 * M * kUH3 * kUW3;
-  static constexpr size_t nu_elems = (size_t)3 * kNH3 * kNW3;
-  static constexpr size_t om_elems = (size_t)kOH3 * kOW3;
-  static constexpr size_t py_elems = (size_t)M * (kTY3 + 1) * kTX3;  // post_{+y}, row ty at ty + 1
-  static constexpr size_t my_elems = (size_t)M * (kTY3 + 1) * kTX3;  // post_{-y}, row ty at ty
-  static constexpr size_t hx_elems = (size_t)2 * M * kTY3;           // halo columns' post_{+x} / post_{-x}
-  static constexpr size_t total = (u_elems + nu_elems + om_elems + py_elems + my_elems + hx_elems) * sizeof(R);
+  static constexpr size_t a128(size_t b) { return (b + 127) / 128 * 128; }
+  static constexpr uint32_t u_box = (uint32_t)(M * kUH3 * kUW3 * sizeof(R));  // bytes of one U box
+  static constexpr uint32_t f_box = (uint32_t)(7 * M * kTY3 * kTX3 * sizeof(R));
+  static constexpr size_t u_slot = a128(u_box);  // TMA destinations start on 128 bytes
+  static constexpr size_t f_off = kURing3 * u_slot;
+  static constexpr size_t nu_off = f_off + (k3f_f_tma<R>() ? a128(f_box) : 0);
+  static constexpr size_t om_off = nu_off + (size_t)3 * kNH3 * kNW3 * sizeof(R);
+  static constexpr size_t py_off = om_off + (size_t)kOH3 * kOW3 * sizeof(R);
+  static constexpr size_t py_bytes = (size_t)M * (kTY3 + 1) * kTX3 * sizeof(R);
+  static constexpr size_t my_off = py_off + py_bytes;
+  static constexpr size_t hx_off = my_off + py_bytes;
+  static constexpr size_t hf_off = hx_off + (size_t)2 * M * kTY3 * sizeof(R);
+  static constexpr size_t bar_off = (hf_off + (size_t)kHalo3 * M * sizeof(R) + 7) / 8 * 8;
+  // plus 128 bytes of slack: the kernel starts its layout on the first
+  // 128-byte boundary of its dynamic shared memory
+  static constexpr size_t total = bar_off + (kURing3 + 1) * sizeof(unsigned long long) + 128;
 };
+
+__device__ __forceinline__ void tma_load_box3(const CUtensorMap* tm, uint32_t dst, uint32_t bar, int x, int y, int z,
+                                              uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(dst),
+      "l"(tm), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_box4(const CUtensorMap* tm, uint32_t dst, uint32_t bar, int x, int y, int z,
+                                              int w, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(tm), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+      : "memory");
+}
 
 template <class R>
 __device__ __forceinline__ void cp_async_elem(R* dst, const R* src) {
@@ -51,25 +95,36 @@ __device__ __forceinline__ void cp_async_elem(R* dst, const R* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// resident blocks per SM the registers are budgeted for
+// resident blocks per SM the registers are budgeted for: 2 in FP32 (about
+// 100 KB of shared memory a block), 1 for FP32 reactive Euler (119 KB) and FP64
 template <int SYS, class R>
-constexpr int k3f_min_blocks() { return sizeof(R) == 4 ? 2 : 1; }
+constexpr int k3f_min_blocks() { return (sizeof(R) == 4 && SYS != SYS_REACT) ? 2 : 1; }
 
+// tu0/tu1: U copies 0/1 as {ex, ey, ez, m} (rows of G.px elements), boxes
+// {40, 14, 1, m}; tf0/tf1: distribution buffers 0/1 as {pitch, ny * nz, 7 m},
+// boxes {32, 8, 7 m}
 template <int SYS, class R>
 __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
-    k3_fused(DevParams P, R* const* buf, Ctl* ctl, int slot, ExtGeom3 G, R* Ue2, double* partials, int zc) {
+    k3_fused(const __grid_constant__ CUtensorMap tu0, const __grid_constant__ CUtensorMap tu1,
+             const __grid_constant__ CUtensorMap tf0, const __grid_constant__ CUtensorMap tf1, DevParams P,
+             R* const* buf, Ctl* ctl, int slot, ExtGeom3 G, R* Ue2, double* partials, int zc) {
   constexpr int M = Fields3<SYS>::M, Q = 7;
   constexpr bool SRC = SYS == SYS_REACT;
+  constexpr bool FBOX = k3f_f_tma<R>();
   using L = Smem3F<M, R>;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  R* Us = (R*)smem_raw;              // [ring][M][kUH3][kUW3]
-  R* nus = Us + L::u_elems;          // [3][kNH3][kNW3]
-  R* oms = nus + L::nu_elems;        // [kOH3][kOW3]
-  R* pys = oms + L::om_elems;        // [M][kTY3 + 1][kTX3]
-  R* mys = pys + L::py_elems;        // [M][kTY3 + 1][kTX3]
-  R* hxs = mys + L::my_elems;        // [2][M][kTY3]
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  unsigned char* const smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
+  const R* fs = (const R*)(smem_raw + L::f_off);  // [7 m][kTY3][kTX3]
+  R* nus = (R*)(smem_raw + L::nu_off);            // [3][kNH3][kNW3]
+  R* oms = (R*)(smem_raw + L::om_off);            // [kOH3][kOW3]
+  R* pys = (R*)(smem_raw + L::py_off);            // [M][kTY3 + 1][kTX3]
+  R* mys = (R*)(smem_raw + L::my_off);            // [M][kTY3 + 1][kTX3]
+  R* hxs = (R*)(smem_raw + L::hx_off);            // [2][M][kTY3]
+  R* hfs = (R*)(smem_raw + L::hf_off);            // [kHalo3][M]
+  unsigned long long* bars = (unsigned long long*)(smem_raw + L::bar_off);  // U slots 0..3, f box 4
   __shared__ StepCoef3 s_cf;
   __shared__ R s_k[9];  // a0, 1/(2 lambda), dt/2, alpha_0..2, a_1..3
+  __shared__ int s_abort;
   const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
   if (t == 0) {
     const StepCoef3 c = step_coef3(P, ctl, slot);
@@ -82,6 +137,9 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
       s_k[3 + j] = R(c.alpha[j]);
       s_k[6 + j] = R(c.aj[j]);
     }
+    for (int i = 0; i < kURing3 + 1; i++) mbar_init(smem_u32(&bars[i]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
   }
   __syncthreads();
   const StepCoef3 cf = s_cf;
@@ -93,9 +151,10 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
   const int par = ctl->parity[slot];
   const R* f = buf[par];
   R* fo = buf[par ^ 1];
-  const R* Ue = ue_copy<M>(Ue2, G, par);
   R* Uo_ext = ue_copy<M>(Ue2, G, par ^ 1);  // U^{n+1} of the interior, for the next step
-  const long long n = (long long)G.ex * G.ey * G.ez;
+  const CUtensorMap* tu = par ? &tu1 : &tu0;
+  const CUtensorMap* tf = par ? &tf1 : &tf0;
+  const long long n = G.size();
   const long long nf = 7ll * M * P.plane;
   unsigned int* const stc = &ctl->status;
   const Phys<R> K = make_phys<R>(P);
@@ -114,24 +173,31 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
   const int x = x0 + tx, y = y0 + ty;
   const bool own_valid = x < P.nx && y < P.ny3;
   const int mx = map_index(x, P.nx, P.bc[0], P.bc[1]), my = map_index(y, P.ny3, P.bc[2], P.bc[3]);
+  const int q0 = zb - 3, q1 = ze + 2;
 
-  // U(plane) on the tile + 3 into ring slot plane % 4 (ext coordinates: x0 + ix,
-  // y0 + iy, plane + GH; points past the extension are never used for an
-  // output and are not copied)
-  auto load_u = [&](int plane) {
-    R* dst = Us + (size_t)(((plane % kURing3) + kURing3) % kURing3) * M * kUH3 * kUW3;
-    const int ek = plane + GH;
-    constexpr int items = M * kUH3 * kUW3;
-    for (int it = t; it < items; it += kThreads3F) {
-      const int c = it / (kUH3 * kUW3), rem = it % (kUH3 * kUW3), iy = rem / kUW3, ix = rem % kUW3;
-      const int ei = x0 + ix, ej = y0 + iy;
-      if (ei < G.ex && ej < G.ey) cp_async_elem(dst + it, Ue + chk((long long)c * n + G.idx(ek, ej, ei), (long long)M * n, stc));
-    }
-    cp_async_commit();
+  // U(p) on the tile + 3 (ext coordinates x0.., y0.., p + GH) into ring slot
+  // (p - q0) % 4; points past the extension arrive as zeros and are never
+  // used for an output
+  auto uslot = [&](int p) -> const R* { return (const R*)(smem_raw + (size_t)((p - q0) % kURing3) * L::u_slot); };
+  auto issue_u = [&](int p) {
+    const int s = (p - q0) % kURing3;
+    tma_load_box4(tu, smem_u32(smem_raw + (size_t)s * L::u_slot), smem_u32(&bars[s]), x0, y0, p + GH, 0, L::u_box);
   };
-  auto uslot = [&](int plane) -> const R* {
-    return Us + (size_t)(((plane % kURing3) + kURing3) % kURing3) * M * kUH3 * kUW3;
+  // f^n of the own columns of plane pp (mapped to mk): rows mk * ny + y0..
+  auto issue_f = [&](int pp) {
+    const int mk = map_index(pp, P.nz3, P.bc_z[0], P.bc_z[1]);
+    tma_load_box3(tf, smem_u32(smem_raw + L::f_off), smem_u32(&bars[kURing3]), XPAD + x0, mk * P.ny3 + y0, 0,
+                  L::f_box);
   };
+
+  // this thread's halo node (t < kHalo3): the one direction qq (along dir) it
+  // streams into the tile
+  int hx = 0, hy = 0, hq = 0, hdir = 0;
+  if (t < kTY3) { hx = -1; hy = t; hq = 1; hdir = 0; }
+  else if (t < 2 * kTY3) { hx = kTX3; hy = t - kTY3; hq = 4; hdir = 0; }
+  else if (t < 2 * kTY3 + kTX3) { hx = t - 2 * kTY3; hy = -1; hq = 2; hdir = 1; }
+  else if (t < kHalo3) { hx = t - 2 * kTY3 - kTX3; hy = kTY3; hq = 5; hdir = 1; }
+  const int hmx = map_index(x0 + hx, P.nx, P.bc[0], P.bc[1]), hmy = map_index(y0 + hy, P.ny3, P.bc[2], P.bc[3]);
 
   R sp0 = R(0), sp1 = R(0), sp2 = R(0);
   Acc<R> acc[M];
@@ -144,13 +210,47 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
 #pragma unroll
   for (int c = 0; c < M; c++) kp0[c] = kxp[c] = kxm[c] = kyp[c] = kym[c] = pz1[c] = pz2[c] = R(0);
 
-  const int q0 = zb - 3, q1 = ze + 2;
-  load_u(q0);
+  // load bookkeeping of thread 0, the issuing thread: it issues a load only
+  // while every wait it made has succeeded, and before exiting waits for every
+  // load it issued and has not seen land (a CTA whose wait gave up leaves no
+  // copy in flight)
+  int u_issued = q0 - 1, u_seen = q0 - 1;
+  int f_issued = 0, f_seen = 0;
+  unsigned f_waits = 0;
+  bool ok0 = true;
+  if (t == 0) {
+    issue_u(q0);
+    u_issued = q0;
+    if (FBOX && zb + 1 <= q1) {
+      issue_f(zb - 1);
+      f_issued = 1;
+    }
+  }
+
 #pragma unroll 1
   for (int q = q0; q <= q1; q++) {
-    cp_async_wait_all();  // U(q) of this thread's copies
-    if (q < q1) load_u(q + 1);
-    __syncthreads();      // U(q) of every thread visible
+    const bool got = mbar_wait_bounded(smem_u32(&bars[(q - q0) % kURing3]), (unsigned)((q - q0) / kURing3) & 1u);
+    if (!got) s_abort = 1;
+    if (t == 0) {
+      if (got) u_seen = q;
+      ok0 = ok0 && got;
+      if (ok0 && q < q1) {  // slot (q + 1 - q0) % 4 last held U(q - 3): read for the last time in plane q - 1
+        issue_u(q + 1);
+        u_issued = q + 1;
+      }
+    }
+    const bool posts = q >= zb + 1;
+    const int pp = q - 2;  // plane of this iteration's posts
+    const int mk = map_index(pp, P.nz3, P.bc_z[0], P.bc_z[1]);
+    if (posts && t < kHalo3) {  // the halo node's f^n of its direction, for phase 3
+      const long long off = cell3(P, hmx, hmy, mk);
+#pragma unroll
+      for (int c = 0; c < M; c++)
+        cp_async_elem(hfs + t * M + c, f + chk((long long)(hq * M + c) * P.plane + off, nf, stc));
+      cp_async_commit();
+    }
+    __syncthreads();  // U(q) landed for every thread (or the CTA stops here)
+    if (s_abort) break;
     // 1: nu(q - 1) on the tile + 2
     if (q >= zb - 1) {
       const R* Um1 = uslot(q - 2);
@@ -205,10 +305,8 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
       }
     }
     __syncthreads();
-    if (q >= zb + 1) {
+    if (posts) {
       // 3: posts of plane pp = q - 2
-      const int pp = q - 2;
-      const int mk = map_index(pp, P.nz3, P.bc_z[0], P.bc_z[1]);
       const R* Ut = uslot(pp);
       constexpr int CS = kUH3 * kUW3;
       // own column: all seven directions
@@ -219,11 +317,33 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
 #pragma unroll
         for (int c = 0; c < M; c++) U[c] = Ut[c * CS + o];
         const R w = oms[(ty + 1) * kOW3 + (tx + 1)];
-        const long long off = cell3(P, mx, my, mk);
+        if constexpr (FBOX) {
+          const bool fgot = mbar_wait_bounded(smem_u32(&bars[kURing3]), f_waits & 1u);
+          f_waits++;
+          if (!fgot) s_abort = 1;
+          if (t == 0) {
+            if (fgot) f_seen++;
+            ok0 = ok0 && fgot;
+          }
+          if (own_valid) {
 #pragma unroll
-        for (int k = 0; k < Q; k++)
+            for (int k = 0; k < Q; k++)
 #pragma unroll
-          for (int c = 0; c < M; c++) fq[k][c] = f[chk((long long)(k * M + c) * P.plane + off, nf, stc)];
+              for (int c = 0; c < M; c++) fq[k][c] = fs[(k * M + c) * (kTY3 * kTX3) + ty * kTX3 + tx];
+          } else {  // a lane past the lattice's edge (ragged tile): its ghost node is the mapped node
+            const long long off = cell3(P, mx, my, mk);
+#pragma unroll
+            for (int k = 0; k < Q; k++)
+#pragma unroll
+              for (int c = 0; c < M; c++) fq[k][c] = f[chk((long long)(k * M + c) * P.plane + off, nf, stc)];
+          }
+        } else {
+          const long long off = cell3(P, mx, my, mk);
+#pragma unroll
+          for (int k = 0; k < Q; k++)
+#pragma unroll
+            for (int c = 0; c < M; c++) fq[k][c] = f[chk((long long)(k * M + c) * P.plane + off, nf, stc)];
+        }
         const Prim3<R> pw = prim3<SYS, R>(K, U);
         if constexpr (SRC)
           source3<SYS, R>(K, U, S);
@@ -259,36 +379,30 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
         mys[(c * (kTY3 + 1) + ty) * kTX3 + tx] = pown[5][c];
       }
       // halo: the one direction each halo column / row streams into the tile
-      if (t < 2 * kTY3 + 2 * kTX3) {
-        int hx, hy, qq, dir;
-        if (t < kTY3) { hx = -1; hy = t; qq = 1; dir = 0; }
-        else if (t < 2 * kTY3) { hx = kTX3; hy = t - kTY3; qq = 4; dir = 0; }
-        else if (t < 2 * kTY3 + kTX3) { hx = t - 2 * kTY3; hy = -1; qq = 2; dir = 1; }
-        else { hx = t - 2 * kTY3 - kTX3; hy = kTY3; qq = 5; dir = 1; }
-        const int gxh = x0 + hx, gyh = y0 + hy;
+      if (t < kHalo3) {
+        cp_async_wait_all();  // this thread's own copies of its halo f^n
         const int o = (hy + 3) * kUW3 + (hx + 3);
         R U[M], fq[M], S[M], F[M];
 #pragma unroll
-        for (int c = 0; c < M; c++) U[c] = Ut[c * CS + o];
+        for (int c = 0; c < M; c++) {
+          U[c] = Ut[c * CS + o];
+          fq[c] = hfs[t * M + c];
+        }
         const R w = oms[(hy + 1) * kOW3 + (hx + 1)];
-        const long long off = cell3(P, map_index(gxh, P.nx, P.bc[0], P.bc[1]), map_index(gyh, P.ny3, P.bc[2], P.bc[3]), mk);
-#pragma unroll
-        for (int c = 0; c < M; c++) fq[c] = f[chk((long long)(qq * M + c) * P.plane + off, nf, stc)];
         const Prim3<R> pw = prim3<SYS, R>(K, U);
         if constexpr (SRC)
           source3<SYS, R>(K, U, S);
         else
 #pragma unroll
           for (int c = 0; c < M; c++) S[c] = R(0);
-        flux3<SYS, R>(K, P, U, pw, dir, F);
-        R* dst = qq == 1 ? hxs + hy : (qq == 4 ? hxs + M * kTY3 + hy
-                                              : (qq == 2 ? pys + hx : mys + kTY3 * kTX3 + hx));
-        const int cstride = (qq == 1 || qq == 4) ? kTY3 : (kTY3 + 1) * kTX3;
+        flux3<SYS, R>(K, P, U, pw, hdir, F);
+        R* dst = hq == 1 ? hxs + hy : (hq == 4 ? hxs + M * kTY3 + hy : (hq == 2 ? pys + hx : mys + kTY3 * kTX3 + hx));
+        const int cstride = (hq == 1 || hq == 4) ? kTY3 : (kTY3 + 1) * kTX3;
 #pragma unroll
         for (int c = 0; c < M; c++) {
-          const R feq = qq <= 3 ? (al[dir] * U[c] + F[c]) * inv2l : (al[dir] * U[c] - F[c]) * inv2l;
+          const R feq = hq <= 3 ? (al[hdir] * U[c] + F[c]) * inv2l : (al[hdir] * U[c] - F[c]) * inv2l;
           R v = fq[c] - w * (fq[c] - feq);
-          if constexpr (SRC) v += hdt * aj[dir] * S[c];
+          if constexpr (SRC) v += hdt * aj[hdir] * S[c];
           dst[c * cstride] = v;
         }
       }
@@ -356,7 +470,11 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
         if constexpr (SYS != SYS_ADV) bad |= !(wn.rho > R(0)) || !(wn.p > R(0));
         if (bad) st |= ST_NONPHYSICAL;
       }
-      __syncthreads();  // the sideways posts of plane q - 2 are in shared memory
+      __syncthreads();  // the sideways posts of plane q - 2 are in shared memory; the f box is read
+      if (FBOX && t == 0 && ok0 && q + 1 <= q1) {  // the own f^n of plane q - 1, for the next plane's posts
+        issue_f(q - 1);
+        f_issued++;
+      }
       // gather them for plane q - 2 (streamed one plane later)
 #pragma unroll
       for (int c = 0; c < M; c++) {
@@ -372,6 +490,15 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
       }
     }
   }
+  cp_async_wait_all();
+  if (t == 0) {  // loads issued and not seen landing: only after a wait gave up
+    bool drained = true;
+    for (int p = u_seen + 1; p <= u_issued; p++)
+      drained = mbar_wait_bounded(smem_u32(&bars[(p - q0) % kURing3]), (unsigned)((p - q0) / kURing3) & 1u) && drained;
+    for (int i = f_seen; i < f_issued; i++) drained = mbar_wait_bounded(smem_u32(&bars[kURing3]), (unsigned)i & 1u) && drained;
+    if (!drained) st |= ST_TIMEOUT;
+  }
+  if (s_abort) st |= ST_TIMEOUT;
   // side outputs per warp (partial slot bid * 8 + warp): no block barrier
   warp_side_outputs3<M, R>(sp0, sp1, sp2, acc, ctl, (slot + 1) % 3,
                            partials + (bid * (kThreads3F / 32) + ty) * M, st);
@@ -381,6 +508,34 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
 // launch shape of the fused 3D step: tiles of 32 x 8 columns, chunks of zc planes
 inline dim3 grid3_fused(int nx, int ny, int nz, int zc) {
   return dim3((unsigned)((nx + kTX3 - 1) / kTX3), (unsigned)((ny + kTY3 - 1) / kTY3), (unsigned)((nz + zc - 1) / zc));
+}
+
+// TMA descriptors of the fused 3D step: both U copies of the ghost-extended
+// grid and both distribution buffers (layouts as described at k3_fused)
+template <int M, class R>
+inline int k3f_encode_maps(FusedPlan& fp, const DevParams& P, const ExtGeom3& G, void* Ue2, void* const* fbuf) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return -1;
+  const CUtensorMapDataType dt = sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  const cuuint64_t s = sizeof(R);
+  for (int b = 0; b < 2; b++) {
+    cuuint64_t udims[4] = {(cuuint64_t)G.ex, (cuuint64_t)G.ey, (cuuint64_t)G.ez, (cuuint64_t)M};
+    cuuint64_t ustr[3] = {(cuuint64_t)G.px * s, (cuuint64_t)G.px * G.ey * s, (cuuint64_t)G.size() * s};
+    cuuint32_t ubox[4] = {(cuuint32_t)kUW3, (cuuint32_t)kUH3, 1u, (cuuint32_t)M};
+    cuuint32_t e4[4] = {1u, 1u, 1u, 1u};
+    CUresult r = enc(&fp.tu3[b], dt, 4, (R*)Ue2 + (size_t)b * M * G.size(), udims, ustr, ubox, e4,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return -1;
+    cuuint64_t fdims[3] = {(cuuint64_t)P.pitch, (cuuint64_t)P.ny, (cuuint64_t)(7 * M)};
+    cuuint64_t fstr[2] = {(cuuint64_t)P.pitch * s, (cuuint64_t)P.plane * s};
+    cuuint32_t fbox[3] = {(cuuint32_t)kTX3, (cuuint32_t)kTY3, (cuuint32_t)(7 * M)};
+    cuuint32_t e3[3] = {1u, 1u, 1u};
+    r = enc(&fp.tf3[b], dt, 3, fbuf[b], fdims, fstr, fbox, e3, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return -1;
+  }
+  return 0;
 }
 
 }  // namespace lbmh

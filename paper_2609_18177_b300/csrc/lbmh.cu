@@ -96,6 +96,9 @@ __global__ void k_set_bound(Ctl* ctl, int slot, unsigned long long b0, unsigned 
 // per-(system, dimension, precision) operations
 // ---------------------------------------------------------------------------
 
+int ensure_scratch(lbmh_handle* h);
+void free_scratch(lbmh_handle* h);
+
 struct Ops {
   int (*launch_step)(lbmh_handle*, int slot, double T);
   int (*launch_unfused_diag)(lbmh_handle*, int slot);  // K0..K2 only
@@ -215,7 +218,7 @@ template <int SYS, class R>
 struct Impl3 {
   static constexpr int M = Fields3<SYS>::M, Q = 7;
 
-  static ExtGeom3 geom(const lbmh_handle* h) { return ExtGeom3{h->G.ex, h->G.ey, h->G.ez}; }
+  static ExtGeom3 geom(const lbmh_handle* h) { return ExtGeom3{h->G.ex, h->G.ey, h->G.ez, ext_pitch3(h->G.ex)}; }
 
   static int launch_step(lbmh_handle* h, int slot, double T) {
     DevParams P = h->P;
@@ -233,7 +236,9 @@ struct Impl3 {
     if (h->kernel == LBMH_KERNEL_FUSED) {  // indicator, omega, collision and streaming in one pass
       const int zc = h->fp.band;
       const dim3 gf = grid3_fused(P.nx, P.ny3, P.nz3, zc);
-      k3_fused<SYS, R><<<gf, kThreads3F, h->fp.smem, h->stream>>>(P, buf, h->ctl, slot, G, (R*)h->Ue, h->partials, zc);
+      k3_fused<SYS, R><<<gf, kThreads3F, h->fp.smem, h->stream>>>(h->fp.tu3[0], h->fp.tu3[1], h->fp.tf3[0],
+                                                                  h->fp.tf3[1], P, buf, h->ctl, slot, G, (R*)h->Ue,
+                                                                  h->partials, zc);
       h->u3_valid = true;
       h->nblocks = (int)(gf.x * gf.y * gf.z) * (kThreads3F / 32);
       cudaError_t e = cudaGetLastError();
@@ -243,7 +248,7 @@ struct Impl3 {
     k3_indicator<SYS, R><<<ge, kBlock3, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->Ue, (R*)h->nue);
     k3_omega<R><<<grid3_omega(G.ex, G.ey, G.ez), kBlock3, 0, h->stream>>>(P, h->ctl, slot, G, (const R*)h->nue,
                                                                           (R*)h->ome);
-    if (!h->idx64_3d && k3_offsets_fit_int(P, M, (long long)G.ex * G.ey * G.ez))
+    if (!h->idx64_3d && k3_offsets_fit_int(P, M, G.size()))
       k3_collide_stream<SYS, R, int><<<gn, kBlock3, 0, h->stream>>>(P, buf, h->ctl, slot, G, (R*)h->Ue,
                                                                     (const R*)h->ome, h->partials);
     else
@@ -313,6 +318,13 @@ struct Impl3 {
     int zc = 32;
     const char* e = getenv("LBMH_3D_ZCHUNK");
     if (e && atoi(e) >= 8) zc = atoi(e);
+    // the U boxes read the ghost-extended copies: allocated here (the two U
+    // copies only), then described to the TMA unit
+    if (ensure_scratch(h) != LBMH_OK) return -1;
+    if (k3f_encode_maps<M, R>(h->fp, h->P, geom(h), h->Ue, h->fbuf) != 0) {
+      free_scratch(h);
+      return -1;
+    }
     h->fp.smem = (int)L::total;
     h->fp.band = zc;
     const dim3 g = grid3_fused(h->P.nx, h->P.ny3, h->P.nz3, zc);
@@ -387,10 +399,24 @@ int ensure_utmp(lbmh_handle* h, size_t bytes) {
   return LBMH_OK;
 }
 
+// releases the ghost-extended scratch (ensure_scratch allocates it again)
+void free_scratch(lbmh_handle* h) {
+  long long next = (long long)(h->dim == 3 ? ext_pitch3(h->G.ex) : h->G.ex) * h->G.ey * h->G.ez;
+  size_t b1 = (size_t)next * h->m * h->elem * (h->dim == 3 ? 2 : 1), b2 = (size_t)next * h->elem;
+  if (h->Ue) h->device_bytes -= (long long)b1;
+  if (h->nue) h->device_bytes -= (long long)b2;
+  if (h->ome) h->device_bytes -= (long long)b2;
+  cudaFree(h->Ue);
+  cudaFree(h->nue);
+  cudaFree(h->ome);
+  h->Ue = h->nue = h->ome = nullptr;
+}
+
 // ghost-extended scratch of the unfused path (also used by lbmh_omega)
 int ensure_scratch(lbmh_handle* h) {
   if (h->Ue) return LBMH_OK;
-  long long next = (long long)h->G.ex * h->G.ey * h->G.ez;
+  // 3D rows are padded to ext_pitch3 (16-byte row starts for the TMA boxes)
+  long long next = (long long)(h->dim == 3 ? ext_pitch3(h->G.ex) : h->G.ex) * h->G.ey * h->G.ez;
   size_t b1 = (size_t)next * h->m * h->elem * (h->dim == 3 ? 2 : 1), b2 = (size_t)next * h->elem;
   // the fused 3D step keeps nu and omega on chip: only the two U copies
   const bool u_only = h->dim == 3 && h->kernel == LBMH_KERNEL_FUSED;
@@ -552,9 +578,12 @@ int create_impl(const lbmh_problem* p, const SlabGeom* sg, lbmh_handle** out) {
     P.row0 = sg->row0;
   }
 
-  // 3D: the fused z-marching kernel only when asked for (measured slower than
-  // the four-kernel path at 256^3: 1.80 against 1.64 ms per step)
-  bool want_fused = p->dim == 3 ? p->kernel == LBMH_KERNEL_FUSED : p->kernel != LBMH_KERNEL_UNFUSED;
+  // 3D: the fused z-marching kernel by default in FP32 (256^3 Euler: 1.30
+  // against 1.64 ms per step for the four-kernel path); in FP64, bound by the
+  // FP64 pipe, the four-kernel path (25.7 against 33.7 ms) unless asked for
+  const bool auto_fused3 = p->precision == LBMH_FP32;
+  bool want_fused = p->dim == 3 ? (p->kernel == LBMH_KERNEL_FUSED || (p->kernel == LBMH_KERNEL_AUTO && auto_fused3))
+                                : p->kernel != LBMH_KERNEL_UNFUSED;
   if (p->kernel == LBMH_KERNEL_FUSED && !h->ops->has_fused) {
     delete h;
     return fail(nullptr, LBMH_ERR_UNSUPPORTED, "no fused kernel for this system/dimension/precision");

@@ -48,7 +48,7 @@ CASES = [(s, bc) for s in (W.ADVECTION, W.EULER, W.REACTIVE) for bc in (W.PERIOD
 IDS = [f"{W.SYSTEM_NAMES[s]}-{'per' if bc == 0 else 'out'}" for s, bc in CASES]
 
 
-KERNELS = [(lbmh.KERNEL_FUSED, "fused"), (lbmh.KERNEL_AUTO, "four-kernel")]
+KERNELS = [(lbmh.KERNEL_FUSED, "fused"), (lbmh.KERNEL_UNFUSED, "four-kernel")]
 
 
 @pytest.mark.parametrize("kernel", [k for k, _ in KERNELS], ids=[n for _, n in KERNELS])
