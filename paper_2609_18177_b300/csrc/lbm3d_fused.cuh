@@ -1,7 +1,7 @@
 // Fused 3D (D3Q7) step: one kernel per step after the ghost layers of U.
 //
-// A block of 256 threads owns a tile of 32 x 8 output columns (x, y) and
-// marches a chunk of planes along z.  The only state read from global memory
+// A block of 32 x TY threads owns a tile of 32 x TY output columns (x, y) and
+// marches a chunk of planes along z (TY = 8, Tile3F).  The only state read from global memory
 // besides the distributions is U^n on the ghost-extended grid (written as a
 // side product by the previous step, its ghost layers refilled before this
 // kernel); the indicator (Eq. 2.13/2.14), its 27-point box sum and omega
@@ -29,12 +29,27 @@
 
 namespace lbmh {
 
-constexpr int kTX3 = 32, kTY3 = 8, kThreads3F = kTX3 * kTY3;
-constexpr int kUW3 = kTX3 + 8, kUH3 = kTY3 + 6;  // U tile + 3 (38 x 14 used), loaded as a 40 x 14 box
-constexpr int kNW3 = kTX3 + 4, kNH3 = kTY3 + 4;  // nu tile + 2
-constexpr int kOW3 = kTX3 + 2, kOH3 = kTY3 + 2;  // omega tile + 1
+constexpr int kTX3 = 32;
+constexpr int kUW3 = kTX3 + 8;  // U tile + 3 (38 columns used), loaded as a 40-column box
+constexpr int kNW3 = kTX3 + 4;  // nu tile + 2
+constexpr int kOW3 = kTX3 + 2;  // omega tile + 1
 constexpr int kURing3 = 4;
-constexpr int kHalo3 = 2 * kTY3 + 2 * kTX3;      // halo columns and rows that stream into the tile
+
+// Tile height (rows of 32 columns; one warp per row).  8 rows, 256 threads.
+// Tiles of 16 rows (512 threads, one block per SM) cut the indicator's
+// recompute on the tile + 2 from 1.75 to 1.44 evaluations per output node,
+// but ran slower (256^3 Euler FP32: 1.37 against 1.30 ms per step): two
+// blocks of 8 warps overlap one another's barriers, one block of 16 does not.
+template <int SYS, class R>
+struct Tile3F {
+  static constexpr int TY = 8;
+  static constexpr int threads = kTX3 * TY;
+  static constexpr int UH = TY + 6, NH = TY + 4, OH = TY + 2;  // U tile + 3, nu tile + 2, omega tile + 1
+  static constexpr int halo = 2 * TY + 2 * kTX3;               // halo columns and rows that stream into the tile
+  // resident blocks per SM the registers are budgeted for (two blocks of 8
+  // rows fit in shared memory only without the reactive field)
+  static constexpr int min_blocks = (TY == 8 && sizeof(R) == 4 && SYS != SYS_REACT) ? 2 : 1;
+};
 
 // The own columns' f^n through one TMA box per plane in FP32.  FP64 (bound by
 // the FP64 pipe) loads it where it is used: the box would not fit beside the
@@ -44,21 +59,23 @@ constexpr bool k3f_f_tma() {
   return sizeof(R) == 4;
 }
 
-template <int M, class R>
+template <int SYS, class R>
 struct Smem3F {
+  static constexpr int M = Fields3<SYS>::M, TY = Tile3F<SYS, R>::TY;
+  static constexpr int UH = Tile3F<SYS, R>::UH, NH = Tile3F<SYS, R>::NH, OH = Tile3F<SYS, R>::OH;
   static constexpr size_t a128(size_t b) { return (b + 127) / 128 * 128; }
-  static constexpr uint32_t u_box = (uint32_t)(M * kUH3 * kUW3 * sizeof(R));  // bytes of one U box
-  static constexpr uint32_t f_box = (uint32_t)(7 * M * kTY3 * kTX3 * sizeof(R));
+  static constexpr uint32_t u_box = (uint32_t)(M * UH * kUW3 * sizeof(R));  // bytes of one U box
+  static constexpr uint32_t f_box = (uint32_t)(7 * M * TY * kTX3 * sizeof(R));
   static constexpr size_t u_slot = a128(u_box);  // TMA destinations start on 128 bytes
   static constexpr size_t f_off = kURing3 * u_slot;
   static constexpr size_t nu_off = f_off + (k3f_f_tma<R>() ? a128(f_box) : 0);
-  static constexpr size_t om_off = nu_off + (size_t)3 * kNH3 * kNW3 * sizeof(R);
-  static constexpr size_t py_off = om_off + (size_t)kOH3 * kOW3 * sizeof(R);
-  static constexpr size_t py_bytes = (size_t)M * (kTY3 + 1) * kTX3 * sizeof(R);
+  static constexpr size_t om_off = nu_off + (size_t)3 * NH * kNW3 * sizeof(R);
+  static constexpr size_t py_off = om_off + (size_t)OH * kOW3 * sizeof(R);
+  static constexpr size_t py_bytes = (size_t)M * (TY + 1) * kTX3 * sizeof(R);
   static constexpr size_t my_off = py_off + py_bytes;
   static constexpr size_t hx_off = my_off + py_bytes;
-  static constexpr size_t hf_off = hx_off + (size_t)2 * M * kTY3 * sizeof(R);
-  static constexpr size_t bar_off = (hf_off + (size_t)kHalo3 * M * sizeof(R) + 7) / 8 * 8;
+  static constexpr size_t hf_off = hx_off + (size_t)2 * M * TY * sizeof(R);
+  static constexpr size_t bar_off = (hf_off + (size_t)Tile3F<SYS, R>::halo * M * sizeof(R) + 7) / 8 * 8;
   // plus 128 bytes of slack: the kernel starts its layout on the first
   // 128-byte boundary of its dynamic shared memory
   static constexpr size_t total = bar_off + (kURing3 + 1) * sizeof(unsigned long long) + 128;
@@ -95,32 +112,30 @@ __device__ __forceinline__ void cp_async_elem(R* dst, const R* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// resident blocks per SM the registers are budgeted for: 2 in FP32 (about
-// 100 KB of shared memory a block), 1 for FP32 reactive Euler (119 KB) and FP64
-template <int SYS, class R>
-constexpr int k3f_min_blocks() { return (sizeof(R) == 4 && SYS != SYS_REACT) ? 2 : 1; }
-
 // tu0/tu1: U copies 0/1 as {ex, ey, ez, m} (rows of G.px elements), boxes
-// {40, 14, 1, m}; tf0/tf1: distribution buffers 0/1 as {pitch, ny * nz, 7 m},
-// boxes {32, 8, 7 m}
+// {40, TY + 6, 1, m}; tf0/tf1: distribution buffers 0/1 as {pitch, ny * nz,
+// 7 m}, boxes {32, TY, 7 m}
 template <int SYS, class R>
-__global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
+__global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_blocks)
     k3_fused(const __grid_constant__ CUtensorMap tu0, const __grid_constant__ CUtensorMap tu1,
              const __grid_constant__ CUtensorMap tf0, const __grid_constant__ CUtensorMap tf1, DevParams P,
              R* const* buf, Ctl* ctl, int slot, ExtGeom3 G, R* Ue2, double* partials, int zc) {
   constexpr int M = Fields3<SYS>::M, Q = 7;
   constexpr bool SRC = SYS == SYS_REACT;
   constexpr bool FBOX = k3f_f_tma<R>();
-  using L = Smem3F<M, R>;
+  using L = Smem3F<SYS, R>;
+  constexpr int TY = Tile3F<SYS, R>::TY, NT = Tile3F<SYS, R>::threads;
+  constexpr int UH = Tile3F<SYS, R>::UH, NH = Tile3F<SYS, R>::NH, OH = Tile3F<SYS, R>::OH;
+  constexpr int NHALO = Tile3F<SYS, R>::halo;
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   unsigned char* const smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
-  const R* fs = (const R*)(smem_raw + L::f_off);  // [7 m][kTY3][kTX3]
-  R* nus = (R*)(smem_raw + L::nu_off);            // [3][kNH3][kNW3]
-  R* oms = (R*)(smem_raw + L::om_off);            // [kOH3][kOW3]
-  R* pys = (R*)(smem_raw + L::py_off);            // [M][kTY3 + 1][kTX3]
-  R* mys = (R*)(smem_raw + L::my_off);            // [M][kTY3 + 1][kTX3]
-  R* hxs = (R*)(smem_raw + L::hx_off);            // [2][M][kTY3]
-  R* hfs = (R*)(smem_raw + L::hf_off);            // [kHalo3][M]
+  const R* fs = (const R*)(smem_raw + L::f_off);  // [7 m][TY][kTX3]
+  R* nus = (R*)(smem_raw + L::nu_off);            // [3][NH][kNW3]
+  R* oms = (R*)(smem_raw + L::om_off);            // [OH][kOW3]
+  R* pys = (R*)(smem_raw + L::py_off);            // [M][TY + 1][kTX3]
+  R* mys = (R*)(smem_raw + L::my_off);            // [M][TY + 1][kTX3]
+  R* hxs = (R*)(smem_raw + L::hx_off);            // [2][M][TY]
+  R* hfs = (R*)(smem_raw + L::hf_off);            // [NHALO][M]
   unsigned long long* bars = (unsigned long long*)(smem_raw + L::bar_off);  // U slots 0..3, f box 4
   __shared__ StepCoef3 s_cf;
   __shared__ R s_k[9];  // a0, 1/(2 lambda), dt/2, alpha_0..2, a_1..3
@@ -168,7 +183,7 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
   else
     om_fixed = P.omega_fixed;
 
-  const int x0 = blockIdx.x * kTX3, y0 = blockIdx.y * kTY3;
+  const int x0 = blockIdx.x * kTX3, y0 = blockIdx.y * TY;
   const int zb = blockIdx.z * zc, ze = min(zb + zc, P.nz3);
   const int x = x0 + tx, y = y0 + ty;
   const bool own_valid = x < P.nx && y < P.ny3;
@@ -190,13 +205,13 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
                   L::f_box);
   };
 
-  // this thread's halo node (t < kHalo3): the one direction qq (along dir) it
+  // this thread's halo node (t < NHALO): the one direction qq (along dir) it
   // streams into the tile
   int hx = 0, hy = 0, hq = 0, hdir = 0;
-  if (t < kTY3) { hx = -1; hy = t; hq = 1; hdir = 0; }
-  else if (t < 2 * kTY3) { hx = kTX3; hy = t - kTY3; hq = 4; hdir = 0; }
-  else if (t < 2 * kTY3 + kTX3) { hx = t - 2 * kTY3; hy = -1; hq = 2; hdir = 1; }
-  else if (t < kHalo3) { hx = t - 2 * kTY3 - kTX3; hy = kTY3; hq = 5; hdir = 1; }
+  if (t < TY) { hx = -1; hy = t; hq = 1; hdir = 0; }
+  else if (t < 2 * TY) { hx = kTX3; hy = t - TY; hq = 4; hdir = 0; }
+  else if (t < 2 * TY + kTX3) { hx = t - 2 * TY; hy = -1; hq = 2; hdir = 1; }
+  else if (t < NHALO) { hx = t - 2 * TY - kTX3; hy = TY; hq = 5; hdir = 1; }
   const int hmx = map_index(x0 + hx, P.nx, P.bc[0], P.bc[1]), hmy = map_index(y0 + hy, P.ny3, P.bc[2], P.bc[3]);
 
   R sp0 = R(0), sp1 = R(0), sp2 = R(0);
@@ -242,7 +257,7 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
     const bool posts = q >= zb + 1;
     const int pp = q - 2;  // plane of this iteration's posts
     const int mk = map_index(pp, P.nz3, P.bc_z[0], P.bc_z[1]);
-    if (posts && t < kHalo3) {  // the halo node's f^n of its direction, for phase 3
+    if (posts && t < NHALO) {  // the halo node's f^n of its direction, for phase 3
       const long long off = cell3(P, hmx, hmy, mk);
 #pragma unroll
       for (int c = 0; c < M; c++)
@@ -256,11 +271,11 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
       const R* Um1 = uslot(q - 2);
       const R* U00 = uslot(q - 1);
       const R* Up1 = uslot(q);
-      R* nd = nus + (size_t)(((q - 1) % 3 + 3) % 3) * kNH3 * kNW3;
-      for (int it = t; it < kNH3 * kNW3; it += kThreads3F) {
+      R* nd = nus + (size_t)(((q - 1) % 3 + 3) % 3) * NH * kNW3;
+      for (int it = t; it < NH * kNW3; it += NT) {
         const int iy = it / kNW3, ix = it % kNW3;
         const int o = (iy + 1) * kUW3 + (ix + 1);  // position in the U tile
-        constexpr int CS = kUH3 * kUW3;
+        constexpr int CS = UH * kUW3;
         R U0[M], dm[M], dp[M];
 #pragma unroll
         for (int c = 0; c < M; c++) U0[c] = U00[c * CS + o];
@@ -285,8 +300,8 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
     if (q >= zb + 1) {
       const R* nb[3];
 #pragma unroll
-      for (int pz = 0; pz < 3; pz++) nb[pz] = nus + (size_t)(((q - 3 + pz) % 3 + 3) % 3) * kNH3 * kNW3;
-      for (int it = t; it < kOH3 * kOW3; it += kThreads3F) {
+      for (int pz = 0; pz < 3; pz++) nb[pz] = nus + (size_t)(((q - 3 + pz) % 3 + 3) % 3) * NH * kNW3;
+      for (int it = t; it < OH * kOW3; it += NT) {
         const int jy = it / kOW3, jx = it % kOW3;
         R w;
         if (fixed_omega) {
@@ -308,7 +323,7 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
     if (posts) {
       // 3: posts of plane pp = q - 2
       const R* Ut = uslot(pp);
-      constexpr int CS = kUH3 * kUW3;
+      constexpr int CS = UH * kUW3;
       // own column: all seven directions
       R pown[Q][M];
       {
@@ -329,7 +344,7 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
 #pragma unroll
             for (int k = 0; k < Q; k++)
 #pragma unroll
-              for (int c = 0; c < M; c++) fq[k][c] = fs[(k * M + c) * (kTY3 * kTX3) + ty * kTX3 + tx];
+              for (int c = 0; c < M; c++) fq[k][c] = fs[(k * M + c) * (TY * kTX3) + ty * kTX3 + tx];
           } else {  // a lane past the lattice's edge (ragged tile): its ghost node is the mapped node
             const long long off = cell3(P, mx, my, mk);
 #pragma unroll
@@ -375,11 +390,11 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
       }
 #pragma unroll
       for (int c = 0; c < M; c++) {
-        pys[(c * (kTY3 + 1) + ty + 1) * kTX3 + tx] = pown[2][c];
-        mys[(c * (kTY3 + 1) + ty) * kTX3 + tx] = pown[5][c];
+        pys[(c * (TY + 1) + ty + 1) * kTX3 + tx] = pown[2][c];
+        mys[(c * (TY + 1) + ty) * kTX3 + tx] = pown[5][c];
       }
       // halo: the one direction each halo column / row streams into the tile
-      if (t < kHalo3) {
+      if (t < NHALO) {
         cp_async_wait_all();  // this thread's own copies of its halo f^n
         const int o = (hy + 3) * kUW3 + (hx + 3);
         R U[M], fq[M], S[M], F[M];
@@ -396,8 +411,8 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
 #pragma unroll
           for (int c = 0; c < M; c++) S[c] = R(0);
         flux3<SYS, R>(K, P, U, pw, hdir, F);
-        R* dst = hq == 1 ? hxs + hy : (hq == 4 ? hxs + M * kTY3 + hy : (hq == 2 ? pys + hx : mys + kTY3 * kTX3 + hx));
-        const int cstride = (hq == 1 || hq == 4) ? kTY3 : (kTY3 + 1) * kTX3;
+        R* dst = hq == 1 ? hxs + hy : (hq == 4 ? hxs + M * TY + hy : (hq == 2 ? pys + hx : mys + TY * kTX3 + hx));
+        const int cstride = (hq == 1 || hq == 4) ? TY : (TY + 1) * kTX3;
 #pragma unroll
         for (int c = 0; c < M; c++) {
           const R feq = hq <= 3 ? (al[hdir] * U[c] + F[c]) * inv2l : (al[hdir] * U[c] - F[c]) * inv2l;
@@ -480,10 +495,10 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
       for (int c = 0; c < M; c++) {
         const R left = __shfl_up_sync(0xffffffffu, pown[1][c], 1);
         const R right = __shfl_down_sync(0xffffffffu, pown[4][c], 1);
-        kxp[c] = tx == 0 ? hxs[c * kTY3 + ty] : left;
-        kxm[c] = tx == 31 ? hxs[(M + c) * kTY3 + ty] : right;
-        kyp[c] = pys[(c * (kTY3 + 1) + ty) * kTX3 + tx];
-        kym[c] = mys[(c * (kTY3 + 1) + ty + 1) * kTX3 + tx];
+        kxp[c] = tx == 0 ? hxs[c * TY + ty] : left;
+        kxm[c] = tx == 31 ? hxs[(M + c) * TY + ty] : right;
+        kyp[c] = pys[(c * (TY + 1) + ty) * kTX3 + tx];
+        kym[c] = mys[(c * (TY + 1) + ty + 1) * kTX3 + tx];
         kp0[c] = pown[0][c];
         pz2[c] = pz1[c];
         pz1[c] = pown[3][c];
@@ -501,19 +516,20 @@ __global__ void __launch_bounds__(kThreads3F, k3f_min_blocks<SYS, R>())
   if (s_abort) st |= ST_TIMEOUT;
   // side outputs per warp (partial slot bid * 8 + warp): no block barrier
   warp_side_outputs3<M, R>(sp0, sp1, sp2, acc, ctl, (slot + 1) % 3,
-                           partials + (bid * (kThreads3F / 32) + ty) * M, st);
+                           partials + (bid * (NT / 32) + ty) * M, st);
   if (bid == 0 && t == 0) advance_ctl3(ctl, slot, cf);
 }
 
-// launch shape of the fused 3D step: tiles of 32 x 8 columns, chunks of zc planes
-inline dim3 grid3_fused(int nx, int ny, int nz, int zc) {
-  return dim3((unsigned)((nx + kTX3 - 1) / kTX3), (unsigned)((ny + kTY3 - 1) / kTY3), (unsigned)((nz + zc - 1) / zc));
+// launch shape of the fused 3D step: tiles of 32 x ty columns, chunks of zc planes
+inline dim3 grid3_fused(int nx, int ny, int nz, int ty, int zc) {
+  return dim3((unsigned)((nx + kTX3 - 1) / kTX3), (unsigned)((ny + ty - 1) / ty), (unsigned)((nz + zc - 1) / zc));
 }
 
 // TMA descriptors of the fused 3D step: both U copies of the ghost-extended
 // grid and both distribution buffers (layouts as described at k3_fused)
-template <int M, class R>
+template <int SYS, class R>
 inline int k3f_encode_maps(FusedPlan& fp, const DevParams& P, const ExtGeom3& G, void* Ue2, void* const* fbuf) {
+  constexpr int M = Fields3<SYS>::M, TY = Tile3F<SYS, R>::TY;
   EncodeTiledFn enc = encode_fn();
   if (!enc) return -1;
   const CUtensorMapDataType dt = sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
@@ -521,7 +537,7 @@ inline int k3f_encode_maps(FusedPlan& fp, const DevParams& P, const ExtGeom3& G,
   for (int b = 0; b < 2; b++) {
     cuuint64_t udims[4] = {(cuuint64_t)G.ex, (cuuint64_t)G.ey, (cuuint64_t)G.ez, (cuuint64_t)M};
     cuuint64_t ustr[3] = {(cuuint64_t)G.px * s, (cuuint64_t)G.px * G.ey * s, (cuuint64_t)G.size() * s};
-    cuuint32_t ubox[4] = {(cuuint32_t)kUW3, (cuuint32_t)kUH3, 1u, (cuuint32_t)M};
+    cuuint32_t ubox[4] = {(cuuint32_t)kUW3, (cuuint32_t)Tile3F<SYS, R>::UH, 1u, (cuuint32_t)M};
     cuuint32_t e4[4] = {1u, 1u, 1u, 1u};
     CUresult r = enc(&fp.tu3[b], dt, 4, (R*)Ue2 + (size_t)b * M * G.size(), udims, ustr, ubox, e4,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
@@ -529,7 +545,7 @@ inline int k3f_encode_maps(FusedPlan& fp, const DevParams& P, const ExtGeom3& G,
     if (r != CUDA_SUCCESS) return -1;
     cuuint64_t fdims[3] = {(cuuint64_t)P.pitch, (cuuint64_t)P.ny, (cuuint64_t)(7 * M)};
     cuuint64_t fstr[2] = {(cuuint64_t)P.pitch * s, (cuuint64_t)P.plane * s};
-    cuuint32_t fbox[3] = {(cuuint32_t)kTX3, (cuuint32_t)kTY3, (cuuint32_t)(7 * M)};
+    cuuint32_t fbox[3] = {(cuuint32_t)kTX3, (cuuint32_t)TY, (cuuint32_t)(7 * M)};
     cuuint32_t e3[3] = {1u, 1u, 1u};
     r = enc(&fp.tf3[b], dt, 3, fbuf[b], fdims, fstr, fbox, e3, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

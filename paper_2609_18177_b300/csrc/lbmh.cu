@@ -234,13 +234,14 @@ struct Impl3 {
       k3_moments_ext<SYS, R><<<ge, kBlock3, 0, h->stream>>>(P, buf, h->ctl, slot, G, (R*)h->Ue);
     }
     if (h->kernel == LBMH_KERNEL_FUSED) {  // indicator, omega, collision and streaming in one pass
+      using T3 = Tile3F<SYS, R>;
       const int zc = h->fp.band;
-      const dim3 gf = grid3_fused(P.nx, P.ny3, P.nz3, zc);
-      k3_fused<SYS, R><<<gf, kThreads3F, h->fp.smem, h->stream>>>(h->fp.tu3[0], h->fp.tu3[1], h->fp.tf3[0],
-                                                                  h->fp.tf3[1], P, buf, h->ctl, slot, G, (R*)h->Ue,
-                                                                  h->partials, zc);
+      const dim3 gf = grid3_fused(P.nx, P.ny3, P.nz3, T3::TY, zc);
+      k3_fused<SYS, R><<<gf, T3::threads, h->fp.smem, h->stream>>>(h->fp.tu3[0], h->fp.tu3[1], h->fp.tf3[0],
+                                                                   h->fp.tf3[1], P, buf, h->ctl, slot, G, (R*)h->Ue,
+                                                                   h->partials, zc);
       h->u3_valid = true;
-      h->nblocks = (int)(gf.x * gf.y * gf.z) * (kThreads3F / 32);
+      h->nblocks = (int)(gf.x * gf.y * gf.z) * (T3::threads / 32);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_fail(h, e, "3D fused step launch");
       return LBMH_OK;
@@ -308,12 +309,14 @@ struct Impl3 {
   // the fused step's shared memory, z chunk (planes a block marches; at least
   // 8; LBMH_3D_ZCHUNK overrides it for tuning runs) and partial-sum slots
   static int setup_fused(lbmh_handle* h) {
-    using L = Smem3F<M, R>;
+    using L = Smem3F<SYS, R>;
+    using T3 = Tile3F<SYS, R>;
     auto kern = k3_fused<SYS, R>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::total) != cudaSuccess)
       return -1;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads3F, L::total) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T3::threads, L::total) != cudaSuccess ||
+        per_sm < 1)
       return -1;
     int zc = 32;
     const char* e = getenv("LBMH_3D_ZCHUNK");
@@ -321,14 +324,14 @@ struct Impl3 {
     // the U boxes read the ghost-extended copies: allocated here (the two U
     // copies only), then described to the TMA unit
     if (ensure_scratch(h) != LBMH_OK) return -1;
-    if (k3f_encode_maps<M, R>(h->fp, h->P, geom(h), h->Ue, h->fbuf) != 0) {
+    if (k3f_encode_maps<SYS, R>(h->fp, h->P, geom(h), h->Ue, h->fbuf) != 0) {
       free_scratch(h);
       return -1;
     }
     h->fp.smem = (int)L::total;
     h->fp.band = zc;
-    const dim3 g = grid3_fused(h->P.nx, h->P.ny3, h->P.nz3, zc);
-    h->fp.blocks = (int)(g.x * g.y * g.z) * (kThreads3F / 32);
+    const dim3 g = grid3_fused(h->P.nx, h->P.ny3, h->P.nz3, T3::TY, zc);
+    h->fp.blocks = (int)(g.x * g.y * g.z) * (T3::threads / 32);
     return 0;
   }
 
