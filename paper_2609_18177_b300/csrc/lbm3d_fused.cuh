@@ -264,8 +264,8 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
         cp_async_elem(hfs + t * M + c, f + chk((long long)(hq * M + c) * P.plane + off, nf, stc));
       cp_async_commit();
     }
-    __syncthreads();  // U(q) landed for every thread (or the CTA stops here)
-    if (s_abort) break;
+    // no block barrier here: each thread waited for U(q) itself, and every
+    // buffer phase 1 writes was last read before the previous plane's barriers
     // 1: nu(q - 1) on the tile + 2
     if (q >= zb - 1) {
       const R* Um1 = uslot(q - 2);
@@ -296,6 +296,7 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
       }
     }
     __syncthreads();
+    if (s_abort) break;  // a wait gave up (set before this barrier, read by all after it)
     // 2: omega(q - 2) on the tile + 1 (27 terms in the order (bk, bj, bi))
     if (q >= zb + 1) {
       const R* nb[3];
