@@ -103,6 +103,30 @@ def test_batch_fp64_matches_oracle():
     b.close()
 
 
+def test_fp32_batched_dam_break_to_T_meets_the_contract_against_the_oracle():
+    """The batched workload's smallest sampled lattice (n = 274, seed 0 of the
+    256-lattice recipe) in an FP32 batch beside two other dam breaks, to
+    T = 0.1 (271 steps), against the FP64 oracle run as many steps: the
+    accuracy contract's norm within the shallow-water tolerance."""
+    from paper_2609_18177_b300 import accuracy as A
+    cases = [W.dam_break_bump(n) for n in (274, 97, 160)]
+    cap = sum(lbmh.Batch.footprint(pb, lbmh.FP32) for pb, _ in cases) + (8 << 20)
+    b = lbmh.Batch(W.SWE, precision=lbmh.FP32, capacity_bytes=cap, max_instances=4)
+    slots = [b.add(pb.with_(precision=lbmh.FP32), U0, T=0.1) for pb, U0 in cases]
+    while True:
+        b.step(30)
+        done, t, steps, status = b.poll()
+        if all(done[s] == 1 for s in slots):
+            break
+    pb, U0 = cases[0]
+    nsteps = int(steps[slots[0]])
+    assert 260 <= nsteps <= 280 and t[slots[0]] >= 0.1, (nsteps, t[slots[0]])
+    r = oracle.Run(pb, U0).step(nsteps)  # the same number of steps (dt from each path's own speed bound)
+    err = A.contract_l1(b.moments(slots[0]), r.moments(), pb.system, pb.dim)
+    assert err["max"] <= A.tolerance(W.SWE), err
+    b.close()
+
+
 def test_step_targets_end_times_and_poll():
     b = lbmh.Batch(W.EULER, precision=lbmh.FP32, capacity_bytes=1 << 27, max_instances=8)
     pb, U0 = W.riemann_2d_seeded(80, seed=4)

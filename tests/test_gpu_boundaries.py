@@ -3,11 +3,14 @@ Example 5.13) on the fused CUDA path against the FP64 oracle: every system,
 1D and 2D, grids wider than one 120-column strip, corners where two kinds of
 side meet; the Example 5.13 lattice itself at reduced size, alone and in a
 batch.  FP64: relative max error <= 1e-12 per field; FP32: relative L1 <=
-2e-5 and relative max <= 5e-4 (the bars of the other parity tests)."""
+2e-5 in the accuracy contract's norm (momentum as one vector per node: the
+y-momentum of Example 5.13, whose front runs along x, is nearly zero, and a
+per-component L1 would divide by that) and relative max <= 5e-4 per field."""
 import numpy as np
 import pytest
 
 import oracle
+from paper_2609_18177_b300 import accuracy as A
 from paper_2609_18177_b300 import lbmh
 from paper_2609_18177_b300 import workloads as W
 
@@ -31,18 +34,12 @@ def rel_max(g, o):
     return np.abs(g2 - o2).max(axis=1) / np.where(s > 0, s, 1.0)
 
 
-def rel_l1(g, o):
-    m = o.shape[0]
-    g2, o2 = g.reshape(m, -1), o.reshape(m, -1)
-    s = np.abs(o2).sum(axis=1)
-    return np.abs(g2 - o2).sum(axis=1) / np.where(s > 0, s, 1.0)
-
-
-def check(Ug, Uo, precision, where):
+def check(Ug, Uo, precision, where, system, dim):
     if precision == lbmh.FP64:
         assert np.all(rel_max(Ug, Uo) <= FP64_TOL), (where, rel_max(Ug, Uo))
     else:
-        assert np.all(rel_l1(Ug, Uo) <= FP32_L1), (where, rel_l1(Ug, Uo))
+        err = A.contract_l1(Ug, Uo, system, dim)
+        assert err["max"] <= FP32_L1, (where, err)
         assert np.all(rel_max(Ug, Uo) <= FP32_MAX), (where, rel_max(Ug, Uo))
 
 
@@ -84,7 +81,7 @@ def test_boundaries_match_oracle(system, dim, bc, sponge, precision):
     for n in range(4):
         r.step(5)
         s.step(5)
-        check(s.moments(), r.moments(), precision, 5 * (n + 1))
+        check(s.moments(), r.moments(), precision, 5 * (n + 1), system, dim)
     s.close()
 
 
@@ -105,7 +102,7 @@ def test_cellular_detonation_reduced(precision):
     for n in range(3):
         r.step(10)
         s.step(10)
-        check(s.moments(), r.moments(), precision, 10 * (n + 1))
+        check(s.moments(), r.moments(), precision, 10 * (n + 1), pb.system, pb.dim)
         assert s.info()["status"] & 1 == 0
     s.close()
 
