@@ -9,7 +9,8 @@
 // of round trips through global nu and omega arrays.  Per plane q:
 //   U(q) on the tile + 3 arrives (one TMA box, one plane ahead) in a ring of 4
 //   1  nu(q-1) on the tile + 2 from U(q-2..q)         (ring of 3 nu planes)
-//   2  omega(q-2) on the tile + 1 from nu(q-3..q-1)
+//   2  omega(q-2) on the tile + 1 from nu(q-3..q-1), by the thread whose post
+//      needs it (own column, or the halo node it streams from)
 //   3  posts of plane q-2: every direction at the tile's own columns, the one
 //      direction each halo column or row streams into the tile
 //   4  plane q-3 streamed (F_k(x) = post_k(x - e_k), Eq. 2.2), the implicit
@@ -32,7 +33,6 @@ namespace lbmh {
 constexpr int kTX3 = 32;
 constexpr int kUW3 = kTX3 + 8;  // U tile + 3 (38 columns used), loaded as a 40-column box
 constexpr int kNW3 = kTX3 + 4;  // nu tile + 2
-constexpr int kOW3 = kTX3 + 2;  // omega tile + 1
 constexpr int kURing3 = 4;
 
 // Tile height (rows of 32 columns; one warp per row).  8 rows, 256 threads.
@@ -44,7 +44,7 @@ template <int SYS, class R>
 struct Tile3F {
   static constexpr int TY = 8;
   static constexpr int threads = kTX3 * TY;
-  static constexpr int UH = TY + 6, NH = TY + 4, OH = TY + 2;  // U tile + 3, nu tile + 2, omega tile + 1
+  static constexpr int UH = TY + 6, NH = TY + 4;  // U tile + 3, nu tile + 2
   static constexpr int halo = 2 * TY + 2 * kTX3;               // halo columns and rows that stream into the tile
   // resident blocks per SM the registers are budgeted for (two blocks of 8
   // rows fit in shared memory only without the reactive field)
@@ -62,15 +62,14 @@ constexpr bool k3f_f_tma() {
 template <int SYS, class R>
 struct Smem3F {
   static constexpr int M = Fields3<SYS>::M, TY = Tile3F<SYS, R>::TY;
-  static constexpr int UH = Tile3F<SYS, R>::UH, NH = Tile3F<SYS, R>::NH, OH = Tile3F<SYS, R>::OH;
+  static constexpr int UH = Tile3F<SYS, R>::UH, NH = Tile3F<SYS, R>::NH;
   static constexpr size_t a128(size_t b) { return (b + 127) / 128 * 128; }
   static constexpr uint32_t u_box = (uint32_t)(M * UH * kUW3 * sizeof(R));  // bytes of one U box
   static constexpr uint32_t f_box = (uint32_t)(7 * M * TY * kTX3 * sizeof(R));
   static constexpr size_t u_slot = a128(u_box);  // TMA destinations start on 128 bytes
   static constexpr size_t f_off = kURing3 * u_slot;
   static constexpr size_t nu_off = f_off + (k3f_f_tma<R>() ? a128(f_box) : 0);
-  static constexpr size_t om_off = nu_off + (size_t)3 * NH * kNW3 * sizeof(R);
-  static constexpr size_t py_off = om_off + (size_t)OH * kOW3 * sizeof(R);
+  static constexpr size_t py_off = nu_off + (size_t)3 * NH * kNW3 * sizeof(R);
   static constexpr size_t py_bytes = (size_t)M * (TY + 1) * kTX3 * sizeof(R);
   static constexpr size_t my_off = py_off + py_bytes;
   static constexpr size_t hx_off = my_off + py_bytes;
@@ -125,13 +124,12 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
   constexpr bool FBOX = k3f_f_tma<R>();
   using L = Smem3F<SYS, R>;
   constexpr int TY = Tile3F<SYS, R>::TY, NT = Tile3F<SYS, R>::threads;
-  constexpr int UH = Tile3F<SYS, R>::UH, NH = Tile3F<SYS, R>::NH, OH = Tile3F<SYS, R>::OH;
+  constexpr int UH = Tile3F<SYS, R>::UH, NH = Tile3F<SYS, R>::NH;
   constexpr int NHALO = Tile3F<SYS, R>::halo;
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   unsigned char* const smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
   const R* fs = (const R*)(smem_raw + L::f_off);  // [7 m][TY][kTX3]
   R* nus = (R*)(smem_raw + L::nu_off);            // [3][NH][kNW3]
-  R* oms = (R*)(smem_raw + L::om_off);            // [OH][kOW3]
   R* pys = (R*)(smem_raw + L::py_off);            // [M][TY + 1][kTX3]
   R* mys = (R*)(smem_raw + L::my_off);            // [M][TY + 1][kTX3]
   R* hxs = (R*)(smem_raw + L::hx_off);            // [2][M][TY]
@@ -297,30 +295,23 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
     }
     __syncthreads();
     if (s_abort) break;  // a wait gave up (set before this barrier, read by all after it)
-    // 2: omega(q - 2) on the tile + 1 (27 terms in the order (bk, bj, bi))
-    if (q >= zb + 1) {
-      const R* nb[3];
+    // 2: omega(q - 2) at a position (jy, jx) of the tile + 1, by the thread
+    // whose post needs it (27 terms in the order (bk, bj, bi)): no shared
+    // omega plane and no barrier of its own
+    const R* nb[3];
 #pragma unroll
-      for (int pz = 0; pz < 3; pz++) nb[pz] = nus + (size_t)(((q - 3 + pz) % 3 + 3) % 3) * NH * kNW3;
-      for (int it = t; it < OH * kOW3; it += NT) {
-        const int jy = it / kOW3, jx = it % kOW3;
-        R w;
-        if (fixed_omega) {
-          w = om_fixed;
-        } else {
-          R s = R(0);
+    for (int pz = 0; pz < 3; pz++) nb[pz] = nus + (size_t)(((q - 3 + pz) % 3 + 3) % 3) * NH * kNW3;
+    auto omega_at = [&](int jy, int jx) -> R {
+      if (fixed_omega) return om_fixed;
+      R s = R(0);
 #pragma unroll
-          for (int pz = 0; pz < 3; pz++)
+      for (int pz = 0; pz < 3; pz++)
 #pragma unroll
-            for (int bj = 0; bj < 3; bj++)
+        for (int bj = 0; bj < 3; bj++)
 #pragma unroll
-              for (int bi = 0; bi < 3; bi++) s += nb[pz][(jy + bj) * kNW3 + jx + bi];
-          w = R(1) + fdiv(R(1), R(1) + s);
-        }
-        oms[it] = w;
-      }
-    }
-    __syncthreads();
+          for (int bi = 0; bi < 3; bi++) s += nb[pz][(jy + bj) * kNW3 + jx + bi];
+      return R(1) + fdiv(R(1), R(1) + s);
+    };
     if (posts) {
       // 3: posts of plane pp = q - 2
       const R* Ut = uslot(pp);
@@ -332,7 +323,7 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
         const int o = (ty + 3) * kUW3 + (tx + 3);
 #pragma unroll
         for (int c = 0; c < M; c++) U[c] = Ut[c * CS + o];
-        const R w = oms[(ty + 1) * kOW3 + (tx + 1)];
+        const R w = omega_at(ty + 1, tx + 1);
         if constexpr (FBOX) {
           const bool fgot = mbar_wait_bounded(smem_u32(&bars[kURing3]), f_waits & 1u);
           f_waits++;
@@ -404,7 +395,7 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
           U[c] = Ut[c * CS + o];
           fq[c] = hfs[t * M + c];
         }
-        const R w = oms[(hy + 1) * kOW3 + (hx + 1)];
+        const R w = omega_at(hy + 1, hx + 1);
         const Prim3<R> pw = prim3<SYS, R>(K, U);
         if constexpr (SRC)
           source3<SYS, R>(K, U, S);
