@@ -1,12 +1,12 @@
 // Fused 3D (D3Q7) step: one kernel per step after the ghost layers of U.
 //
 // A block of 32 x TY threads owns a tile of 32 x TY output columns (x, y) and
-// marches a chunk of planes along z (TY = 8, Tile3F).  The only state read from global memory
-// besides the distributions is U^n on the ghost-extended grid (written as a
-// side product by the previous step, its ghost layers refilled before this
-// kernel); the indicator (Eq. 2.13/2.14), its 27-point box sum and omega
-// (Eq. 2.15/2.16) are computed in shared memory as the tile marches, instead
-// of round trips through global nu and omega arrays.  Per plane q:
+// marches a chunk of planes along z (TY = 8, Tile3F).  The only state read
+// from global memory besides the distributions is U^n on the ghost-extended
+// grid (written as a side product by the previous step, its ghost layers
+// refilled before this kernel); the indicator (Eq. 2.13/2.14), its 27-point
+// box sum and omega (Eq. 2.15/2.16) are computed on chip as the tile marches,
+// instead of round trips through global nu and omega arrays.  Per plane q:
 //   U(q) on the tile + 3 arrives (one TMA box, one plane ahead) in a ring of 4
 //   1  nu(q-1) on the tile + 2 from U(q-2..q)         (ring of 3 nu planes)
 //   2  omega(q-2) on the tile + 1 from nu(q-3..q-1), by the thread whose post
@@ -20,9 +20,9 @@
 // phases 1 and 2 of the next plane run (lanes of a ragged tile past the
 // lattice's edge hold ghost nodes: they load the mapped node's f^n instead);
 // the halo nodes' f^n (one direction each) is copied with cp.async at the
-// start of the plane.  Sideways posts
-// pass between lanes by warp shuffles (x) and shared memory (y, and the
-// halo); the +-z posts stay in the thread's registers.  Every node's values
+// start of the plane.  Sideways posts pass between lanes by warp shuffles (x)
+// and shared memory (y, and the halo); the +-z posts stay in the thread's
+// registers.  Every node's values
 // are those of the four-kernel path (the same expressions in the same order),
 // so the two paths agree to rounding.
 #pragma once
@@ -45,7 +45,7 @@ struct Tile3F {
   static constexpr int TY = 8;
   static constexpr int threads = kTX3 * TY;
   static constexpr int UH = TY + 6, NH = TY + 4;  // U tile + 3, nu tile + 2
-  static constexpr int halo = 2 * TY + 2 * kTX3;               // halo columns and rows that stream into the tile
+  static constexpr int halo = 2 * TY + 2 * kTX3;  // halo columns and rows that stream into the tile
   // resident blocks per SM the registers are budgeted for (two blocks of 8
   // rows fit in shared memory only without the reactive field)
   static constexpr int min_blocks = (TY == 8 && sizeof(R) == 4 && SYS != SYS_REACT) ? 2 : 1;
