@@ -557,12 +557,12 @@ def run_lines1d(args):
                     "us_per_step": ms * 1e3 / steps, "mlups": pb.nodes * steps / (ms / 1e3) / 1e6,
                     "l2_gbs": bytes_step * steps / (ms / 1e3) / 1e9, "status": st})
     # accuracy at the examples' end times: the FP32 result against the FP64
-    # path (pinned to the oracle by the GPU tests) in the contract's norm, for
-    # the lattices whose FP64 run to T takes seconds (n <= 2^16)
+    # path (pinned to the oracle by the GPU tests) in the contract's norm, every
+    # size (the FP64 runs to T at 2^18 nodes take about two minutes)
     from paper_2609_18177_b300 import accuracy as A
     acc = []
     if not args.no_accuracy and not args.case:
-        for n in (1 << 12, 1 << 14, 1 << 16):
+        for n in (1 << 12, 1 << 14, 1 << 16, 1 << 18):
             for name, gen, T in (("sod", W.sod, 0.2), ("shu-osher", W.shu_osher, 1.8)):
                 pb, U0 = gen(n)
                 res = {}

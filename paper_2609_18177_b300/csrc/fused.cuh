@@ -757,7 +757,7 @@ __global__ void __launch_bounds__(FT) k_fused2d(const __grid_constant__ CUtensor
 // Coefficients of one 1D step in the path's type, computed by one thread
 template <class R>
 struct Coef1D {
-  R a0, a1, inv2l, hdt, al0, om_fixed;
+  R a0, a0lo, a1, inv2l, hdt, al0, om_fixed;  // a0 + a0lo: the rest coefficient (rest_coef)
   double dt;
 };
 
@@ -781,11 +781,13 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
     if (!cf.active) {
       if (blockIdx.x == 0) advance_ctl<1>(ctl, slot, cf);
     } else {
-      s_cf.a0 = R(cf.a0);
       s_cf.a1 = R(cf.aj[0]);
       s_cf.inv2l = R(1.0 / (2.0 * cf.lam));
       s_cf.hdt = R(0.5 * cf.dt);
       s_cf.al0 = R(cf.alpha[0]);
+      const RestCoef<R> rc = rest_coef<R>(cf.a0, &s_cf.al0, 1, s_cf.inv2l);
+      s_cf.a0 = rc.hi;
+      s_cf.a0lo = rc.lo;
       if constexpr (sizeof(R) == 4)
         s_cf.om_fixed = P.pf.omega_fixed;
       else
@@ -801,7 +803,7 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
   const Phys<R> K = make_phys<R>(P);
   const R* fin = buf[s_par];
   R* fout = buf[s_par ^ 1];
-  const R a0 = cf.a0, a1 = cf.a1, inv2l = cf.inv2l, hdt = cf.hdt, al0 = cf.al0;
+  const R a0 = cf.a0, a0lo = cf.a0lo, a1 = cf.a1, inv2l = cf.inv2l, hdt = cf.hdt, al0 = cf.al0;
   const bool fixed_omega = P.omega_mode == 1;
   R sp0 = R(0);
   Acc<R> acc[M];
@@ -851,7 +853,7 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
     if constexpr (SRC) source<SYS, 1, R>(K, U, K.xb + R(pos_index(gx, P.nx, P.bc[0], P.bc[1])) * K.dx, R(0), S);
 #pragma unroll
     for (int c = 0; c < M; c++) {
-      R feq0 = a0 * U[c], feq1 = (al0 * U[c] + F[c]) * inv2l, feq2 = (al0 * U[c] - F[c]) * inv2l;
+      R feq0 = rest_eq(a0, a0lo, U[c]), feq1 = (al0 * U[c] + F[c]) * inv2l, feq2 = (al0 * U[c] - F[c]) * inv2l;
       post0[c] = f[0][c] - om * (f[0][c] - feq0);
       R q1 = f[1][c] - om * (f[1][c] - feq1), q2 = f[2][c] - om * (f[2][c] - feq2);
       if constexpr (SRC) {

@@ -264,7 +264,9 @@ __global__ void __launch_bounds__(kBlock) k3_init_eq(DevParams P, const double* 
   const double dt = P.cfl * P.dx / (ab[0] + ab[1] + ab[2]);
   const double lam = P.dx / dt;
   const double al[3] = {ab[0] + P.eps, ab[1] + P.eps, ab[2] + P.eps};
-  const R a0 = R(1.0 - (al[0] + al[1] + al[2]) / lam), inv2l = R(1.0 / (2.0 * lam));
+  const R inv2l = R(1.0 / (2.0 * lam));
+  const R alr[3] = {R(al[0]), R(al[1]), R(al[2])};
+  const RestCoef<R> rc = rest_coef<R>(1.0 - (al[0] + al[1] + al[2]) / lam, alr, 3, inv2l);
   const Phys<R> K = make_phys<R>(P);
   const long long nf = 7ll * M * P.plane;  // elements of the distributions (index guards)
   double s[3] = {0.0, 0.0, 0.0};
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(kBlock) k3_init_eq(DevParams P, const double* 
     for (int c = 0; c < M; c++) U[c] = R(U0[c * nn + node]);
     const Prim3<R> w = prim3<SYS, R>(K, U);
 #pragma unroll
-    for (int c = 0; c < M; c++) f[chk((long long)c * P.plane + off, nf, &ctl->status)] = a0 * U[c];
+    for (int c = 0; c < M; c++) f[chk((long long)c * P.plane + off, nf, &ctl->status)] = rest_eq(rc.hi, rc.lo, U[c]);
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       R F[M];
@@ -644,8 +646,8 @@ struct K3Occupancy {
 // with half the source)
 template <int SYS, class R>
 __device__ __forceinline__ void post_q(const Phys<R>& K, const DevParams& P, const R* U, const Prim3<R>& pw,
-                                       const R* S, R w, const R* fq, int q, R a0, R alq, R akq, R inv2l, R hdt,
-                                       R* out) {
+                                       const R* S, R w, const R* fq, int q, R a0, R a0lo, R alq, R akq, R inv2l,
+                                       R hdt, R* out) {
   constexpr int M = Fields3<SYS>::M;
   R F[M];
 #pragma unroll
@@ -653,7 +655,7 @@ __device__ __forceinline__ void post_q(const Phys<R>& K, const DevParams& P, con
   if (q != 0) flux3<SYS, R>(K, P, U, pw, (q - 1) % 3, F);
 #pragma unroll
   for (int c = 0; c < M; c++) {
-    const R feq = q == 0 ? a0 * U[c] : (q <= 3 ? (alq * U[c] + F[c]) * inv2l : (alq * U[c] - F[c]) * inv2l);
+    const R feq = q == 0 ? rest_eq(a0, a0lo, U[c]) : (q <= 3 ? (alq * U[c] + F[c]) * inv2l : (alq * U[c] - F[c]) * inv2l);
     R v = fq[c] - w * (fq[c] - feq);
     if constexpr (SYS == SYS_REACT) v += hdt * akq * S[c];
     out[c] = v;
@@ -687,7 +689,7 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks))
   constexpr bool SRC = SYS == SYS_REACT;
   // step coefficients (FP64) and their conversions, by one thread per block
   __shared__ StepCoef3 s_cf;
-  __shared__ R s_k[9];  // a0, 1/(2 lambda), dt/2, alpha_0..2, a_1..3
+  __shared__ R s_k[10];  // a0, 1/(2 lambda), dt/2, alpha_0..2, a_1..3, a0lo
   if (threadIdx.x == 0) {
     const StepCoef3 c = step_coef3(P, ctl, slot);
     s_cf = c;
@@ -699,6 +701,9 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks))
       s_k[3 + j] = R(c.alpha[j]);
       s_k[6 + j] = R(c.aj[j]);
     }
+    const RestCoef<R> rc = rest_coef<R>(c.a0, &s_k[3], 3, s_k[1]);
+    s_k[0] = rc.hi;
+    s_k[9] = rc.lo;
   }
   __syncthreads();
   const StepCoef3 cf = s_cf;
@@ -725,7 +730,7 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks))
   const int mi = map_index(i, P.nx, P.bc[0], P.bc[1]);
   const int mkm = map_index(k - 1, P.nz3, P.bc_z[0], P.bc_z[1]), mkp = map_index(k + 1, P.nz3, P.bc_z[0], P.bc_z[1]);
   const Phys<R> K = make_phys<R>(P);
-  const R a0 = s_k[0], inv2l = s_k[1], hdt = s_k[2];
+  const R a0 = s_k[0], a0lo = s_k[9], inv2l = s_k[1], hdt = s_k[2];
   const R al[3] = {s_k[3], s_k[4], s_k[5]};
   const R aj[3] = {s_k[6], s_k[7], s_k[8]};
   R sp0 = R(0), sp1 = R(0), sp2 = R(0);
@@ -789,7 +794,7 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks))
         const int qq = q == 0 ? 0 : (q == 1 ? 1 : (q == 2 ? 4 : (q == 3 ? 2 : 5)));
         const int dir = qq == 0 ? 0 : (qq - 1) % 3;
         R* o = q == 0 ? p0 : (q == 1 ? ppx : (q == 2 ? pmx : (q == 3 ? ppy : pmy)));
-        post_q<SYS, R>(K, P, oU, pw, S, ow, of[q], qq, a0, al[dir], qq == 0 ? a0 : aj[dir], inv2l, hdt, o);
+        post_q<SYS, R>(K, P, oU, pw, S, ow, of[q], qq, a0, a0lo, al[dir], qq == 0 ? a0 : aj[dir], inv2l, hdt, o);
       }
     }
     if constexpr (PF) {
@@ -823,7 +828,7 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks))
         const Prim3<R> pz = prim3<SYS, R>(K, zU[s2]);
         R Sz[M];
         if constexpr (SRC) source3<SYS, R>(K, zU[s2], Sz);
-        post_q<SYS, R>(K, P, zU[s2], pz, Sz, zw[s2], zf[s2], qq, a0, al[2], aj[2], inv2l, hdt, Fk[qq]);
+        post_q<SYS, R>(K, P, zU[s2], pz, Sz, zw[s2], zf[s2], qq, a0, a0lo, al[2], aj[2], inv2l, hdt, Fk[qq]);
       }
       R Ubar[M];
 #pragma unroll

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
   R* hfs = (R*)(smem_raw + L::hf_off);            // [NHALO][M]
   unsigned long long* bars = (unsigned long long*)(smem_raw + L::bar_off);  // U slots 0..3, f box 4
   __shared__ StepCoef3 s_cf;
-  __shared__ R s_k[9];  // a0, 1/(2 lambda), dt/2, alpha_0..2, a_1..3
+  __shared__ R s_k[10];  // a0, 1/(2 lambda), dt/2, alpha_0..2, a_1..3, a0lo
   __shared__ int s_abort;
   const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
   if (t == 0) {
@@ -150,6 +150,9 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
       s_k[3 + j] = R(c.alpha[j]);
       s_k[6 + j] = R(c.aj[j]);
     }
+    const RestCoef<R> rc = rest_coef<R>(c.a0, &s_k[3], 3, s_k[1]);
+    s_k[0] = rc.hi;
+    s_k[9] = rc.lo;
     for (int i = 0; i < kURing3 + 1; i++) mbar_init(smem_u32(&bars[i]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
   const long long nf = 7ll * M * P.plane;
   unsigned int* const stc = &ctl->status;
   const Phys<R> K = make_phys<R>(P);
-  const R a0 = s_k[0], inv2l = s_k[1], hdt = s_k[2];
+  const R a0 = s_k[0], a0lo = s_k[9], inv2l = s_k[1], hdt = s_k[2];
   const R al[3] = {s_k[3], s_k[4], s_k[5]};
   const R aj[3] = {s_k[6], s_k[7], s_k[8]};
   const bool fixed_omega = P.omega_mode == 1;
@@ -361,7 +364,7 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
         for (int d = 0; d < 3; d++) flux3<SYS, R>(K, P, U, pw, d, F[d]);
 #pragma unroll
         for (int c = 0; c < M; c++) {
-          R v = fq[0][c] - w * (fq[0][c] - a0 * U[c]);
+          R v = fq[0][c] - w * (fq[0][c] - rest_eq(a0, a0lo, U[c]));
           if constexpr (SRC) v += hdt * a0 * S[c];
           pown[0][c] = v;
         }

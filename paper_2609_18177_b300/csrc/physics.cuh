@@ -32,6 +32,44 @@ __device__ __forceinline__ float rmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double rmax(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ double fexp(double x) { return exp(x); }
 
+// The coefficient a_0 = 1 - sum_j alpha_j / lambda of the rest equilibrium
+// (Eq. 2.20) in FP32, as an unevaluated sum hi + lo of two floats built from
+// the FP32-rounded alpha_j and 1/(2 lambda) that the moving equilibria use, so
+// that a_0 + sum_j 2 alpha_j / (2 lambda) = 1 holds to ~2^-48.  Rounded on
+// their own, the FP32 coefficients made a node's equilibria sum to U (1 + d)
+// with one d ~ 2^-25 for every node of a step, and each step moved the mass by
+// omega d: a drift linear in the number of steps (1D Shu-Osher, 2^18 nodes,
+// 756,609 steps: L1 1.6e-2 against FP64; with hi + lo 8.5e-4).  In FP64 hi is
+// a_0 and lo is 0.  `al` holds the d FP32 alpha_j.
+template <class R>
+struct RestCoef {
+  R hi, lo;
+};
+template <class R>
+__host__ __device__ __forceinline__ RestCoef<R> rest_coef(double a0, const R* al, int d, R inv2l) {
+  RestCoef<R> c;
+  if constexpr (sizeof(R) == 4) {
+    double s = 0.0;
+    for (int j = 0; j < d; j++) s += (double)al[j];
+    const double a0c = 1.0 - 2.0 * s * (double)inv2l;
+    c.hi = R(a0c);
+    c.lo = R(a0c - (double)c.hi);
+  } else {
+    c.hi = R(a0);
+    c.lo = R(0);
+  }
+  return c;
+}
+
+// the rest equilibrium a_0 U with a_0 = hi + lo (FP32) or hi (FP64)
+template <class R>
+__device__ __forceinline__ R rest_eq(R hi, R lo, R U) {
+  if constexpr (sizeof(R) == 4)
+    return hi * U + lo * U;
+  else
+    return hi * U;
+}
+
 // Problem constants in the arithmetic type of the path.
 template <class R>
 struct Phys {

@@ -81,8 +81,9 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(DevParams P, const double* U
   double dt = P.cfl * P.dx / (D == 2 ? ab0 + ab1 : ab0);
   double lam = P.dx / dt;
   double al0 = ab0 + P.eps, al1 = D == 2 ? ab1 + P.eps : 0.0;
-  const R a0 = R(1.0 - (D == 2 ? al0 + al1 : al0) / lam), inv2l = R(1.0 / (2.0 * lam));
+  const R inv2l = R(1.0 / (2.0 * lam));
   const R al[2] = {R(al0), R(al1)};
+  const RestCoef<R> rc = rest_coef<R>(1.0 - (D == 2 ? al0 + al1 : al0) / lam, al, D, inv2l);
   const Phys<R> K = make_phys<R>(P);
   double s0 = 0.0, s1 = 0.0;
   for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < nn;
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(DevParams P, const double* U
       R feq[M];
       if (k == 0) {
 #pragma unroll
-        for (int c = 0; c < M; c++) feq[c] = a0 * U[c];
+        for (int c = 0; c < M; c++) feq[c] = rest_eq(rc.hi, rc.lo, U[c]);
       } else {
         int jd = (k - 1) % D;
         R F[M];

@@ -213,9 +213,10 @@ __global__ void k_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
   for (int c = 0; c < M; c++) usum[c] = 0.0;
   unsigned st = 0u;
   const Phys<R> K = make_phys<R>(P);
-  const R a0 = R(cf.a0), inv2l = R(1.0 / (2.0 * cf.lam)), hdt = R(0.5 * cf.dt);
+  const R inv2l = R(1.0 / (2.0 * cf.lam)), hdt = R(0.5 * cf.dt);
   const R al[2] = {R(cf.alpha[0]), R(cf.alpha[1])};
   const R ak[3] = {R(cf.a0), R(cf.aj[0]), R(cf.aj[1])};
+  const RestCoef<R> rc = rest_coef<R>(cf.a0, al, D, inv2l);
   if (node < nn) {
     int j = (int)(node / P.nx), i = (int)(node % P.nx);
     R Fk[Q][M];
@@ -234,7 +235,7 @@ __global__ void k_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
       R feq[M];
       if (k == 0) {
 #pragma unroll
-        for (int c = 0; c < M; c++) feq[c] = a0 * U[c];
+        for (int c = 0; c < M; c++) feq[c] = rest_eq(rc.hi, rc.lo, U[c]);
       } else {
         int jd = (k - 1) % D;
         R F[M];
