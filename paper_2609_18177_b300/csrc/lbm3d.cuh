@@ -72,8 +72,9 @@ __device__ __forceinline__ void flux3(const Phys<R>& K, const DevParams& P, cons
   if constexpr (SYS == SYS_ADV) {
     F[0] = adv3<R>(K, P, dir) * U[0];
   } else {
-    const R vel[3] = {w.u, w.v, w.w};
-    const R vn = vel[dir];
+    // selected, not indexed: dir may be a run-time value (the fused kernel's
+    // halo posts), and an indexed array would live in local memory
+    const R vn = dir == 0 ? w.u : (dir == 1 ? w.v : w.w);
     F[0] = w.rho * vn;
 #pragma unroll
     for (int t = 0; t < 3; t++) F[1 + t] = U[1 + t] * vn + (dir == t ? w.p : R(0));
@@ -87,8 +88,7 @@ __device__ __forceinline__ R speed3(const Phys<R>& K, const DevParams& P, const 
   if constexpr (SYS == SYS_ADV) {
     return rabs(adv3<R>(K, P, dir));
   } else {
-    const R vel[3] = {w.u, w.v, w.w};
-    return rabs(vel[dir]) + w.c;
+    return rabs(dir == 0 ? w.u : (dir == 1 ? w.v : w.w)) + w.c;
   }
 }
 

@@ -406,13 +406,14 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
 #pragma unroll
           for (int c = 0; c < M; c++) S[c] = R(0);
         flux3<SYS, R>(K, P, U, pw, hdir, F);
+        const R alh = hdir == 0 ? al[0] : al[1], ajh = hdir == 0 ? aj[0] : aj[1];  // selected, not indexed
         R* dst = hq == 1 ? hxs + hy : (hq == 4 ? hxs + M * TY + hy : (hq == 2 ? pys + hx : mys + TY * kTX3 + hx));
         const int cstride = (hq == 1 || hq == 4) ? TY : (TY + 1) * kTX3;
 #pragma unroll
         for (int c = 0; c < M; c++) {
-          const R feq = hq <= 3 ? (al[hdir] * U[c] + F[c]) * inv2l : (al[hdir] * U[c] - F[c]) * inv2l;
+          const R feq = hq <= 3 ? (alh * U[c] + F[c]) * inv2l : (alh * U[c] - F[c]) * inv2l;
           R v = fq[c] - w * (fq[c] - feq);
-          if constexpr (SRC) v += hdt * aj[hdir] * S[c];
+          if constexpr (SRC) v += hdt * ajh * S[c];
           dst[c * cstride] = v;
         }
       }
