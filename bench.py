@@ -574,6 +574,20 @@ def run_lines1d(args):
                 acc.append({"case": name, "n": n, "T": T, "steps_fp64": res[lbmh.FP64][1],
                             "steps_fp32": res[lbmh.FP32][1], "l1_fp32_vs_fp64": e,
                             "meets_tolerance": bool(e["max"] <= A.tolerance(pb.system))})
+    # the FP64 oracle as it stands on a bounded sample (its OpenMP loop runs
+    # over rows, and a 1D lattice has one: a single core)
+    cpu = None
+    if not args.no_cpu_baseline and not args.case:
+        orc = _native_oracle()
+        orc.set_threads(1)
+        pb1, U1 = W.sod(1 << 14)
+        mlups1, steps1, el1 = _time_oracle(pb1, U1, 8.0)
+        orc.set_threads(os.cpu_count() or 1)
+        cpu = {"value": mlups1, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"Sod 2^14 nodes, FP64, {steps1} steps ({el1:.1f} s), one core (the oracle's OpenMP "
+                         "loop is over rows; a 1D lattice has one); oracle built -O3 -march=native "
+                         "-ffp-contract=off on this host",
+               "cpu": _cpu_model()}
     head = ([c for c in out if c["case"] == "sod" and c["n"] == 1 << 18 and c["dtype"] == "f32"] or out)[0]
     return {
         "metric": METRIC, "workload": "lines1d", "value": head["mlups"], "unit": "MLUPS",
@@ -586,6 +600,7 @@ def run_lines1d(args):
         "l1_err_vs_fp64": {"norm": "relative L1 per quantity (contract norm)",
                            "reference": "FP64 fused GPU path to the same end time (oracle parity 1e-12 per step)",
                            "cases": acc},
+        "cpu_baseline": cpu,
     }
 
 
