@@ -46,14 +46,25 @@ struct RestCoef {
   R hi, lo;
 };
 template <class R>
-__host__ __device__ __forceinline__ RestCoef<R> rest_coef(double a0, const R* al, int d, R inv2l) {
+__device__ __forceinline__ RestCoef<R> rest_coef(double a0, const R* al, int d, R inv2l) {
   RestCoef<R> c;
   if constexpr (sizeof(R) == 4) {
-    double s = 0.0;
-    for (int j = 0; j < d; j++) s += (double)al[j];
-    const double a0c = 1.0 - 2.0 * s * (double)inv2l;
-    c.hi = R(a0c);
-    c.lo = R(a0c - (double)c.hi);
+    // 1 - sum_j 2 al_j inv2l in FP32 arithmetic without FP64 (a dependent
+    // FP64 chain at the start of each block cost the 1D step ~3 %): every
+    // product split exactly as p + e (fma), the running sum hi + lo kept by
+    // TwoSum; 2 p and 2 e are exact
+    float hi = 1.0f, lo = 0.0f;
+    for (int j = 0; j < d; j++) {
+      const float p = al[j] * inv2l;
+      const float e = fmaf(al[j], inv2l, -p);  // al_j inv2l = p + e exactly
+      const float b = -2.0f * p;
+      const float s2 = hi + b, bb = s2 - hi;
+      lo += ((hi - (s2 - bb)) + (b - bb)) - 2.0f * e;
+      hi = s2;
+    }
+    const float t = hi + lo;
+    c.lo = lo - (t - hi);
+    c.hi = t;
   } else {
     c.hi = R(a0);
     c.lo = R(0);
