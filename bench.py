@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-n", type=int, default=384)
     ap.add_argument("--workload", default="riemann2d",
-                    choices=["riemann2d", "batched", "served", "lines1d", "cube3d"])
+                    choices=["riemann2d", "batched", "served", "lines1d", "cube3d", "slabs"])
     ap.add_argument("--lattice", default="riemann2d", choices=["riemann2d", "reactive", "dambreak"],
                     help="single-lattice line: the lattice stepped (default: the 2D Riemann roofline run)")
     ap.add_argument("--case", default=None,
@@ -604,6 +604,91 @@ def run_lines1d(args):
     }
 
 
+def run_slabs(args):
+    """The slab decomposition of one lattice along y (the multi-GPU form), with
+    its slabs held side by side on this one GPU: each step the host takes the
+    maximum of the slabs' speed bounds (a read and a write of d numbers per
+    slab), steps every slab once, and copies each slab's three outermost rows
+    into its neighbour's halo through device buffers.  The 8192^2 Riemann
+    workload in FP32, 1, 2 and 4 slabs; the slabs' rows must equal the whole
+    lattice bit for bit (checked on the rows next to every cut).  The line's
+    `clocks` cover the whole run, host-side set-up included (the GPU idles
+    there); `clocks_timed_4_slabs` the timed loop of 4 slabs."""
+    import torch
+    from paper_2609_18177_b300 import lbmh
+    from paper_2609_18177_b300 import slab as S
+    from paper_2609_18177_b300 import workloads as W
+    n = args.n
+    steps = max(4, min(args.steps, 600))
+    pb, U0 = workload(n, args.seed, "fp32", "riemann2d")
+    with lbmh.Solver(pb, precision=lbmh.FP32, kernel=lbmh.KERNEL_FUSED) as s:
+        s.set_state(U0).step(max(3, args.warmup))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(steps)
+        torch.cuda.synchronize()
+        whole_ms = (time.perf_counter() - t0) * 1e3 / steps
+        want = s.moments()
+    cases = []
+    timed = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))  # the timed loops only
+    for world in (2, 4):
+        rows = S.partition_rows(pb.ny, world)
+        slabs = [lbmh.Slab(pb, b, e, precision=lbmh.FP32) for (b, e) in rows]
+        nbr = [S.neighbours(r, world, pb.bc[2] == W.PERIODIC) for r in range(world)]
+        local = [np.ascontiguousarray(U0[:, S.local_rows(pb.ny, b, e, sl.halo), :]) for (b, e), sl in zip(rows, slabs)]
+        ab0 = np.max([sl.state_speed_bound(u) for sl, u in zip(slabs, local)], axis=0)
+        for sl, u in zip(slabs, local):
+            sl.set_state_bound(u, ab0)
+        del local
+        bufs = [[torch.empty(sl.halo_bytes, dtype=torch.uint8, device="cuda") for _ in range(2)] for sl in slabs]
+
+        def one_step():
+            ab = np.max([sl.get_speed_bound() for sl in slabs], axis=0)
+            for sl in slabs:
+                sl.set_speed_bound(ab).step(1)
+            for r, sl in enumerate(slabs):
+                for side in (0, 1):
+                    if nbr[r][side] is not None:
+                        sl.halo_get(side, bufs[r][side])
+            for r, sl in enumerate(slabs):
+                lo, hi = nbr[r]
+                if lo is not None:
+                    sl.halo_set(0, bufs[lo][1])
+                if hi is not None:
+                    sl.halo_set(1, bufs[hi][0])
+
+        for _ in range(max(3, args.warmup)):
+            one_step()
+        torch.cuda.synchronize()
+        if world == 4:
+            timed.start()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            one_step()
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / steps
+        if world == 4:
+            clocks_timed = timed.stop()
+        same = True
+        for (b, e), sl in zip(rows, slabs):
+            U = sl.moments()
+            mine = U[:, sl.halo[0]:U.shape[1] - sl.halo[1], :]
+            for rr in sorted({0, 1, 2, e - b - 3, e - b - 2, e - b - 1}):
+                same &= bool(np.array_equal(mine[:, rr, :], want[:, b + rr, :]))
+            sl.close()
+        cases.append({"slabs": world, "ms_per_step": ms, "mlups": pb.nodes / (ms / 1e3) / 1e6,
+                      "overhead_vs_whole": ms / whole_ms - 1.0, "rows_next_to_cuts_bitwise_equal": same})
+    return {
+        "metric": METRIC, "workload": "slabs", "value": cases[0]["mlups"], "unit": "MLUPS",
+        "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"2D Euler seeded 4-quadrant Riemann {n}x{n}, FP32, decomposed along y into "
+                               "slabs held on one GPU (host maximum of the speed bounds, device-buffer halo "
+                               "copies); wall time per step", "steps": steps},
+        "whole_lattice_ms_per_step": whole_ms, "cases": cases,
+        "clocks_timed_4_slabs": clocks_timed,
+    }
+
+
 def run_cube3d(args):
     """The 3D (D3Q7) path: Euler on a periodic n^3 cube with a seeded random
     state (smooth fields plus a jump), FP32 and FP64, and reactive Euler (the
@@ -659,11 +744,11 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in ("batched", "served", "lines1d", "cube3d"):
+    if args.workload in ("batched", "served", "lines1d", "cube3d", "slabs"):
         sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
         sampler.start()
         line = {"batched": run_batched, "served": run_served, "lines1d": run_lines1d,
-                "cube3d": run_cube3d}[args.workload](args)
+                "cube3d": run_cube3d, "slabs": run_slabs}[args.workload](args)
         line["clocks"] = sampler.stop()  # sampled over the whole run, reference solves included
         print(json.dumps(line), flush=True)
         return 0
