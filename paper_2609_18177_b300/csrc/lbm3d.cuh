@@ -458,8 +458,9 @@ __global__ void k3_indicator(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, 
 // K2: omega = 1 + 1/(1 + nu~), nu~ the sum over the 3^3 box (Eq. 2.15, 2.16).
 // Grid (ceil(ex / 128), ey, ceil(ez / kZ3)): a thread marches kZ3 planes of
 // its (x, y) column and keeps the 3 x 3 windows of nu of the planes k - 1, k,
-// k + 1 in registers, so a node costs 9 loads instead of 27; the 27 terms are
-// still added one at a time in the order (bk, bj, bi).
+// k + 1 in registers, so a node costs 9 loads instead of 27.  The 27 terms
+// are added as the fused step adds them: the three planes at each (bj, bi)
+// first, (nu_{k-1} + nu_k) + nu_{k+1}, then those sums in the order (bj, bi).
 template <class R>
 __global__ void k3_omega(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, const R* nu, R* om) {
   const int ei = blockIdx.x * blockDim.x + threadIdx.x, ej = blockIdx.y;
@@ -494,9 +495,7 @@ __global__ void k3_omega(DevParams P, const Ctl* ctl, int slot, ExtGeom3 G, cons
     load_plane(ek + 1, win[2]);
     R s = R(0);
 #pragma unroll
-    for (int pz = 0; pz < 3; pz++)
-#pragma unroll
-      for (int q = 0; q < 9; q++) s += win[pz][q];
+    for (int q = 0; q < 9; q++) s += (win[0][q] + win[1][q]) + win[2][q];
     om[chk(G.idx(ek, ej, ei), n, stc)] = R(1) + fdiv(R(1), R(1) + s);
 #pragma unroll
     for (int q = 0; q < 9; q++) {

@@ -8,9 +8,11 @@
 // box sum and omega (Eq. 2.15/2.16) are computed on chip as the tile marches,
 // instead of round trips through global nu and omega arrays.  Per plane q:
 //   U(q) on the tile + 3 arrives (one TMA box, one plane ahead) in a ring of 4
-//   1  nu(q-1) on the tile + 2 from U(q-2..q)         (ring of 3 nu planes)
-//   2  omega(q-2) on the tile + 1 from nu(q-3..q-1), by the thread whose post
-//      needs it (own column, or the halo node it streams from)
+//   1  nu(q-1) on the tile + 2 from U(q-2..q); the thread that computes a
+//      position keeps its nu of planes q-3, q-2 in registers and writes the
+//      sum nu(q-3) + nu(q-2) + nu(q-1) there (one shared plane)
+//   2  omega(q-2) on the tile + 1 from that plane's 3 x 3 window, by the thread
+//      whose post needs it (own column, or the halo node it streams from)
 //   3  posts of plane q-2: every direction at the tile's own columns, the one
 //      direction each halo column or row streams into the tile
 //   4  plane q-3 streamed (F_k(x) = post_k(x - e_k), Eq. 2.2), the implicit
@@ -69,7 +71,7 @@ struct Smem3F {
   static constexpr size_t u_slot = a128(u_box);  // TMA destinations start on 128 bytes
   static constexpr size_t f_off = kURing3 * u_slot;
   static constexpr size_t nu_off = f_off + (k3f_f_tma<R>() ? a128(f_box) : 0);
-  static constexpr size_t py_off = nu_off + (size_t)3 * NH * kNW3 * sizeof(R);
+  static constexpr size_t py_off = nu_off + (size_t)NH * kNW3 * sizeof(R);
   static constexpr size_t py_bytes = (size_t)M * (TY + 1) * kTX3 * sizeof(R);
   static constexpr size_t my_off = py_off + py_bytes;
   static constexpr size_t hx_off = my_off + py_bytes;
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   unsigned char* const smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
   const R* fs = (const R*)(smem_raw + L::f_off);  // [7 m][TY][kTX3]
-  R* nus = (R*)(smem_raw + L::nu_off);            // [3][NH][kNW3]
+  R* nus = (R*)(smem_raw + L::nu_off);            // [NH][kNW3]: nu summed over planes q-3..q-1
   R* pys = (R*)(smem_raw + L::py_off);            // [M][TY + 1][kTX3]
   R* mys = (R*)(smem_raw + L::my_off);            // [M][TY + 1][kTX3]
   R* hxs = (R*)(smem_raw + L::hx_off);            // [2][M][TY]
@@ -225,6 +227,12 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
   R kp0[M], kxp[M], kxm[M], kyp[M], kym[M], pz1[M], pz2[M];
 #pragma unroll
   for (int c = 0; c < M; c++) kp0[c] = kxp[c] = kxm[c] = kyp[c] = kym[c] = pz1[c] = pz2[c] = R(0);
+  // nu of this thread's phase-1 positions (t, t + NT, ...) on the two planes
+  // before the one being computed
+  constexpr int NUI = (NH * kNW3 + NT - 1) / NT;
+  R nu3[NUI], nu2[NUI];
+#pragma unroll
+  for (int i = 0; i < NUI; i++) nu3[i] = nu2[i] = R(0);
 
   // load bookkeeping of thread 0, the issuing thread: it issues a load only
   // while every wait it made has succeeded, and before exiting waits for every
@@ -272,8 +280,10 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
       const R* Um1 = uslot(q - 2);
       const R* U00 = uslot(q - 1);
       const R* Up1 = uslot(q);
-      R* nd = nus + (size_t)(((q - 1) % 3 + 3) % 3) * NH * kNW3;
-      for (int it = t; it < NH * kNW3; it += NT) {
+#pragma unroll
+      for (int i = 0; i < NUI; i++) {
+        const int it = t + i * NT;
+        if (it >= NH * kNW3) break;
         const int iy = it / kNW3, ix = it % kNW3;
         const int o = (iy + 1) * kUW3 + (ix + 1);  // position in the U tile
         constexpr int CS = UH * kUW3;
@@ -293,26 +303,23 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
           }
           sum += theta3<SYS, R>(K, w, d, dm, dp);
         }
-        nd[it] = sum;
+        nus[it] = (nu3[i] + nu2[i]) + sum;  // planes q-3, q-2, q-1 (garbage before q = zb + 1, never read)
+        nu3[i] = nu2[i];
+        nu2[i] = sum;
       }
     }
     __syncthreads();
     if (s_abort) break;  // a wait gave up (set before this barrier, read by all after it)
     // 2: omega(q - 2) at a position (jy, jx) of the tile + 1, by the thread
-    // whose post needs it (27 terms in the order (bk, bj, bi)): no shared
+    // whose post needs it (the z-summed nu in the order (bj, bi)): no shared
     // omega plane and no barrier of its own
-    const R* nb[3];
-#pragma unroll
-    for (int pz = 0; pz < 3; pz++) nb[pz] = nus + (size_t)(((q - 3 + pz) % 3 + 3) % 3) * NH * kNW3;
     auto omega_at = [&](int jy, int jx) -> R {
       if (fixed_omega) return om_fixed;
       R s = R(0);
 #pragma unroll
-      for (int pz = 0; pz < 3; pz++)
+      for (int bj = 0; bj < 3; bj++)
 #pragma unroll
-        for (int bj = 0; bj < 3; bj++)
-#pragma unroll
-          for (int bi = 0; bi < 3; bi++) s += nb[pz][(jy + bj) * kNW3 + jx + bi];
+        for (int bi = 0; bi < 3; bi++) s += nus[(jy + bj) * kNW3 + jx + bi];
       return R(1) + fdiv(R(1), R(1) + s);
     };
     if (posts) {
