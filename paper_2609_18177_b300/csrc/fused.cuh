@@ -548,7 +548,9 @@ __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml
             for (int k = 0; k < Q; k++) {
               R fk = f2[(k * M + c) * NC + sc0 + j];
               R pk = fk - om * (fk - feq[k]);
-              if constexpr (SRC) pk += hdt * akk[k] * Sr[c];
+              if constexpr (SRC) {
+                if (src_field<SYS, 2>(c)) pk += hdt * akk[k] * Sr[c];
+              }
               post[j][k][c] = pk;
             }
           }
@@ -583,7 +585,35 @@ __device__ __forceinline__ void run_segment2d(Pipe2D& pp, const CUtensorMap* tml
             Ubar[c] = s;
           }
           R Us[M];  // moments of the stored f^{n+1}, summed k = 0..Q-1 as the next step does
-          if constexpr (SRC) {
+          if constexpr (SYS == SYS_REACT) {
+            // the second half-source dt/2 a_k S(U^{n+1}): Eq. (2.8) makes
+            // dt/2 S(U^{n+1}) = U^{n+1} - Ubar, so S is not evaluated again
+            R Un[M];
+            const R yr = K.yb + R(y + P.row0) * K.dx;
+            unsigned stn = 0u;
+            if (outc[j]) {
+              stn = implicit_moment<SYS, 2, R>(K, Ubar, xr_out[j], yr, cc.dt, hdt, Un);
+            } else {  // halo column: its result is not stored
+  #pragma unroll
+              for (int c = 0; c < M; c++) Un[c] = Ubar[c];
+            }
+  #pragma unroll
+            for (int c = 0; c < M; c++) {
+              if (src_field<SYS, 2>(c)) {
+                const R hs = Un[c] - Ubar[c];
+                R s = R(0);
+  #pragma unroll
+                for (int k = 0; k < Q; k++) {
+                  Fk[k][c] += akk[k] * hs;
+                  s += Fk[k][c];
+                }
+                Us[c] = s;
+              } else {
+                Us[c] = Ubar[c];  // no source: the same sum as Ubar
+              }
+            }
+            if (outc[j] && row_out) st |= stn;
+          } else if constexpr (SRC) {  // shallow water: S(U^{n+1}) evaluated
             R Un[M], Sn[M];
             const R yr = K.yb + R(y + P.row0) * K.dx;
             unsigned stn = 0u;
@@ -857,9 +887,11 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
       post0[c] = f[0][c] - om * (f[0][c] - feq0);
       R q1 = f[1][c] - om * (f[1][c] - feq1), q2 = f[2][c] - om * (f[2][c] - feq2);
       if constexpr (SRC) {
-        post0[c] += hdt * a0 * S[c];
-        q1 += hdt * a1 * S[c];
-        q2 += hdt * a1 * S[c];
+        if (src_field<SYS, 1>(c)) {
+          post0[c] += hdt * a0 * S[c];
+          q1 += hdt * a1 * S[c];
+          q2 += hdt * a1 * S[c];
+        }
       }
       p1s[c][t] = q1;
       p2s[c][t] = q2;
@@ -875,10 +907,11 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
         Ubar[c] = Fk[0][c] + Fk[1][c] + Fk[2][c];
       }
       const R xo = K.xb + R(gx) * K.dx;
-      if constexpr (SRC) {
-        st |= implicit_moment<SYS, 1, R>(K, Ubar, xo, R(0), cf.dt, hdt, Un);
-        source<SYS, 1, R>(K, Un, xo, R(0), Sn);
-      }
+      // the second half-source dt/2 a_k S(U^{n+1}): reactive Euler takes it
+      // from Eq. (2.8), dt/2 S(U^{n+1}) = U^{n+1} - Ubar, without evaluating S
+      // again; shallow water evaluates S(U^{n+1})
+      if constexpr (SRC) st |= implicit_moment<SYS, 1, R>(K, Ubar, xo, R(0), cf.dt, hdt, Un);
+      if constexpr (SYS == SYS_SWE) source<SYS, 1, R>(K, Un, xo, R(0), Sn);
       const R ak[3] = {a0, a1, a1};
 #pragma unroll
       for (int c = 0; c < M; c++) Uo[c] = R(0);
@@ -887,7 +920,11 @@ __global__ void __launch_bounds__(FT) k_fused1d(DevParams P, R* const* buf, Ctl*
 #pragma unroll
         for (int c = 0; c < M; c++) {
           R v = Fk[k][c];
-          if constexpr (SRC) v += hdt * ak[k] * Sn[c];
+          if constexpr (SYS == SYS_REACT) {
+            if (src_field<SYS, 1>(c)) v += ak[k] * (Un[c] - Ubar[c]);
+          } else if constexpr (SRC) {
+            v += hdt * ak[k] * Sn[c];
+          }
           fout[chk((long long)(k * M + c) * P.plane + gx + XPAD, (long long)Q * M * P.plane, &ctl->status)] = v;
           Uo[c] += v;
         }

@@ -656,7 +656,9 @@ __device__ __forceinline__ void post_q(const Phys<R>& K, const DevParams& P, con
   for (int c = 0; c < M; c++) {
     const R feq = q == 0 ? rest_eq(a0, a0lo, U[c]) : (q <= 3 ? (alq * U[c] + F[c]) * inv2l : (alq * U[c] - F[c]) * inv2l);
     R v = fq[c] - w * (fq[c] - feq);
-    if constexpr (SYS == SYS_REACT) v += hdt * akq * S[c];
+    if constexpr (SYS == SYS_REACT) {
+      if (src_field<SYS, 3>(c)) v += hdt * akq * S[c];
+    }
     out[c] = v;
   }
 }
@@ -837,16 +839,14 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks))
         for (int q = 0; q < Q; q++) sum += Fk[q][c];
         Ubar[c] = sum;
       }
-      R Sn[M];
-#pragma unroll
-      for (int c = 0; c < M; c++) Sn[c] = R(0);
+      // the second half-source dt/2 a_q S(U^{n+1}): Eq. (2.8) makes
+      // dt/2 S_5(U^{n+1}) = (rho Y)^{n+1} - (rho Y)bar, so S is not evaluated again
+      R hs = R(0);
       if constexpr (SRC) {
         if (K.react && Ubar[5] != R(0)) {
-          R Un[M];
-#pragma unroll
-          for (int c = 0; c < M; c++) Un[c] = Ubar[c];
-          st |= react_implicit3<R>(K, Ubar, cf.dt, hdt, &Un[5]);
-          source3<SYS, R>(K, Un, Sn);
+          R z;
+          st |= react_implicit3<R>(K, Ubar, cf.dt, hdt, &z);
+          hs = z - Ubar[5];
         }
       }
       const IX oo = fidx(i, y, k);
@@ -859,7 +859,9 @@ __global__ void __launch_bounds__(kLanes3, (K3Occupancy<SYS, R>::blocks))
 #pragma unroll
         for (int c = 0; c < M; c++) {
           R v = Fk[q][c];
-          if constexpr (SRC) v += hdt * akq * Sn[c];
+          if constexpr (SRC) {
+            if (src_field<SYS, 3>(c)) v += akq * hs;
+          }
           fo[chk((IX)(q * M + c) * pl + oo, nf, stc)] = v;
           Uo[c] += v;
         }

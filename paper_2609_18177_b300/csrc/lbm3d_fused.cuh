@@ -372,7 +372,9 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
 #pragma unroll
         for (int c = 0; c < M; c++) {
           R v = fq[0][c] - w * (fq[0][c] - rest_eq(a0, a0lo, U[c]));
-          if constexpr (SRC) v += hdt * a0 * S[c];
+          if constexpr (SRC) {
+            if (src_field<SYS, 3>(c)) v += hdt * a0 * S[c];
+          }
           pown[0][c] = v;
         }
 #pragma unroll
@@ -383,8 +385,10 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
             R vp = fq[1 + d][c] - w * (fq[1 + d][c] - fp);
             R vm = fq[4 + d][c] - w * (fq[4 + d][c] - fm);
             if constexpr (SRC) {
-              vp += hdt * aj[d] * S[c];
-              vm += hdt * aj[d] * S[c];
+              if (src_field<SYS, 3>(c)) {
+                vp += hdt * aj[d] * S[c];
+                vm += hdt * aj[d] * S[c];
+              }
             }
             pown[1 + d][c] = vp;
             pown[4 + d][c] = vm;
@@ -420,7 +424,9 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
         for (int c = 0; c < M; c++) {
           const R feq = hq <= 3 ? (alh * U[c] + F[c]) * inv2l : (alh * U[c] - F[c]) * inv2l;
           R v = fq[c] - w * (fq[c] - feq);
-          if constexpr (SRC) v += hdt * ajh * S[c];
+          if constexpr (SRC) {
+            if (src_field<SYS, 3>(c)) v += hdt * ajh * S[c];
+          }
           dst[c * cstride] = v;
         }
       }
@@ -446,16 +452,14 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
           for (int k = 0; k < Q; k++) sum += Fk[k][c];
           Ubar[c] = sum;
         }
-        R Sn[M];
-#pragma unroll
-        for (int c = 0; c < M; c++) Sn[c] = R(0);
+        // the second half-source dt/2 a_k S(U^{n+1}): Eq. (2.8) makes
+        // dt/2 S_5(U^{n+1}) = (rho Y)^{n+1} - (rho Y)bar, so S is not evaluated again
+        R hs = R(0);
         if constexpr (SRC) {
           if (K.react && Ubar[5] != R(0)) {
-            R Un[M];
-#pragma unroll
-            for (int c = 0; c < M; c++) Un[c] = Ubar[c];
-            st |= react_implicit3<R>(K, Ubar, cf.dt, hdt, &Un[5]);
-            source3<SYS, R>(K, Un, Sn);
+            R z;
+            st |= react_implicit3<R>(K, Ubar, cf.dt, hdt, &z);
+            hs = z - Ubar[5];
           }
         }
         const long long oo = cell3(P, x, y, p);
@@ -468,7 +472,9 @@ __global__ void __launch_bounds__(Tile3F<SYS, R>::threads, Tile3F<SYS, R>::min_b
 #pragma unroll
           for (int c = 0; c < M; c++) {
             R v = Fk[k][c];
-            if constexpr (SRC) v += hdt * akq * Sn[c];
+            if constexpr (SRC) {
+              if (src_field<SYS, 3>(c)) v += akq * hs;
+            }
             fo[chk((long long)(k * M + c) * P.plane + oo, nf, stc)] = v;
             Uo[c] += v;
           }

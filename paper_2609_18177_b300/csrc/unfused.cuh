@@ -251,10 +251,12 @@ __global__ void k_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
 #pragma unroll
       for (int c = 0; c < M; c++) {
         R fk = f[chk((long long)(k * M + c) * P.plane + off, (long long)Q * M * P.plane, stc)];
-        Fk[k][c] = fk - wk * (fk - feq[c]) + hdt * akk * S[c];
+        R v = fk - wk * (fk - feq[c]);
+        if (src_field<SYS, D>(c)) v += hdt * akk * S[c];
+        Fk[k][c] = v;
       }
     }
-    R Ubar[M], Un[M], S[M];
+    R Ubar[M], Un[M], Sn[M];
 #pragma unroll
     for (int c = 0; c < M; c++) {
       R s = R(0);
@@ -264,7 +266,10 @@ __global__ void k_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
     }
     const R xn = K.xb + R(i) * K.dx, yn = K.yb + R(j) * K.dx;
     st |= implicit_moment<SYS, D, R>(K, Ubar, xn, yn, cf.dt, hdt, Un);
-    source<SYS, D, R>(K, Un, xn, yn, S);
+    // the second half-source dt/2 a_k S(U^{n+1}): reactive Euler takes it
+    // from Eq. (2.8), dt/2 S(U^{n+1}) = U^{n+1} - Ubar, without evaluating S
+    // again; the other systems evaluate S(U^{n+1})
+    if constexpr (SYS != SYS_REACT) source<SYS, D, R>(K, Un, xn, yn, Sn);
     long long off = cell(P, i, j);
     R Us[M];
 #pragma unroll
@@ -274,7 +279,12 @@ __global__ void k_collide_stream(DevParams P, R* const* buf, Ctl* ctl, int slot,
       R akk = k == 0 ? ak[0] : ak[1 + (k - 1) % D];
 #pragma unroll
       for (int c = 0; c < M; c++) {
-        R v = Fk[k][c] + hdt * akk * S[c];
+        R v = Fk[k][c];
+        if constexpr (SYS == SYS_REACT) {
+          if (src_field<SYS, D>(c)) v += akk * (Un[c] - Ubar[c]);
+        } else {
+          v += hdt * akk * Sn[c];
+        }
         fo[chk((long long)(k * M + c) * P.plane + off, (long long)Q * M * P.plane, stc)] = v;
         Us[c] += v;  // the moments the next step will see (Eq. 2.3, k = 0..Q-1)
       }
