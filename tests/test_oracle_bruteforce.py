@@ -49,6 +49,41 @@ def test_push_form_wet_dry():
         assert np.all(np.abs(f - r.f) <= 1e-13 * np.abs(r.f).max())
 
 
+@pytest.mark.parametrize("dim", [1, 2])
+def test_push_form_bed_with_dry_cells(dim):
+    """The bed-slope source next to dry nodes: a dam break towards the
+    Gaussian bump, whose top sticks out of a shallow pool (h = 0 there), and
+    one node with 0 < h < h_dry (dry, at rest).  The pure-Python push-form
+    stepper applies Section 5's bed source and the dry-node rule on its own;
+    the oracle must agree with it to rounding."""
+    if dim == 1:
+        pb = W.Problem(system=W.SWE, dim=1, nx=12, x0=-1.0, x1=1.0, cfl=0.9, bc=(W.OUTFLOW,) * 4,
+                       bed_amp=0.5, bed_w2=0.1, bed_xc=0.2)
+    else:
+        pb = W.Problem(system=W.SWE, dim=2, nx=8, ny=7, x0=-1.0, x1=1.0, y0=-0.875, y1=0.875, cfl=0.9,
+                       bc=(W.OUTFLOW,) * 4, bed_amp=0.5, bed_w2=0.1, bed_xc=0.2, bed_yc=0.0)
+    X, Y = W.cell_centres(pb)
+    b = pb.bed_amp * np.exp(-((X - pb.bed_xc) ** 2 + (Y - pb.bed_yc) ** 2 if dim == 2 else (X - pb.bed_xc) ** 2)
+                            / pb.bed_w2)
+    h = np.where(X <= -0.4, 1.5, np.maximum(0.0, 0.3 - b))
+    assert np.any(h == 0.0) and np.any(h > 0.0)
+    # one node in the pool beyond the bump with 0 < h < h_dry and momentum h u
+    # (u = 1 if it were wet): the rule takes it as dry, at rest
+    i = np.argmax(X.ravel() > 0.6)
+    h.flat[i] = 0.5 * pb.h_dry
+    u = np.zeros_like(h)
+    u.flat[i] = 1.0
+    U0 = W.swe_conservative(pb, h, u)
+    r = oracle.Run(pb, U0)
+    f = r.f.copy()
+    for _ in range(4):
+        f, dt = BF.step(pb, f)
+        r.step(1)
+        assert r.info[2] == pytest.approx(dt, rel=1e-14)
+        scale = np.abs(r.f).max(axis=(0, 2, 3), keepdims=True)
+        assert np.all(np.abs(f - r.f) <= 1e-13 * scale), np.abs(f - r.f).max()
+
+
 def boundary_cases():
     """Reflecting walls, fixed inflow and the sponge layer (Example 5.13's
     boundaries) on every system, including corners where two kinds meet."""
