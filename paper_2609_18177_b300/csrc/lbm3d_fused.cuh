@@ -39,7 +39,7 @@ constexpr int kURing3 = 4;
 
 // Tile height (rows of 32 columns; one warp per row).  8 rows, 256 threads.
 // Tiles of 16 rows (512 threads, one block per SM) cut the indicator's
-// recompute on the tile + 2 from 1.75 to 1.44 evaluations per output node,
+// recompute on the tile + 2 from 1.69 to 1.41 evaluations per output node,
 // but ran slower (256^3 Euler FP32: 1.37 against 1.30 ms per step): two
 // blocks of 8 warps overlap one another's barriers, one block of 16 does not.
 template <int SYS, class R>
