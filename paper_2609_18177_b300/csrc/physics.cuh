@@ -312,8 +312,9 @@ __device__ __forceinline__ float arrhenius_f32(const Phys<float>& K, float rho, 
 // Euler: rho*Y alone (S is identically 0 in the other fields, and adding
 // dt/2 a_k * 0 would still cost a multiply-add per direction and field).  The
 // other systems add to every field: for shallow water, skipping the zero field
-// together with the second half-source taken from Eq. (2.8) (below) made the
-// 2D step slower (2048^2 dam break 0.1545 against 0.150 ms).
+// together with taking the second half-source dt/2 S(U^{n+1}) as U^{n+1} - Ubar
+// (Eq. 2.8; the kernels' moment step does so for reactive Euler) made the 2D
+// step slower (2048^2 dam break 0.1545 against 0.150 ms).
 template <int SYS, int D>
 __host__ __device__ constexpr bool src_field(int c) {
   return SYS == SYS_REACT ? c == D + 2 : true;
